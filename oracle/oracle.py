@@ -1,0 +1,320 @@
+"""FP64 CPU oracle: the plain reference for the CUDA reconstruction path.
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, the smoke check and the
+benchmark's CPU-baseline leg, never by the library. It shares no code with the
+CUDA path. The heavy loops (warp, projection, transpose, tumor fixed point)
+are plain C in oracle.c, compiled by build_oracle(); the optimiser of
+Section 2.2 is written here step by step in the paper's order.
+
+Functions and the passages they follow:
+  dvf          Eq. 1 (x = mean + U w)
+  warp         Section 2.2, trilinear interpolation of f0 at v + x(v)
+  warp_jac     Section 2.2, h_k = (df/dx) . u_k consistent with the interpolation
+  project      Eq. 2, the projection matrix P
+  backproject  gradient formula after Eq. 4, P^T
+  cost         Eq. 2, J = ||P f - a y - b 1||^2
+  fit_ab       Eq. 4, (a, b) = (Y^T Y)^-1 Y^T P f, Y = [y, 1]
+  gradient     gradient formula after Eq. 4: 2 U^T (df/dx) P^T (P f - a y - b 1)
+  reconstruct  Section 2.2: alternate Eq. 3 (Armijo step on w) and Eq. 4
+  tumor        Section 2.3 with the fixed-point inversion of ref. 13
+
+Readings of the paper where it is silent (the CUDA path uses the same):
+  * Armijo rule (Section 2.2 names it, gives no constants): sufficient
+    decrease J(w - mu g; a, b) <= J(w; a, b) - c1 mu |g|^2 with c1 = 1e-4,
+    backtracking mu <- beta mu with beta = 0.5, at most 20 backtracks. The
+    first trial step is mu = step0_mm / |g| (moves w by step0_mm), later ones
+    start from 2 x the last accepted mu. No accepted step: w is kept and the
+    solve stops with stop reason "line search failed".
+  * (a, b) before the first step 1: Eq. 4 at the starting w.
+  * Stop (Section 2.2: gradient "sufficiently small" or the iteration cap):
+    |g| <= grad_tol * |g_0| or max_iters accepted steps.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+STOP_GRAD_TOL = 1
+STOP_MAX_ITERS = 2
+STOP_LINESEARCH_FAILED = 3
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (plain -O2, single thread)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Vol(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double)]
+
+
+class _Geom(ctypes.Structure):
+    _fields_ = [("sad", ctypes.c_double), ("sdd", ctypes.c_double), ("nu", ctypes.c_int),
+                ("nv", ctypes.c_int), ("du", ctypes.c_double), ("dv", ctypes.c_double),
+                ("ds", ctypes.c_double)]
+
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build_oracle())
+    return _lib
+
+
+def _vol(v) -> _Vol:
+    return _Vol(v.nx, v.ny, v.nz, v.dx, v.dy, v.dz)
+
+
+def _geom(g) -> _Geom:
+    return _Geom(g.sad, g.sdd, g.nu, g.nv, g.du, g.dv, g.ds)
+
+
+def _d(a):
+    """C-contiguous float64 copy/view and its pointer."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ----------------------------------------------------------------------------
+# Operators
+# ----------------------------------------------------------------------------
+
+
+def dvf(vol, mean, U, w):
+    """Eq. 1: x = mean + sum_k u_k w_k, [3][nz][ny][nx]."""
+    mean, pm = _d(mean)
+    U, pu = _d(U)
+    w, pw = _d(np.atleast_1d(w))
+    out = np.empty(mean.shape, dtype=np.float64)
+    _L().or_dvf(ctypes.byref(_vol(vol)), pm, pu, ctypes.c_int(U.shape[0]), pw,
+                out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def warp(vol, f0, x):
+    """Section 2.2: f(v) = F0(v + x(v)) (trilinear, zero outside the grid)."""
+    f0, pf = _d(f0)
+    x, px = _d(x)
+    out = np.empty(f0.shape, dtype=np.float64)
+    _L().or_warp(ctypes.byref(_vol(vol)), pf, px, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def warp_jac(vol, f0, x, U):
+    """h_k(v) = (df/dx)(v) . u_k(v), [K][nz][ny][nx]."""
+    f0, pf = _d(f0)
+    x, px = _d(x)
+    U, pu = _d(U)
+    K = U.shape[0]
+    out = np.empty((K,) + f0.shape, dtype=np.float64)
+    _L().or_warp_jac(ctypes.byref(_vol(vol)), pf, px, pu, ctypes.c_int(K),
+                     out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def project(vol, geom, angle, f):
+    """Eq. 2: P f at gantry angle `angle` (rad), [nv][nu]."""
+    f, pf = _d(f)
+    out = np.empty((geom.nv, geom.nu), dtype=np.float64)
+    _L().or_project(ctypes.byref(_vol(vol)), ctypes.byref(_geom(geom)), ctypes.c_double(angle), pf,
+                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def backproject(vol, geom, angle, r):
+    """P^T r, [nz][ny][nx]."""
+    r, pr = _d(r)
+    out = np.empty(vol.shape, dtype=np.float64)
+    _L().or_backproject(ctypes.byref(_vol(vol)), ctypes.byref(_geom(geom)), ctypes.c_double(angle),
+                        pr, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def ray(geom, angle, iu, iv):
+    """Source and unit direction of the ray to pixel (iu, iv)."""
+    src = np.empty(3)
+    d = np.empty(3)
+    _L().or_ray(ctypes.byref(_geom(geom)), ctypes.c_double(angle), ctypes.c_int(iu), ctypes.c_int(iv),
+                src.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                d.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return src, d
+
+
+def tumor(vol, mean, U, w, c0, tol=1e-6, max_iter=100):
+    """Section 2.3 / ref. 13: p with p + x(p) = c0 by p <- c0 - x(p). Returns (p, steps)."""
+    mean, pm = _d(mean)
+    U, pu = _d(U)
+    w, pw = _d(np.atleast_1d(w))
+    c0, pc = _d(c0)
+    p = np.empty(3)
+    it = _L().or_tumor(ctypes.byref(_vol(vol)), pm, pu, ctypes.c_int(U.shape[0]), pw, pc,
+                       ctypes.c_double(tol), ctypes.c_int(max_iter),
+                       p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return p, int(it)
+
+
+def dvf_at(vol, mean, U, w, point):
+    """x = mean + U w interpolated (clamp-to-edge) at a world point (mm)."""
+    mean, pm = _d(mean)
+    U, pu = _d(U)
+    w, pw = _d(np.atleast_1d(w))
+    point, pp = _d(point)
+    out = np.empty(3)
+    _L().or_dvf_at(ctypes.byref(_vol(vol)), pm, pu, ctypes.c_int(U.shape[0]), pw, pp,
+                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Cost, intensity fit, gradient (Eqs. 2-4)
+# ----------------------------------------------------------------------------
+
+
+def cost(p, y, a, b):
+    """Eq. 2: J = || p - a y - b 1 ||_2^2."""
+    r = np.asarray(p, dtype=np.float64) - a * np.asarray(y, dtype=np.float64) - b
+    return float(np.sum(r * r))
+
+
+def fit_ab(p, y):
+    """Eq. 4: (a, b)^T = (Y^T Y)^-1 Y^T p with Y = [y, 1]."""
+    yv = np.asarray(y, dtype=np.float64).ravel()
+    Y = np.stack([yv, np.ones_like(yv)], axis=1)
+    a, b = np.linalg.solve(Y.T @ Y, Y.T @ np.asarray(p, dtype=np.float64).ravel())
+    return float(a), float(b)
+
+
+@dataclasses.dataclass
+class Model:
+    """A patient's PCA motion model as the solver sees it (all float64)."""
+
+    vol: object
+    f0: np.ndarray
+    mean: np.ndarray
+    U: np.ndarray
+    c0: np.ndarray
+
+    @property
+    def K(self):
+        return self.U.shape[0]
+
+
+@dataclasses.dataclass
+class Evaluation:
+    w: np.ndarray
+    f: np.ndarray
+    p: np.ndarray
+
+
+def evaluate(model, geom, angle, w):
+    """x = mean + U w, f = warped f0, p = P f."""
+    x = dvf(model.vol, model.mean, model.U, w)
+    f = warp(model.vol, model.f0, x)
+    p = project(model.vol, geom, angle, f)
+    return Evaluation(np.array(w, dtype=np.float64), f, p)
+
+
+def gradient(model, geom, angle, w, a, b, y):
+    """dJ/dw = 2 U^T (df/dx) P^T (P f - a y - b 1), as the sum over voxels of
+    2 (P^T r)(v) h_k(v). Returns (g, J, p)."""
+    x = dvf(model.vol, model.mean, model.U, w)
+    f = warp(model.vol, model.f0, x)
+    h = warp_jac(model.vol, model.f0, x, model.U)
+    p = project(model.vol, geom, angle, f)
+    r = p - a * np.asarray(y, dtype=np.float64) - b
+    bp = backproject(model.vol, geom, angle, r)
+    g = np.array([2.0 * np.sum(bp * h[k]) for k in range(model.K)])
+    return g, float(np.sum(r * r)), p
+
+
+@dataclasses.dataclass
+class SolveOptions:
+    max_iters: int = 10
+    grad_tol: float = 1e-6
+    c1: float = 1e-4
+    beta: float = 0.5
+    max_backtracks: int = 20
+    step0_mm: float = 1.0
+    tumor_tol: float = 1e-6
+    tumor_max_iter: int = 100
+
+
+@dataclasses.dataclass
+class SolveResult:
+    w: np.ndarray
+    a: float
+    b: float
+    J: float
+    grad: np.ndarray
+    iters: int
+    backtracks: int
+    stop_reason: int
+    tumor: np.ndarray
+    tumor_steps: int
+    history: list  # per accepted step: dict(J_after_step1, J_after_step2, mu, w)
+
+
+def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None) -> SolveResult:
+    """Section 2.2: alternate step 1 (Eq. 3, gradient step with Armijo's rule at
+    fixed a, b) and step 2 (Eq. 4, exact a, b at fixed w), then Section 2.3."""
+    o = opts or SolveOptions()
+    y = np.asarray(y, dtype=np.float64)
+    w = np.array(w0, dtype=np.float64)
+    # (a, b) at the starting w by Eq. 4.
+    a, b = fit_ab(evaluate(model, geom, angle, w).p, y)
+    g, J, _ = gradient(model, geom, angle, w, a, b, y)
+    g0 = float(np.linalg.norm(g))
+    mu_prev = None
+    n = 0
+    backtracks = 0
+    stop = STOP_MAX_ITERS
+    history = []
+    while True:
+        gn = float(np.linalg.norm(g))
+        if gn <= o.grad_tol * g0 or gn == 0.0:
+            stop = STOP_GRAD_TOL
+            break
+        if n >= o.max_iters:
+            stop = STOP_MAX_ITERS
+            break
+        # Step 1: w <- w - mu g, mu by backtracking from the initial trial.
+        mu = o.step0_mm / gn if mu_prev is None else 2.0 * mu_prev
+        accepted = None
+        for bt in range(o.max_backtracks + 1):
+            trial = evaluate(model, geom, angle, w - mu * g)
+            J_t = cost(trial.p, y, a, b)
+            if J_t <= J - o.c1 * mu * gn * gn:
+                accepted = trial
+                break
+            backtracks += 1
+            mu *= o.beta
+        if accepted is None:
+            stop = STOP_LINESEARCH_FAILED
+            break
+        w = accepted.w
+        mu_prev = mu
+        # Step 2: (a, b) by Eq. 4 at the new w.
+        a, b = fit_ab(accepted.p, y)
+        g, J, _ = gradient(model, geom, angle, w, a, b, y)
+        history.append(dict(J_step1=J_t, J_step2=J, mu=mu, w=w.copy()))
+        n += 1
+    p_t, steps = tumor(model.vol, model.mean, model.U, w, model.c0, o.tumor_tol, o.tumor_max_iter)
+    return SolveResult(w=w, a=a, b=b, J=J, grad=g, iters=n, backtracks=backtracks, stop_reason=stop,
+                       tumor=p_t, tumor_steps=steps, history=history)

@@ -1,0 +1,412 @@
+"""Pins of the FP64 oracle against facts it does not compute itself.
+
+Each test ties one oracle routine to a closed form, an exact special case, a
+library routine, a brute-force construction or a finite difference, so that a
+dropped term, a wrong sign, a swapped axis or a transposed operand fails at
+least one of them.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from phantom import Geometry, Volume, build_pca, phantom_volume, training_dvfs, tumor_centre
+
+RNG = np.random.default_rng(12345)
+
+
+def _rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _grid_points(vol):
+    ax, ay, az = vol.axes()
+    return np.meshgrid(az, ay, ax, indexing="ij")  # z, y, x
+
+
+# ----------------------------------------------------------------------------
+# Eq. 1: DVF synthesis
+# ----------------------------------------------------------------------------
+
+
+def test_dvf_zero_w_is_mean_exactly():
+    vol = Volume(7, 5, 4, 1.0, 2.0, 3.0)
+    mean = RNG.standard_normal((3,) + vol.shape)
+    U = RNG.standard_normal((3, 3) + vol.shape)
+    assert np.array_equal(O.dvf(vol, mean, U, np.zeros(3)), mean)
+
+
+def test_dvf_matches_tensor_contraction_and_is_affine_in_w():
+    vol = Volume(6, 5, 4, 1.0, 2.0, 3.0)
+    mean = RNG.standard_normal((3,) + vol.shape)
+    U = RNG.standard_normal((4, 3) + vol.shape)
+    w1, w2 = RNG.standard_normal(4), RNG.standard_normal(4)
+    expect = mean + np.tensordot(w1, U, axes=(0, 0))
+    assert _rel(O.dvf(vol, mean, U, w1), expect) < 1e-14
+    lhs = O.dvf(vol, mean, U, w1 + w2) - mean
+    rhs = (O.dvf(vol, mean, U, w1) - mean) + (O.dvf(vol, mean, U, w2) - mean)
+    assert _rel(lhs, rhs) < 1e-13
+
+
+# ----------------------------------------------------------------------------
+# Section 2.2: trilinear warp and its exact derivative
+# ----------------------------------------------------------------------------
+
+
+def test_warp_zero_dvf_is_identity_bitwise():
+    vol = Volume(9, 7, 5, 2.0, 2.0, 2.5)
+    f0 = RNG.random(vol.shape)
+    assert np.array_equal(O.warp(vol, f0, np.zeros((3,) + vol.shape)), f0)
+
+
+def test_warp_integer_shift_is_exact_shift_with_zero_fill():
+    vol = Volume(9, 8, 7, 2.0, 3.0, 2.5)
+    f0 = RNG.random(vol.shape)
+    sx, sy, sz = 2, -1, 3  # voxels; pull-back: f(v) = f0(v + s)
+    x = np.zeros((3,) + vol.shape)
+    x[0], x[1], x[2] = sx * vol.dx, sy * vol.dy, sz * vol.dz
+    f = O.warp(vol, f0, x)
+    expect = np.zeros(vol.shape)
+    for k in range(vol.nz):
+        for j in range(vol.ny):
+            for i in range(vol.nx):
+                ii, jj, kk = i + sx, j + sy, k + sz
+                if 0 <= ii < vol.nx and 0 <= jj < vol.ny and 0 <= kk < vol.nz:
+                    expect[k, j, i] = f0[kk, jj, ii]
+    assert np.array_equal(f, expect)
+
+
+def test_warp_reproduces_affine_image_under_subvoxel_shift():
+    vol = Volume(10, 9, 8, 2.0, 3.0, 2.5)
+    zi, yi, xi = np.meshgrid(np.arange(vol.nz), np.arange(vol.ny), np.arange(vol.nx), indexing="ij")
+    beta = np.array([0.3, -0.7, 1.1])
+    f0 = 2.0 + beta[0] * xi + beta[1] * yi + beta[2] * zi
+    shift = np.array([0.37, -0.81, 0.55])  # mm
+    x = np.zeros((3,) + vol.shape)
+    for c in range(3):
+        x[c] = shift[c]
+    f = O.warp(vol, f0, x)
+    q = shift / vol.spacing
+    expect = 2.0 + beta[0] * (xi + q[0]) + beta[1] * (yi + q[1]) + beta[2] * (zi + q[2])
+    inside = ((xi + q[0] >= 0) & (xi + q[0] <= vol.nx - 1) & (yi + q[1] >= 0) &
+              (yi + q[1] <= vol.ny - 1) & (zi + q[2] >= 0) & (zi + q[2] <= vol.nz - 1))
+    assert inside.sum() > 100
+    assert np.max(np.abs(f[inside] - expect[inside])) < 1e-12
+    # Beyond the support (-1, n) the interpolant is exactly zero.
+    x[0] = -5.0 * vol.nx * vol.dx
+    assert np.all(O.warp(vol, f0, x) == 0.0)
+
+
+def test_warp_jacobian_of_affine_image_is_its_slope():
+    vol = Volume(10, 9, 8, 2.0, 3.0, 2.5)
+    zi, yi, xi = np.meshgrid(np.arange(vol.nz), np.arange(vol.ny), np.arange(vol.nx), indexing="ij")
+    beta = np.array([0.3, -0.7, 1.1])  # per index step
+    f0 = 2.0 + beta[0] * xi + beta[1] * yi + beta[2] * zi
+    x = np.zeros((3,) + vol.shape)
+    x[0], x[1], x[2] = 0.41, -0.93, 0.77
+    U = RNG.standard_normal((2, 3) + vol.shape)
+    h = O.warp_jac(vol, f0, x, U)
+    q = np.array([0.41, -0.93, 0.77]) / vol.spacing
+    inside = ((xi + q[0] > 0) & (xi + q[0] < vol.nx - 1) & (yi + q[1] > 0) &
+              (yi + q[1] < vol.ny - 1) & (zi + q[2] > 0) & (zi + q[2] < vol.nz - 1))
+    for k in range(2):
+        expect = sum(beta[c] / vol.spacing[c] * U[k, c] for c in range(3))
+        assert np.max(np.abs(h[k][inside] - expect[inside])) < 1e-12
+
+
+def test_warp_jacobian_matches_central_differences():
+    vol = Volume(12, 11, 10, 2.0, 3.0, 2.5)
+    f0 = RNG.random(vol.shape)
+    mean = 1.5 * RNG.standard_normal((3,) + vol.shape)
+    U = RNG.standard_normal((3, 3) + vol.shape)
+    w = np.array([0.3, -0.2, 0.4])
+    x = O.dvf(vol, mean, U, w)
+    h = O.warp_jac(vol, f0, x, U)
+    eps = 1e-6
+    q = np.stack([x[c] / vol.spacing[c] for c in range(3)])
+    frac = q - np.floor(q)
+    zi, yi, xi = np.meshgrid(np.arange(vol.nz), np.arange(vol.ny), np.arange(vol.nx), indexing="ij")
+    idx = np.stack([xi, yi, zi]) + q
+    dims = np.array([vol.nx, vol.ny, vol.nz]).reshape(3, 1, 1, 1)
+    ok = np.all((frac > 1e-3) & (frac < 1 - 1e-3), axis=0) & np.all((idx > -1) & (idx < dims), axis=0)
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = eps
+        fp = O.warp(vol, f0, O.dvf(vol, mean, U, w + e))
+        fm = O.warp(vol, f0, O.dvf(vol, mean, U, w - e))
+        fd = (fp - fm) / (2 * eps)
+        assert ok.sum() > 200
+        assert _rel(h[k][ok], fd[ok]) < 1e-7
+
+
+# ----------------------------------------------------------------------------
+# Eq. 2: cone-beam projection P
+# ----------------------------------------------------------------------------
+
+
+def test_central_ray_through_uniform_block_matches_closed_form():
+    # nx, nz odd put the isocentre on a voxel centre, so the central ray (odd
+    # detector) runs along +y through voxel centres. The interpolant of a
+    # uniform block of n voxels integrates to mu * n * dy along y; the
+    # source-anchored midpoint sum errs by at most |slope jump| ds^2 / 8 at each
+    # of the four kinks: mu ds^2 / (2 dy) in total.
+    vol = Volume(9, 11, 9, 2.0, 3.0, 2.5)
+    mu = 0.02
+    f = np.full(vol.shape, mu)
+    for ds in (0.7, 0.35, 1.3):
+        g = Geometry(1000.0, 1500.0, 3, 3, 1.0, 1.0, ds)
+        p = O.project(vol, g, 0.0, f)
+        exact = mu * vol.ny * vol.dy
+        assert abs(p[1, 1] - exact) <= mu * ds * ds / (2 * vol.dy) + 1e-12
+
+
+def test_projection_rotates_with_the_gantry():
+    # Projecting f at angle th + 90 deg equals projecting f rotated by -90 deg
+    # about z at angle th (square in-plane grid, so the rotation maps the grid
+    # onto itself): g[k, j, i] = f[k, i, n - 1 - j].
+    vol = Volume(10, 10, 6, 2.0, 2.0, 2.5)
+    f = RNG.random(vol.shape)
+    g = np.empty_like(f)
+    n = vol.nx
+    for j in range(n):
+        for i in range(n):
+            g[:, j, i] = f[:, i, n - 1 - j]
+    geom = Geometry(1000.0, 1500.0, 12, 8, 2.0, 2.5, 0.6)
+    th = 0.37
+    assert _rel(O.project(vol, geom, th + math.pi / 2, f), O.project(vol, geom, th, g)) < 1e-12
+
+
+def test_point_object_lands_at_pinhole_position():
+    vol = Volume(21, 19, 17, 2.0, 2.0, 2.5)
+    geom = Geometry(1000.0, 1500.0, 150, 130, 0.5, 0.5, 0.25)
+    i0, j0, k0 = 14, 5, 12
+    f = np.zeros(vol.shape)
+    f[k0, j0, i0] = 1.0
+    P = vol.origin + np.array([i0, j0, k0]) * vol.spacing
+    for th in (0.0, 0.6, 2.3):
+        S = np.array([geom.sad * math.sin(th), -geom.sad * math.cos(th), 0.0])
+        e = np.array([-math.sin(th), math.cos(th), 0.0])
+        u = np.array([math.cos(th), math.sin(th), 0.0])
+        lam = (P - S) @ e
+        iu = geom.sdd * ((P - S) @ u) / lam / geom.du + 0.5 * (geom.nu - 1)
+        iv = geom.sdd * (P[2] - S[2]) / lam / geom.dv + 0.5 * (geom.nv - 1)
+        p = O.project(vol, geom, th, f)
+        assert p.sum() > 0
+        vv, uu = np.meshgrid(np.arange(geom.nv), np.arange(geom.nu), indexing="ij")
+        cu, cv = (p * uu).sum() / p.sum(), (p * vv).sum() / p.sum()
+        assert abs(cu - iu) < 0.35 and abs(cv - iv) < 0.35
+
+
+def _voxelised_sphere(vol, radius, sub=4):
+    ax, ay, az = vol.axes()
+    offs = (np.arange(sub) + 0.5) / sub - 0.5
+    z, y, x = np.meshgrid(az, ay, ax, indexing="ij")
+    acc = np.zeros(vol.shape)
+    for ox in offs:
+        for oy in offs:
+            for oz in offs:
+                px, py, pz = x + ox * vol.dx, y + oy * vol.dy, z + oz * vol.dz
+                acc += (px * px + py * py + pz * pz < radius * radius)
+    return acc / sub ** 3
+
+
+def test_sphere_chords_converge_to_closed_form():
+    radius = 14.0
+    errs = []
+    for d in (2.0, 1.0):
+        n = int(round(40.0 / d))
+        vol = Volume(n, n, n, d, d, d)
+        f = _voxelised_sphere(vol, radius)
+        geom = Geometry(1000.0, 1500.0, 15, 13, 2.4, 2.4, d / 2)
+        th = 0.45
+        p = O.project(vol, geom, th, f)
+        chord = np.zeros_like(p)
+        for iv in range(geom.nv):
+            for iu in range(geom.nu):
+                src, dr = O.ray(geom, th, iu, iv)
+                tc = -src @ dr
+                dist2 = src @ src - tc * tc
+                chord[iv, iu] = 2 * math.sqrt(max(radius ** 2 - dist2, 0.0))
+        core = chord > 2 * math.sqrt(radius ** 2 - (radius - 3.0) ** 2)
+        errs.append(_rel(p[core], chord[core]))
+    assert errs[0] < 0.02
+    assert errs[1] < 0.6 * errs[0]
+
+
+# ----------------------------------------------------------------------------
+# P^T: exact transpose
+# ----------------------------------------------------------------------------
+
+
+def test_adjoint_identity():
+    vol = Volume(12, 10, 8, 2.0, 3.0, 2.5)
+    geom = Geometry(1000.0, 1500.0, 9, 7, 3.0, 3.5, 1.1)
+    for th in (0.3, 1.9):
+        x = RNG.standard_normal(vol.shape)
+        y = RNG.standard_normal((geom.nv, geom.nu))
+        lhs = float(np.sum(O.project(vol, geom, th, x) * y))
+        rhs = float(np.sum(x * O.backproject(vol, geom, th, y)))
+        assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
+
+
+def test_dense_transpose_on_8_cube():
+    vol = Volume(8, 8, 8, 3.0, 3.0, 3.0)
+    geom = Geometry(1000.0, 1500.0, 6, 6, 6.0, 6.0, 1.5)
+    th = 0.8
+    n, R = vol.n, geom.n_rays
+    P = np.empty((R, n))
+    for e in range(n):
+        unit = np.zeros(n)
+        unit[e] = 1.0
+        P[:, e] = O.project(vol, geom, th, unit.reshape(vol.shape)).ravel()
+    PT = np.empty((n, R))
+    for r in range(R):
+        unit = np.zeros(R)
+        unit[r] = 1.0
+        PT[:, r] = O.backproject(vol, geom, th, unit.reshape(geom.nv, geom.nu)).ravel()
+    assert np.count_nonzero(P) > 1000
+    assert np.max(np.abs(P - PT.T)) < 1e-13
+
+
+# ----------------------------------------------------------------------------
+# Eqs. 2-4: cost, intensity fit, gradient
+# ----------------------------------------------------------------------------
+
+
+def _tiny_model(K=3, n=16, d=4.0):
+    vol = Volume(n, n, n, d, d, d)
+    f0 = phantom_volume(vol)
+    pca = build_pca(training_dvfs(vol), K)
+    return O.Model(vol, f0, pca.mean, pca.U, tumor_centre(vol)), pca
+
+
+def test_fit_ab_is_least_squares_minimiser():
+    p = RNG.random((7, 9)) * 3
+    y = 0.8 * p + 0.1 + 0.05 * RNG.standard_normal(p.shape)
+    a, b = O.fit_ab(p, y)
+    A = np.stack([y.ravel(), np.ones(y.size)], axis=1)
+    ref = np.linalg.lstsq(A, p.ravel(), rcond=None)[0]
+    assert abs(a - ref[0]) < 1e-12 and abs(b - ref[1]) < 1e-12
+    J = O.cost(p, y, a, b)
+    for da, db in ((1e-3, 0), (-1e-3, 0), (0, 1e-3), (0, -1e-3), (1e-3, -1e-3)):
+        assert O.cost(p, y, a + da, b + db) > J
+    assert abs(O.cost(p, y, a, b) - np.sum((p - a * y - b) ** 2)) < 1e-12
+
+
+def test_gradient_matches_central_differences_of_J():
+    m, pca = _tiny_model()
+    geom = Geometry(1000.0, 1500.0, 24, 24, 3.2, 3.2, 2.0)
+    th = 0.5
+    y = O.evaluate(m, geom, th, np.array([0.6, -0.4, 0.2])).p
+    y = y + 0.02 * RNG.standard_normal(y.shape)
+    w = np.array([0.13, 0.21, -0.17])
+    a, b = 1.07, 0.013
+    g, J, _ = O.gradient(m, geom, th, w, a, b, y)
+    eps = 1e-5
+    fd = np.empty(3)
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = eps
+        Jp = O.cost(O.evaluate(m, geom, th, w + e).p, y, a, b)
+        Jm = O.cost(O.evaluate(m, geom, th, w - e).p, y, a, b)
+        fd[k] = (Jp - Jm) / (2 * eps)
+    assert _rel(g, fd) < 1e-6
+    assert abs(J - O.cost(O.evaluate(m, geom, th, w).p, y, a, b)) < 1e-12 * J
+
+
+def test_gradient_equals_forward_mode_contraction():
+    # sum_v (P^T r)(v) h_k(v) = sum_rays r (P h_k): the adjoint and the
+    # forward-mode form of the same derivative.
+    m, pca = _tiny_model(n=20, d=3.2)
+    geom = Geometry(1000.0, 1500.0, 20, 18, 3.0, 3.0, 1.6)
+    th = 1.1
+    w = np.array([0.3, -0.1, 0.05])
+    y = O.evaluate(m, geom, th, w * 1.3).p
+    a, b = 0.97, -0.01
+    g, J, p = O.gradient(m, geom, th, w, a, b, y)
+    x = O.dvf(m.vol, m.mean, m.U, w)
+    h = O.warp_jac(m.vol, m.f0, x, m.U)
+    r = p - a * y - b
+    fwd = np.array([2 * np.sum(r * O.project(m.vol, geom, th, h[k])) for k in range(3)])
+    assert _rel(g, fwd) < 1e-10
+
+
+# ----------------------------------------------------------------------------
+# Section 2.2: alternation with Armijo's rule
+# ----------------------------------------------------------------------------
+
+
+def test_cost_never_increases_across_steps(small_case):
+    c = small_case
+    m = O.Model(c["vol"], c["f0"], c["pca"].mean, c["pca"].U, c["c0"])
+    f_t = O.warp(c["vol"], c["f0"], c["x_test"])
+    p_t = O.project(c["vol"], c["geom"], c["angle"], f_t)
+    y = p_t + 0.01 * p_t * np.random.default_rng(0).standard_normal(p_t.shape)
+    res = O.reconstruct(m, c["geom"], c["angle"], y, np.zeros(3), O.SolveOptions(max_iters=6))
+    a0, b0 = O.fit_ab(O.evaluate(m, c["geom"], c["angle"], np.zeros(3)).p, y)
+    J_prev = O.cost(O.evaluate(m, c["geom"], c["angle"], np.zeros(3)).p, y, a0, b0)
+    assert res.iters == 6
+    for h in res.history:
+        assert h["J_step1"] <= J_prev  # step 1 (Armijo, fixed a, b)
+        assert h["J_step2"] <= h["J_step1"] + 1e-12 * J_prev  # step 2 (exact minimiser)
+        J_prev = h["J_step2"]
+
+
+def test_single_mode_recovers_true_coefficient():
+    # One PCA mode, noise-free target inside the model: the alternation reaches
+    # w_true, a = 1, b = 0 (the unique zero-cost point).
+    m, pca = _tiny_model(K=1, n=24, d=3.0)
+    geom = Geometry(1000.0, 1500.0, 32, 32, 2.4, 2.4, 1.5)
+    th = 0.2
+    w_true = np.array([0.9])
+    y = O.evaluate(m, geom, th, w_true).p
+    res = O.reconstruct(m, geom, th, y, np.zeros(1), O.SolveOptions(max_iters=40, grad_tol=1e-9))
+    assert abs(res.w[0] - w_true[0]) < 1e-4
+    assert abs(res.a - 1.0) < 1e-5 and abs(res.b) < 1e-5
+
+
+# ----------------------------------------------------------------------------
+# Section 2.3: tumor by fixed-point inversion
+# ----------------------------------------------------------------------------
+
+
+def test_tumor_under_translation_is_c0_minus_shift():
+    vol = Volume(16, 14, 12, 2.0, 2.0, 2.5)
+    t = np.array([1.3, -2.1, 4.4])
+    mean = np.zeros((3,) + vol.shape)
+    for c in range(3):
+        mean[c] = t[c]
+    U = RNG.standard_normal((2, 3) + vol.shape)
+    c0 = np.array([-3.0, 2.0, 1.5])
+    p, steps = O.tumor(vol, mean, U, np.zeros(2), c0, tol=1e-12)
+    assert np.max(np.abs(p - (c0 - t))) < 1e-12
+    assert steps <= 3
+
+
+def test_tumor_under_affine_dvf_solves_linear_system():
+    # Trilinear interpolation reproduces an affine field exactly, so the fixed
+    # point of p = c0 - (A p + t) is (I + A)^-1 (c0 - t).
+    vol = Volume(20, 18, 16, 2.0, 2.5, 3.0)
+    A = np.array([[0.05, -0.02, 0.01], [0.03, 0.04, -0.02], [-0.01, 0.02, 0.06]])
+    t = np.array([0.7, -1.2, 2.0])
+    z, y, x = _grid_points(vol)
+    pts = np.stack([x, y, z])
+    mean = np.einsum("ab,b...->a...", A, pts) + t.reshape(3, 1, 1, 1)
+    U = np.zeros((1, 3) + vol.shape)
+    c0 = np.array([4.0, -3.0, 2.5])
+    p, _ = O.tumor(vol, mean, U, np.zeros(1), c0, tol=1e-13, max_iter=200)
+    expect = np.linalg.solve(np.eye(3) + A, c0 - t)
+    assert np.max(np.abs(p - expect)) < 1e-10
+
+
+def test_tumor_round_trip_on_pca_dvf(small_case):
+    c = small_case
+    w = np.array([1.2, -0.3, 0.1])
+    p, steps = O.tumor(c["vol"], c["pca"].mean, c["pca"].U, w, c["c0"], tol=1e-13, max_iter=200)
+    x = O.dvf_at(c["vol"], c["pca"].mean, c["pca"].U, w, p)
+    assert np.max(np.abs(p + x - c["c0"])) < 1e-9
+    assert steps < 200
