@@ -1,0 +1,237 @@
+/*
+ * pcarecon: single-projection volumetric reconstruction with a PCA lung-motion
+ * model, and 3D tumor localisation, on one B300 GPU (sm_103a).
+ *
+ * Method: Li, Jia, Lewis, Gu, Folkerts, Men, Jiang, "Real-time volumetric image
+ * reconstruction and 3D tumor localization based on a single x-ray projection
+ * image for lung cancer radiotherapy". Given a patient's reference volume f0, a
+ * mean DVF and K PCA eigenvector fields (Section 2.1, Eq. 1), one measured
+ * cone-beam projection y and its gantry angle, the library minimises
+ *     J(w, a, b) = || P f(x, f0) - a y - b 1 ||^2,  x = mean + U w     (Eq. 2)
+ * by alternating a gradient step on w with Armijo's line search (Eq. 3) and
+ * the exact (a, b) of Eq. 4, then locates the tumor through the inverted
+ * pull-back DVF (Section 2.3). Every step runs in this library's CUDA kernels.
+ *
+ * Conventions (all entry points):
+ *   - Volumes are [nz][ny][nx] float32, x fastest. Voxel (i,j,k) is at
+ *     origin + (i,j,k)*spacing (mm), origin = -(n-1)/2*spacing: the isocentre is
+ *     the volume centre. x lateral (patient right = -x), y anterior-posterior
+ *     (+y posterior), z superior-inferior (+z cranial).
+ *   - Vector fields are planar [3][nz][ny][nx] (mm, component 0 = x);
+ *     eigenvectors are [K][3][nz][ny][nx]. DVFs are pull-back fields: the
+ *     image at v is f0 trilinearly interpolated at v + x(v) (zero outside the
+ *     grid).
+ *   - Gantry angle th (rad): source (SAD sin th, -SAD cos th, 0); detector
+ *     centre at distance SDD from the source along (-sin th, cos th, 0); detector
+ *     axes u = (cos th, sin th, 0), v = (0, 0, 1); pixel (iu, iv) centre at
+ *     (iu - (nu-1)/2) du, (iv - (nv-1)/2) dv; projections are [nv][nu] float32.
+ *   - Projector P: for each pixel, ds * sum over s >= 0 of the trilinear
+ *     interpolant at S + (s + 1/2) ds d (d = unit direction to the pixel
+ *     centre): ray samples are anchored at the source, so P^T is enumerable
+ *     per voxel.
+ *   - Every call returns an int status: 0 = PR_OK, < 0 = error (then
+ *     pr_last_error() gives a message for the calling thread). No exception or
+ *     CUDA error crosses the boundary. A CUDA fault inside a call is reported
+ *     as PR_ECUDA; the context must then be destroyed.
+ *   - Pointers marked "host" are host memory, "device" are device memory of
+ *     the context's GPU; `location` arguments say which (PR_HOST/PR_DEVICE).
+ *     The library never keeps a caller pointer after a call returns: inputs
+ *     are copied, outputs are written before return (synchronous calls) or
+ *     before the context stream reaches the end of the enqueued work
+ *     (*_async calls).
+ *   - All device work runs on the context's stream (the one given to
+ *     pr_create, else one the library creates). A context is not thread-safe:
+ *     one host thread at a time.
+ */
+#ifndef PCARECON_H
+#define PCARECON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define PR_OK 0
+#define PR_EINVAL (-1)      /* bad argument (null pointer, size, shape, value) */
+#define PR_ENOMEM (-2)      /* device or pinned host allocation failed */
+#define PR_EADMIT (-3)      /* the model does not fit the context's HBM budget */
+#define PR_ECUDA (-4)       /* a CUDA runtime call or kernel failed */
+#define PR_ETIMEOUT (-5)    /* a bounded wait ran out */
+#define PR_ENOMODEL (-6)    /* unknown or released model id */
+#define PR_EUNSUPPORTED (-7)
+
+/* ---- why a solve stopped (pr_result.stop_reason) ---- */
+#define PR_STOP_GRAD_TOL 1          /* |grad J| <= grad_tol * |grad J at start| */
+#define PR_STOP_MAX_ITERS 2         /* max_iters accepted steps (Section 2.2's iteration cap) */
+#define PR_STOP_LINESEARCH_FAILED 3 /* Armijo found no step within max_backtracks; w kept */
+#define PR_STOP_NONFINITE 4         /* non-finite projection or measurement; w kept */
+#define PR_STOP_SINGULAR_FIT 5      /* Y^T Y of Eq. 4 is singular (constant y); w kept */
+#define PR_STOP_GUARD 6             /* internal trial bound reached (should not happen) */
+
+#define PR_MAX_K 7 /* most PCA modes per model */
+
+enum { PR_HOST = 0, PR_DEVICE = 1 };
+enum { PR_F32 = 0, PR_BF16 = 1 }; /* storage of f0 and U on the device */
+enum { PR_LOOP_GRAPH = 0, PR_LOOP_HOST = 1 };
+
+typedef struct pr_ctx pr_ctx;
+
+typedef struct {
+    int nx, ny, nz;     /* voxels */
+    double dx, dy, dz;  /* spacing, mm */
+} pr_volume_desc;
+
+typedef struct {
+    double sad, sdd; /* source-isocentre and source-detector distances, mm */
+    int nu, nv;      /* detector pixels */
+    double du, dv;   /* pixel pitch, mm */
+    double ds;       /* ray sample step, mm; <= 0 selects half the smallest voxel spacing */
+} pr_geometry;
+
+/* Solver options (Section 2.2). The paper names Armijo's rule and a stop on a
+ * small gradient or an iteration cap; the constants are this library's
+ * defaults (pr_default_opts). */
+typedef struct {
+    int max_iters;       /* accepted steps; default 10 */
+    double grad_tol;     /* relative gradient-norm stop; default 1e-6 */
+    double c1;           /* Armijo sufficient-decrease constant; default 1e-4 */
+    double beta;         /* backtracking factor; default 0.5 */
+    int max_backtracks;  /* default 20 */
+    double step0_mm;     /* first trial step moves w by this many mm; default 1 */
+    int cold_start;      /* 1: start from w0; 0: start from the model's last accepted w */
+    double w0[PR_MAX_K];
+    int loop_mode;       /* PR_LOOP_GRAPH (on-device loop in a CUDA graph) or PR_LOOP_HOST */
+    double tumor_tol;    /* fixed-point stop, mm; default 1e-6 */
+    int tumor_max_iter;  /* default 100 */
+} pr_solve_opts;
+
+typedef struct {
+    int K;
+    double w[PR_MAX_K];     /* PCA coefficients (Eq. 1) */
+    double a, b;            /* intensity fit (Eq. 4) */
+    double J;               /* cost at (w, a, b) (Eq. 2) */
+    double grad[PR_MAX_K];  /* dJ/dw at (w, a, b) */
+    double grad_norm, grad_norm0;
+    int iters;              /* accepted steps */
+    int trials;             /* cost evaluations in line searches */
+    int backtracks;
+    int stop_reason;        /* PR_STOP_* */
+    double tumor_xyz[3];    /* mm, Section 2.3 */
+    int tumor_steps;
+} pr_result;
+
+/* Library version string (static storage). */
+const char* pr_version(void);
+
+/* Message for the last failed call on this host thread (static storage per thread). */
+const char* pr_last_error(void);
+
+/* Fill *o with the defaults listed in pr_solve_opts. */
+void pr_default_opts(pr_solve_opts* o);
+
+/* Create a context on CUDA device `device`. `stream` is a cudaStream_t to run
+ * on, or NULL to let the library create one. `hbm_budget_bytes` caps the
+ * device memory of all loaded models (0 = 80% of the device memory free at
+ * creation). Ownership of *out passes to the caller; release with pr_destroy. */
+int pr_create(pr_ctx** out, int device, void* stream, size_t hbm_budget_bytes);
+
+/* Free every model and buffer of the context; waits for its stream first. */
+void pr_destroy(pr_ctx* ctx);
+
+/* Section 2.1, Eq. 1: load one patient's motion model and scan geometry.
+ * f0 [nz][ny][nx] reference volume (1/mm), mean_dvf [3][nz][ny][nx] (mm),
+ * U [K][3][nz][ny][nx] eigenvector fields, 1 <= K <= PR_MAX_K, all float32 at
+ * `location`. `storage` selects the device copy of f0 and U (PR_F32 or
+ * PR_BF16, round-to-nearest-even; the mean stays float32). tumor_ref_xyz is the
+ * tumor centre in the reference image (mm), used by Section 2.3. The data are
+ * copied into resident, immutable device buffers; the model's warm-start w is
+ * set to 0. Returns PR_EADMIT if the model would exceed the HBM budget.
+ * *model_id receives a handle. */
+int pr_load_model(pr_ctx* ctx, const pr_volume_desc* vol, const pr_geometry* geom, int location,
+                  const float* f0, const float* mean_dvf, const float* U, int K, int storage,
+                  const double tumor_ref_xyz[3], int* model_id);
+
+/* Release a model and its device buffers. */
+int pr_release_model(pr_ctx* ctx, int model_id);
+
+/* Device bytes held by a model (data, workspace, graph buffers). */
+int pr_model_footprint(pr_ctx* ctx, int model_id, size_t* bytes);
+
+/* Section 2.2 + 2.3: reconstruct from one projection y [nv][nu] (float32 at
+ * y_location) at gantry angle `angle_rad`. opts NULL = defaults. Warm start:
+ * unless opts->cold_start, w starts at the model's last accepted w, and the
+ * final w becomes the next warm start (the paper initialises each frame from
+ * the previous one, Section 4). volume_out (nullable, host) receives the
+ * reconstructed image f [nz][ny][nx]. Synchronous. Errors: PR_EINVAL,
+ * PR_ENOMODEL, PR_ECUDA. A solve that stops on a failed line search or a
+ * non-finite value still returns PR_OK with out->stop_reason telling why. */
+int pr_reconstruct(pr_ctx* ctx, int model_id, const float* y, int y_location, double angle_rad,
+                   const pr_solve_opts* opts, pr_result* out, float* volume_out);
+
+/* As pr_reconstruct with a device-resident y, but only enqueues the solve on
+ * the context stream and returns. y_dev is read by the enqueued work, so it
+ * must stay valid and unchanged until pr_fetch_result returns. Fetch the
+ * result with pr_fetch_result. */
+int pr_reconstruct_async(pr_ctx* ctx, int model_id, const float* y_dev, double angle_rad,
+                         const pr_solve_opts* opts);
+
+/* Wait for the model's last enqueued solve and copy its result to *out. */
+int pr_fetch_result(pr_ctx* ctx, int model_id, pr_result* out);
+
+/* Read / overwrite a model's warm-start coefficients (K doubles, host). */
+int pr_get_state(pr_ctx* ctx, int model_id, double* w);
+int pr_set_state(pr_ctx* ctx, int model_id, const double* w);
+
+/* Eq. 1 + Section 2.2 warp at coefficients w (K doubles, host):
+ * f_dev [nz][ny][nx] (device, nullable) receives f(v) = f0(v + x(v));
+ * h_dev [K][nz][ny][nx] (device, nullable) receives h_k = (df/dx) . u_k, the
+ * exact derivative of the trilinear interpolant. Synchronous. */
+int pr_warp(pr_ctx* ctx, int model_id, const double* w, float* f_dev, float* h_dev);
+
+/* Eq. 2's projection matrix P applied to a caller volume f_dev [nz][ny][nx]
+ * (device) on the grid `vol`, with geometry `geom` at `angle_rad`: p_dev
+ * [nv][nu] (device). Synchronous. */
+int pr_project(pr_ctx* ctx, const pr_volume_desc* vol, const pr_geometry* geom, double angle_rad,
+               const float* f_dev, float* p_dev);
+
+/* P^T (the transpose of pr_project, needed by the gradient formula after
+ * Eq. 4) applied to r_dev [nv][nu] (device) by a voxel-driven gather:
+ * g_dev [nz][ny][nx] (device). Synchronous. */
+int pr_backproject(pr_ctx* ctx, const pr_volume_desc* vol, const pr_geometry* geom,
+                   double angle_rad, const float* r_dev, float* g_dev);
+
+/* Forward model for autograd: p_dev [nv][nu] (device) = P f(mean + U w), w
+ * K doubles (host). Synchronous. */
+int pr_forward(pr_ctx* ctx, int model_id, const double* w, double angle_rad, float* p_dev);
+
+/* Vector-Jacobian product of pr_forward: grad_w[k] = sum over pixels of
+ * grad_p * d p / d w_k = sum over voxels of (P^T grad_p)(v) h_k(v), computed
+ * with the gather adjoint (the per-voxel P^T is never stored). grad_p_dev
+ * [nv][nu] (device), grad_w K doubles (host). Synchronous. */
+int pr_vjp(pr_ctx* ctx, int model_id, const double* w, double angle_rad, const float* grad_p_dev,
+           double* grad_w);
+
+/* One cost/gradient evaluation, the per-step quantity of Section 2.2: for
+ * coefficients w and intensity terms (a, b), with y_dev [nv][nu] (device):
+ * *J = ||P f - a y - b||^2 and grad[k] = dJ/dw_k = 2 sum_v (P^T r)(v) h_k(v),
+ * r = P f - a y - b. mode 0 computes it in forward mode (sum over pixels of
+ * 2 r (P h_k), the same number), mode 1 with the gather adjoint. p_dev
+ * (device, nullable) receives P f. Synchronous. */
+int pr_cost_grad(pr_ctx* ctx, int model_id, const float* y_dev, double angle_rad, const double* w,
+                 double a, double b, int mode, double* J, double* grad, float* p_dev);
+
+/* Section 2.3: tumor position for coefficients w (host, K doubles): the
+ * fixed point p = c0 - x(p) of the pull-back DVF x = mean + U w (trilinear,
+ * clamped to the grid edge), from p = c0, stopping when a step is below tol mm
+ * or after max_iter steps. xyz (host) receives p, *steps the step count. */
+int pr_tumor(pr_ctx* ctx, int model_id, const double* w, double tol, int max_iter, double* xyz,
+             int* steps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCARECON_H */

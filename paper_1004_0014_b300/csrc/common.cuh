@@ -1,0 +1,271 @@
+// Shared device-side definitions of the pcarecon CUDA library: grid and ray
+// geometry, the on-device solver state, sample-position arithmetic shared by
+// the projector and its gather transpose, deterministic block reductions and
+// a launcher that either launches on a stream or records a CUDA-graph node.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <utility>
+
+namespace pr {
+
+constexpr int kMaxK = 7;
+constexpr int kMaxMom = 12;  // doubles per block partial row
+
+// Voxel grid of a model. Device volumes are stored with a one-voxel zero border
+// ("padded"): element (i, j, k), -1 <= i <= nx, sits at
+// ((k + 1) * nyp + (j + 1)) * nxp + (i + 1), so every trilinear tap of a point
+// clamped into the index box [-1, n] is in bounds and the border supplies the
+// zero value of the interpolant outside the grid.
+struct VolDev {
+    int nx, ny, nz;
+    int nxp, nyp, nzp;  // n + 2
+    float dx, dy, dz;
+    float inv_dx, inv_dy, inv_dz;
+    long long n;   // voxels
+    long long np;  // padded voxels
+};
+
+// Ray geometry of one gantry angle, in float. Directions are built per pixel as
+// d00 + iu * eu + iv * ev (world mm, from the source to the pixel centre),
+// normalised, then scaled to index units by inv_sp; `a` is the source in
+// index coordinates ((S - origin) / spacing).
+struct RayGeom {
+    float a[3];
+    float d00[3];
+    float eu[3];
+    float ev[3];
+    float inv_sp[3];
+    float nmax[3];  // nx, ny, nz as float: the interpolant's support is (-1, n)
+    float ds;       // sample step, mm
+    int nu, nv;
+    // For voxel footprints (gather transpose): a world point P lands on the
+    // continuous pixel coordinate (lam (P - S).pu + cu, lam (P - S).pv + cv) with
+    // lam = sdd / ((P - S).ehat).
+    float src[3];     // source, world mm
+    float ehat[3];    // unit central-ray direction
+    float pu[3], pv[3];  // eu / |eu|^2, ev / |ev|^2
+    float cu, cv;     // (nu - 1) / 2, (nv - 1) / 2
+    float sdd;
+    float origin[3];  // world position of voxel (0, 0, 0)
+    float sp[3];      // voxel spacing, mm
+};
+
+// Solver phases handled by the controller in the last block of a reduction.
+enum Phase : int {
+    kPhaseNone = 0,   // plain projection, no reduction
+    kPhaseInit = 1,   // first projection at w0: (a, b) by Eq. 4
+    kPhaseTrial = 2,  // line-search trial: Armijo test, then Eq. 4 on acceptance
+};
+
+// Per-solve parameters (written by the host before each solve).
+struct SolveParams {
+    RayGeom rg;
+    double w0[8];
+    double c1, beta, grad_tol, step0, tumor_tol;
+    int max_iters, max_bt, tumor_max_iter, K;
+    int cold_start;  // 1: start from w0; 0: from the state's last accepted w
+    int pad_;
+};
+
+// On-device state of one solve (FP64 scalars; Section 2.2's alternation).
+struct SolveState {
+    SolveParams prm;
+    double w[8];   // accepted coefficients
+    double wt[8];  // coefficients being evaluated (trial)
+    double g[8];   // dJ/dw at (w, a, b)
+    double a, b, J, Jt, mu, mu_prev, gnorm, gnorm0;
+    double sy, syy, R;
+    int iter, bt, trials, total_bt, stop, accepted, need_grad, running;
+    double tumor[3];
+    int tumor_steps, pad_;
+};
+
+// ---------------------------------------------------------------------------
+// Sample positions: one definition for the projector and its transpose, so the
+// two see bitwise-identical points.
+// ---------------------------------------------------------------------------
+
+// Unit direction of the ray to pixel (iu, iv), in index units per mm.
+__device__ __forceinline__ void ray_dir_index(const RayGeom& g, int iu, int iv, float b[3]) {
+    float fu = (float)iu, fv = (float)iv;
+    float d0 = __fmaf_rn(fv, g.ev[0], __fmaf_rn(fu, g.eu[0], g.d00[0]));
+    float d1 = __fmaf_rn(fv, g.ev[1], __fmaf_rn(fu, g.eu[1], g.d00[1]));
+    float d2 = __fmaf_rn(fv, g.ev[2], __fmaf_rn(fu, g.eu[2], g.d00[2]));
+    float inv = rsqrtf(__fmaf_rn(d0, d0, __fmaf_rn(d1, d1, __fmul_rn(d2, d2))));
+    b[0] = __fmul_rn(__fmul_rn(d0, inv), g.inv_sp[0]);
+    b[1] = __fmul_rn(__fmul_rn(d1, inv), g.inv_sp[1]);
+    b[2] = __fmul_rn(__fmul_rn(d2, inv), g.inv_sp[2]);
+}
+
+// Index-space position of sample s of a ray: a + (s + 1/2) ds b.
+__device__ __forceinline__ void sample_pos(const RayGeom& g, const float b[3], int s, float q[3]) {
+    float t = __fmul_rn((float)s + 0.5f, g.ds);
+    q[0] = __fmaf_rn(t, b[0], g.a[0]);
+    q[1] = __fmaf_rn(t, b[1], g.a[1]);
+    q[2] = __fmaf_rn(t, b[2], g.a[2]);
+}
+
+// Ray parameter interval (mm) inside the index box [lo_c, hi_c] per axis.
+// Returns false when the ray misses it.
+__device__ __forceinline__ bool ray_box(const float a[3], const float b[3], const float lo[3],
+                                        const float hi[3], float& t0, float& t1) {
+    t0 = 0.0f;
+    t1 = 3.0e38f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (b[c] != 0.0f) {
+            float inv = 1.0f / b[c];
+            float ta = (lo[c] - a[c]) * inv, tb = (hi[c] - a[c]) * inv;
+            t0 = fmaxf(t0, fminf(ta, tb));
+            t1 = fminf(t1, fmaxf(ta, tb));
+        } else if (!(a[c] > lo[c] && a[c] < hi[c])) {
+            return false;
+        }
+    }
+    return t1 > t0;
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic reductions
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum NV doubles over the block (blockDim.x a multiple of 32, <= 1024) in a
+// fixed order; thread 0 gets the totals in v.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+    __shared__ double sh[32][NV];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int m = 0; m < NV; ++m) v[m] = warp_sum(v[m]);
+    if (lane == 0)
+#pragma unroll
+        for (int m = 0; m < NV; ++m) sh[wid][m] = v[m];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int m = 0; m < NV; ++m) {
+            double x = lane < nw ? sh[lane][m] : 0.0;
+            v[m] = warp_sum(x);
+        }
+    }
+    __syncthreads();
+}
+
+// Write this block's NV partial sums (thread 0 holds them), then report whether
+// this block is the last of `nblocks` to finish. The last block may then read
+// every row with ldcg and must reset *counter to 0.
+template <int NV>
+__device__ __forceinline__ bool publish_partials(const double (&v)[NV], double* partials, int block,
+                                                 int nblocks, unsigned int* counter) {
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int m = 0; m < NV; ++m) partials[(size_t)block * kMaxMom + m] = v[m];
+        __threadfence();
+        unsigned int prev = atomicAdd(counter, 1u);
+        s_last = (prev == (unsigned int)(nblocks - 1));
+    }
+    __syncthreads();
+    bool last = s_last != 0;
+    if (last) __threadfence();
+    return last;
+}
+
+// In the last block: total of NV partial rows over nblocks, fixed order.
+template <int NV>
+__device__ __forceinline__ void total_partials(const double* partials, int nblocks, double (&tot)[NV]) {
+#pragma unroll
+    for (int m = 0; m < NV; ++m) tot[m] = 0.0;
+    for (int r = threadIdx.x; r < nblocks; r += blockDim.x)
+#pragma unroll
+        for (int m = 0; m < NV; ++m) tot[m] += __ldcg(partials + (size_t)r * kMaxMom + m);
+    block_sum<NV>(tot);
+}
+
+__device__ __forceinline__ void set_loop(SolveState* st, int run, cudaGraphConditionalHandle h,
+                                         int use_graph) {
+    st->running = run;
+    if (use_graph) cudaGraphSetConditional(h, run ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------
+// Storage types
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float ld_val(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ld_val(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+    float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const __nv_bfloat16* p, float (&v)[4]) {
+    uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
+    __nv_bfloat162 lo = *reinterpret_cast<__nv_bfloat162*>(&t.x);
+    __nv_bfloat162 hi = *reinterpret_cast<__nv_bfloat162*>(&t.y);
+    float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+}
+
+}  // namespace pr
+
+// ---------------------------------------------------------------------------
+// Host: launch on a stream, or append a kernel node to a graph chain.
+// ---------------------------------------------------------------------------
+namespace pr {
+
+struct Launcher {
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphNode_t last{};
+    bool has_last = false;
+    int count = 0;  // kernels launched or recorded
+
+    template <typename... KArgs, typename... Args>
+    cudaError_t operator()(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                           Args&&... args) {
+        ++count;
+        if (!graph) {
+            kern<<<grid, block, smem, stream>>>(std::forward<Args>(args)...);
+            return cudaGetLastError();
+        }
+        return node(kern, grid, block, smem, static_cast<KArgs>(args)...);
+    }
+
+    template <typename... KArgs>
+    cudaError_t node(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, KArgs... args) {
+        void* ptrs[] = {(void*)&args...};
+        cudaKernelNodeParams p = {};
+        p.func = (void*)kern;
+        p.gridDim = grid;
+        p.blockDim = block;
+        p.sharedMemBytes = (unsigned)smem;
+        p.kernelParams = ptrs;
+        p.extra = nullptr;
+        cudaGraphNode_t n;
+        cudaError_t e = cudaGraphAddKernelNode(&n, graph, has_last ? &last : nullptr, has_last ? 1 : 0, &p);
+        if (e == cudaSuccess) {
+            last = n;
+            has_last = true;
+        }
+        return e;
+    }
+};
+
+}  // namespace pr

@@ -1,0 +1,87 @@
+// Internal interface between the C-ABI runtime (runtime.cu) and the kernel
+// translation units (warp.cu, project.cu, backproject.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace pr {
+
+// Device buffers of one loaded model (all owned by the runtime).
+struct ModelDev {
+    VolDev vd;
+    int K;
+    int storage;       // 0 = float32, 1 = bfloat16 (f0 and U)
+    const void* f0p;   // padded reference volume
+    const float* mean; // [3][N]
+    const void* U;     // [K][3][N]
+    double c0[3];      // tumor reference position (mm)
+};
+
+// Output selection of the warp kernel (Section 2.2's f and h_k = (df/dx) . u_k).
+enum WarpMode : int {
+    kWarpFH = 0,      // f and h interleaved into the padded solver volume
+    kWarpFPad = 1,    // f only, padded planar (for projection)
+    kWarpFlatF = 2,   // f only, unpadded [N]
+    kWarpFlatFH = 3,  // f [N] (nullable) and h [K][N] (nullable), unpadded
+};
+
+// Channels per voxel of the interleaved solver volume: f, h_1..h_K, rounded up to 4 or 8.
+inline int fh_channels(int K) { return K <= 3 ? 4 : 8; }
+
+// G1: x = mean + U w (Eq. 1), f(v) = F0(v + x(v)), h_k(v) (Section 2.2).
+// w_dev: K doubles in device memory.
+cudaError_t launch_warp(Launcher& L, const ModelDev& m, const double* w_dev, int mode, float* out_pad,
+                        float* f_flat, float* h_flat);
+
+// Round float32 to bfloat16 (round-to-nearest-even), n elements.
+cudaError_t launch_to_bf16(Launcher& L, const float* src, __nv_bfloat16* dst, long long n);
+
+// Copy an unpadded volume into a padded one (border must already be zero).
+cudaError_t launch_pad(Launcher& L, const VolDev& vd, const float* src, float* dst_pad);
+
+// y moments and solve initialisation (first kernel of a solve).
+cudaError_t launch_begin(Launcher& L, const float* y, int R, SolveState* st, double* partials,
+                         unsigned int* counter);
+
+// G2: cone-beam projection of a padded volume with `nch` channels per voxel
+// (1 = planar f, 4 or 8 = interleaved f, h). rg: device RayGeom. p: [R];
+// q: [K][R] (channels 1..K, nullable). For phase != kPhaseNone, y, st,
+// partials and counter drive the fused reduction and the controller.
+cudaError_t launch_project(Launcher& L, const VolDev& vd, const float* vol_pad, int nch, int K,
+                           const RayGeom* rg, int nu, int nv, float* p, float* q, const float* y,
+                           SolveState* st, double* partials, unsigned int* counter, int phase,
+                           cudaGraphConditionalHandle h, int use_graph);
+
+// Residual, cost and gradient from stored p and q at the state's (a, b); then
+// the stop test and the next trial step (runs only when the state asks).
+cudaError_t launch_regrad(Launcher& L, const float* p, const float* q, const float* y, int R, int K,
+                          SolveState* st, double* partials, unsigned int* counter,
+                          cudaGraphConditionalHandle h, int use_graph);
+
+// Generic cost / gradient for explicit (w, a, b) from stored p, q: out[0] = J,
+// out[1 + k] = 2 sum r q_k.
+cudaError_t launch_cost_grad(Launcher& L, const float* p, const float* q, const float* y, int R, int K,
+                             const double* ab_dev, double* partials, unsigned int* counter,
+                             double* out);
+
+// Section 2.3 tumor fixed point at w (device doubles) into xyz_out / steps_out.
+// prm (nullable): take tol and max_iter from these per-solve parameters instead.
+cudaError_t launch_tumor(Launcher& L, const ModelDev& m, const double* w_dev, double tol, int max_iter,
+                         const SolveParams* prm, double* xyz_out, int* steps_out);
+
+// r = p - a y - b with (a, b) = ab_dev[0..1].
+cudaError_t launch_residual(Launcher& L, const float* p, const float* y, int R, const double* ab_dev, float* r);
+
+// P^T by voxel-driven gather. With h (K planes, unpadded) given, the per-voxel
+// values are never stored: out[k] = sum_v (P^T r)(v) h_k(v) (and g_flat may be
+// null); otherwise g_flat [N] receives P^T r.
+cudaError_t launch_backproject(Launcher& L, const VolDev& vd, const RayGeom* rg, const float* r,
+                               float* g_flat, const float* h, int K, double* partials,
+                               unsigned int* counter, double* out);
+
+// Number of blocks the reductions use (size of the partials buffer rows).
+int project_blocks(int nu, int nv);
+int reduce_blocks();
+int backproject_blocks(const VolDev& vd);
+
+}  // namespace pr

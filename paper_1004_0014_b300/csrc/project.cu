@@ -1,0 +1,488 @@
+// G2: cone-beam ray-march projector (Eq. 2's projection matrix P) with the
+// fused residual/moment epilogue, and the on-device controller of Section
+// 2.2's alternation: Eq. 4 for (a, b), Armijo's rule for the step of Eq. 3,
+// and the stopping rule. Also the y-moment / initialisation kernel, the
+// residual-gradient kernel, and the Section 2.3 tumor fixed point.
+//
+// Projector layout: one thread per ray; a warp owns an 8 x 4 patch of
+// detector pixels and a block of 256 threads a 32 x 8 tile, so the 32 samples
+// a warp takes at one step lie within about one voxel of each other and the
+// eight trilinear taps of the warp hit a handful of cache lines. All lanes of
+// a warp march the union of their sample ranges; a point outside the
+// interpolant's support is clamped onto the zero border of the padded volume
+// and adds exactly zero, so the loop has no divergent exits.
+#include <math.h>
+
+#include "internal.h"
+
+namespace pr {
+namespace {
+
+constexpr int kTileU = 32, kTileV = 8, kProjThreads = kTileU * kTileV;
+constexpr int kReduceThreads = 256;
+constexpr int kReduceBlocks = 296;  // 2 per SM on a 148-SM B300
+constexpr int kMaxSamples = 1 << 22;  // samples per ray, far above any real geometry
+
+// ---------------------------------------------------------------------------
+// Controller pieces (thread 0 of the last block; FP64)
+// ---------------------------------------------------------------------------
+
+// Eq. 4: (a, b) = (Y^T Y)^-1 Y^T p with Y = [y, 1].
+__device__ bool fit_ab(const SolveState* st, double sp, double spy, double* a, double* b) {
+    double det = st->syy * st->R - st->sy * st->sy;
+    if (!(det > 1e-12 * st->syy * st->R)) return false;
+    *a = (st->R * spy - st->sy * sp) / det;
+    *b = (st->syy * sp - st->sy * spy) / det;
+    return isfinite(*a) && isfinite(*b);
+}
+
+__device__ void next_trial(SolveState* st, int K) {
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k)
+        if (k < K) st->wt[k] = st->w[k] - st->mu * st->g[k];
+}
+
+// ---------------------------------------------------------------------------
+// Solve initialisation: y moments, finiteness of y, reset of the state.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kReduceThreads)
+k_begin(const float* __restrict__ y, int R, SolveState* st, double* partials, unsigned int* counter) {
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
+        float yv = y[r];
+        if (isfinite(yv)) {
+            v[0] += yv;
+            v[1] += (double)yv * yv;
+        } else {
+            v[2] += 1.0;
+        }
+    }
+    block_sum<3>(v);
+    if (!publish_partials<3>(v, partials, blockIdx.x, gridDim.x, counter)) return;
+    double tot[3];
+    total_partials<3>(partials, gridDim.x, tot);
+    if (threadIdx.x == 0) {
+        *counter = 0;
+        const int K = st->prm.K;
+        st->sy = tot[0];
+        st->syy = tot[1];
+        st->R = (double)R;
+        for (int k = 0; k < kMaxK; ++k) {
+            double w0 = k < K ? (st->prm.cold_start ? st->prm.w0[k] : st->w[k]) : 0.0;
+            st->w[k] = w0;
+            st->wt[k] = w0;
+            st->g[k] = 0.0;
+        }
+        st->a = 1.0;
+        st->b = 0.0;
+        st->J = st->Jt = 0.0;
+        st->mu = st->mu_prev = 0.0;
+        st->gnorm = st->gnorm0 = 0.0;
+        st->iter = st->bt = st->trials = st->total_bt = 0;
+        st->stop = tot[2] > 0.0 ? 4 : 0;  // PR_STOP_NONFINITE
+        st->accepted = 0;
+        st->need_grad = 0;
+        st->running = 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// G2 projector
+// ---------------------------------------------------------------------------
+
+// Trilinear accumulation of one sample into acc[0..NCH).
+template <int NCH>
+__device__ __forceinline__ void accumulate(const float* __restrict__ vol, const VolDev& vd, const float q[3],
+                                           float (&acc)[NCH]) {
+    float qx = fminf(fmaxf(q[0], -1.0f), (float)vd.nx);
+    float qy = fminf(fmaxf(q[1], -1.0f), (float)vd.ny);
+    float qz = fminf(fmaxf(q[2], -1.0f), (float)vd.nz);
+    int ix = min((int)floorf(qx), vd.nx - 1);
+    int iy = min((int)floorf(qy), vd.ny - 1);
+    int iz = min((int)floorf(qz), vd.nz - 1);
+    float tx = qx - (float)ix, ty = qy - (float)iy, tz = qz - (float)iz;
+    long long base = ((long long)(iz + 1) * vd.nyp + (iy + 1)) * vd.nxp + (ix + 1);
+    const long long plane = (long long)vd.nxp * vd.nyp;
+    float wx0 = 1.0f - tx, wy0 = 1.0f - ty, wz0 = 1.0f - tz;
+    float w00 = wy0 * wz0, w10 = ty * wz0, w01 = wy0 * tz, w11 = ty * tz;
+    const long long off[4] = {0, (long long)vd.nxp, plane, plane + vd.nxp};
+    const float wyz[4] = {w00, w10, w01, w11};
+    if (NCH == 1) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float* p = vol + base + off[c];
+            float a0 = __ldg(p), a1 = __ldg(p + 1);
+            acc[0] = __fmaf_rn(wyz[c], __fmaf_rn(tx, a1 - a0, a0), acc[0]);
+        }
+    } else {
+        constexpr int NV4 = NCH / 4;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float4* p = reinterpret_cast<const float4*>(vol + (base + off[c]) * NCH);
+            float w0 = wyz[c] * wx0, w1 = wyz[c] * tx;
+#pragma unroll
+            for (int h = 0; h < NV4; ++h) {
+                float4 a0 = __ldg(p + h), a1 = __ldg(p + NV4 + h);
+                acc[4 * h + 0] = __fmaf_rn(w1, a1.x, __fmaf_rn(w0, a0.x, acc[4 * h + 0]));
+                acc[4 * h + 1] = __fmaf_rn(w1, a1.y, __fmaf_rn(w0, a0.y, acc[4 * h + 1]));
+                acc[4 * h + 2] = __fmaf_rn(w1, a1.z, __fmaf_rn(w0, a0.z, acc[4 * h + 2]));
+                acc[4 * h + 3] = __fmaf_rn(w1, a1.w, __fmaf_rn(w0, a0.w, acc[4 * h + 3]));
+            }
+        }
+    }
+}
+
+struct ProjArgs {
+    const float* vol;
+    VolDev vd;
+    const RayGeom* rg;
+    int nu, nv, K;
+    float* p;
+    float* q;
+    const float* y;
+    SolveState* st;
+    double* partials;
+    unsigned int* counter;
+    int phase;
+    cudaGraphConditionalHandle h;
+    int use_graph;
+};
+
+__device__ void controller_project(SolveState* st, const double (&tot)[3], int phase,
+                                   cudaGraphConditionalHandle h, int use_graph) {
+    const int K = st->prm.K;
+    double a, b;
+    if (phase == kPhaseInit) {
+        if (st->stop == 0 && !fit_ab(st, tot[1], tot[2], &a, &b)) st->stop = 5;  // singular fit
+        if (st->stop == 0) {
+            st->a = a;
+            st->b = b;
+        }
+        st->need_grad = 1;  // the residual kernel computes J, g and decides whether to run
+        return;
+    }
+    // kPhaseTrial: Armijo's sufficient-decrease test at fixed (a, b) (Section 2.2).
+    if (st->stop != 0) {
+        st->need_grad = 0;
+        set_loop(st, 0, h, use_graph);
+        return;
+    }
+    st->trials += 1;
+    if (st->trials > (st->prm.max_iters + 1) * (st->prm.max_bt + 1) + 1) {
+        st->stop = 6;  // internal guard: more trials than the options allow
+        st->need_grad = 0;
+        set_loop(st, 0, h, use_graph);
+        return;
+    }
+    double Jt = tot[0];
+    st->Jt = Jt;
+    bool ok = isfinite(Jt) && Jt <= st->J - st->prm.c1 * st->mu * st->gnorm * st->gnorm;
+    if (ok) {
+        for (int k = 0; k < kMaxK; ++k)
+            if (k < K) st->w[k] = st->wt[k];
+        st->mu_prev = st->mu;
+        st->iter += 1;
+        st->accepted = 1;
+        if (fit_ab(st, tot[1], tot[2], &a, &b)) {  // step 2, Eq. 4
+            st->a = a;
+            st->b = b;
+        } else {
+            st->stop = 5;
+        }
+        st->need_grad = 1;
+        return;
+    }
+    st->accepted = 0;
+    st->need_grad = 0;
+    st->bt += 1;
+    st->total_bt += 1;
+    if (st->bt > st->prm.max_bt) {
+        st->stop = 3;  // PR_STOP_LINESEARCH_FAILED: w keeps its last accepted value
+        set_loop(st, 0, h, use_graph);
+        return;
+    }
+    st->mu *= st->prm.beta;
+    next_trial(st, K);
+}
+
+template <int NCH>
+__global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs A) {
+    const RayGeom g = *A.rg;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int iu = blockIdx.x * kTileU + (wid & 3) * 8 + (lane & 7);
+    const int iv = blockIdx.y * kTileV + (wid >> 2) * 4 + (lane >> 3);
+    const bool valid = iu < A.nu && iv < A.nv;
+
+    float b[3];
+    ray_dir_index(g, valid ? iu : 0, valid ? iv : 0, b);
+    const float lo[3] = {-1.0f, -1.0f, -1.0f};
+    float t0, t1;
+    int s_lo = 0x7fffffff, s_hi = -1;
+    if (valid && ray_box(g.a, b, lo, g.nmax, t0, t1)) {
+        // t0, t1 are bounded by the box; the clamps only keep the int
+        // conversion and the loop counter far from overflow.
+        s_lo = (int)fminf(fmaxf(ceilf(t0 / g.ds - 0.5f), 0.0f), (float)kMaxSamples);
+        s_hi = (int)fminf(floorf(t1 / g.ds - 0.5f), (float)kMaxSamples);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s_lo = min(s_lo, __shfl_xor_sync(0xffffffffu, s_lo, o));
+        s_hi = max(s_hi, __shfl_xor_sync(0xffffffffu, s_hi, o));
+    }
+    float acc[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) acc[c] = 0.0f;
+    for (int s = s_lo; s <= s_hi; ++s) {
+        float q[3];
+        sample_pos(g, b, s, q);
+        accumulate<NCH>(A.vol, A.vd, q, acc);
+    }
+
+    const int R = A.nu * A.nv;
+    const int r = iv * A.nu + iu;
+    float pv = acc[0] * g.ds;
+    if (valid) {
+        A.p[r] = pv;
+        if (NCH > 1 && A.q)
+            for (int k = 0; k < A.K; ++k) A.q[(long long)k * R + r] = acc[1 + (k < NCH - 1 ? k : 0)] * g.ds;
+    }
+    if (A.phase == kPhaseNone) return;
+
+    // Epilogue: J_trial = sum (p - a y - b)^2, sum p, sum p y (FP64 from here on).
+    double v[3] = {0.0, 0.0, 0.0};
+    if (valid) {
+        double yv = A.y[r];
+        double res = (double)pv - A.st->a * yv - A.st->b;
+        v[0] = res * res;
+        v[1] = pv;
+        v[2] = (double)pv * yv;
+    }
+    block_sum<3>(v);
+    const int nblocks = gridDim.x * gridDim.y;
+    if (!publish_partials<3>(v, A.partials, blockIdx.y * gridDim.x + blockIdx.x, nblocks, A.counter)) return;
+    double tot[3];
+    total_partials<3>(A.partials, nblocks, tot);
+    if (threadIdx.x == 0) {
+        *A.counter = 0;
+        controller_project(A.st, tot, A.phase, A.h, A.use_graph);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Residual, cost and gradient from stored p, q (forward-mode form of the
+// gradient formula after Eq. 4: dJ/dw_k = 2 sum_rays r (P h_k)), then the stop
+// test and the next trial step.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kReduceThreads)
+k_regrad(const float* __restrict__ p, const float* __restrict__ q, const float* __restrict__ y, int R, int K,
+         SolveState* st, double* partials, unsigned int* counter, cudaGraphConditionalHandle h,
+         int use_graph) {
+    if (!st->need_grad) return;
+    const double a = st->a, b = st->b;
+    double v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = 0.0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
+        double res = (double)p[r] - a * (double)y[r] - b;
+        v[0] += res * res;
+#pragma unroll
+        for (int k = 0; k < kMaxK; ++k)
+            if (k < K) v[1 + k] += res * (double)q[(long long)k * R + r];
+    }
+    block_sum<8>(v);
+    if (!publish_partials<8>(v, partials, blockIdx.x, gridDim.x, counter)) return;
+    double tot[8];
+    total_partials<8>(partials, gridDim.x, tot);
+    if (threadIdx.x != 0) return;
+    *counter = 0;
+    st->need_grad = 0;
+    st->J = tot[0];
+    double gn2 = 0.0;
+    for (int k = 0; k < kMaxK; ++k) {
+        double gk = k < K ? 2.0 * tot[1 + k] : 0.0;
+        st->g[k] = gk;
+        gn2 += gk * gk;
+    }
+    double gn = sqrt(gn2);
+    st->gnorm = gn;
+    if (st->iter == 0) st->gnorm0 = gn;
+    if (st->stop != 0) {
+        set_loop(st, 0, h, use_graph);
+        return;
+    }
+    if (!isfinite(st->J) || !isfinite(gn)) {
+        st->stop = 4;
+        set_loop(st, 0, h, use_graph);
+        return;
+    }
+    if (gn <= st->prm.grad_tol * st->gnorm0 || gn == 0.0) {
+        st->stop = 1;  // PR_STOP_GRAD_TOL
+        set_loop(st, 0, h, use_graph);
+        return;
+    }
+    if (st->iter >= st->prm.max_iters) {
+        st->stop = 2;  // PR_STOP_MAX_ITERS
+        set_loop(st, 0, h, use_graph);
+        return;
+    }
+    st->mu = st->iter == 0 ? st->prm.step0 / gn : 2.0 * st->mu_prev;
+    st->bt = 0;
+    next_trial(st, K);
+    set_loop(st, 1, h, use_graph);
+}
+
+// Cost and gradient at explicit (a, b) (ab_dev[0..1]) for the step-level entry.
+__global__ void __launch_bounds__(kReduceThreads)
+k_cost_grad(const float* __restrict__ p, const float* __restrict__ q, const float* __restrict__ y, int R, int K,
+            const double* ab, double* partials, unsigned int* counter, double* out) {
+    const double a = ab[0], b = ab[1];
+    double v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = 0.0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
+        double res = (double)p[r] - a * (double)y[r] - b;
+        v[0] += res * res;
+        if (q)
+#pragma unroll
+            for (int k = 0; k < kMaxK; ++k)
+                if (k < K) v[1 + k] += res * (double)q[(long long)k * R + r];
+    }
+    block_sum<8>(v);
+    if (!publish_partials<8>(v, partials, blockIdx.x, gridDim.x, counter)) return;
+    double tot[8];
+    total_partials<8>(partials, gridDim.x, tot);
+    if (threadIdx.x != 0) return;
+    *counter = 0;
+    out[0] = tot[0];
+    for (int k = 0; k < K; ++k) out[1 + k] = 2.0 * tot[1 + k];
+}
+
+// ---------------------------------------------------------------------------
+// Section 2.3: tumor position by the fixed-point inversion of the pull-back
+// DVF (Chen et al.), evaluated at the single point c0: p <- c0 - x(p), with x
+// = mean + U w trilinearly interpolated and clamped to the grid edge. FP64.
+// ---------------------------------------------------------------------------
+template <typename TS>
+__device__ void dvf_at(const float* mean, const TS* U, const VolDev& vd, int K, const double* w,
+                       const double p[3], double out[3]) {
+    const double sp[3] = {(double)vd.dx, (double)vd.dy, (double)vd.dz};
+    const int nn[3] = {vd.nx, vd.ny, vd.nz};
+    int i0[3];
+    double t[3];
+    for (int c = 0; c < 3; ++c) {
+        double o = -0.5 * (nn[c] - 1) * sp[c];
+        double q = (p[c] - o) / sp[c];
+        q = fmin(fmax(q, 0.0), (double)(nn[c] - 1));
+        int i = (int)floor(q);
+        i = max(0, min(i, nn[c] - 2));
+        i0[c] = i;
+        t[c] = q - i;
+    }
+    for (int comp = 0; comp < 3; ++comp) {
+        double acc = 0.0;
+        for (int cz = 0; cz < 2; ++cz)
+            for (int cy = 0; cy < 2; ++cy)
+                for (int cx = 0; cx < 2; ++cx) {
+                    int i = i0[0] + cx, j = i0[1] + cy, k = i0[2] + cz;
+                    if (i >= vd.nx || j >= vd.ny || k >= vd.nz) continue;
+                    long long e = (long long)comp * vd.n + ((long long)k * vd.ny + j) * vd.nx + i;
+                    double xv = mean[e];
+                    for (int m = 0; m < K; ++m) xv += (double)ld_val(U + 3LL * m * vd.n + e) * w[m];
+                    double wt = (cx ? t[0] : 1.0 - t[0]) * (cy ? t[1] : 1.0 - t[1]) * (cz ? t[2] : 1.0 - t[2]);
+                    acc += wt * xv;
+                }
+        out[comp] = acc;
+    }
+}
+
+template <typename TS>
+__global__ void k_tumor(const float* mean, const TS* U, VolDev vd, int K, const double* w, double c0x,
+                        double c0y, double c0z, double tol, int max_iter, const SolveParams* prm,
+                        double* xyz, int* steps) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (prm) {  // per-solve options of an on-device solve
+        tol = prm->tumor_tol;
+        max_iter = prm->tumor_max_iter;
+    }
+    double wl[kMaxK];
+    for (int k = 0; k < kMaxK; ++k) wl[k] = k < K ? w[k] : 0.0;
+    const double c0[3] = {c0x, c0y, c0z};
+    double cur[3] = {c0x, c0y, c0z};
+    int it = 0;
+    while (it < max_iter) {
+        double x[3];
+        dvf_at<TS>(mean, U, vd, K, wl, cur, x);
+        double d2 = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            double nx = c0[c] - x[c];
+            d2 += (nx - cur[c]) * (nx - cur[c]);
+            cur[c] = nx;
+        }
+        ++it;
+        if (sqrt(d2) < tol) break;
+    }
+    xyz[0] = cur[0];
+    xyz[1] = cur[1];
+    xyz[2] = cur[2];
+    *steps = it;
+}
+
+// r = p - a y - b (ab[0] = a, ab[1] = b), the residual of Eq. 2.
+__global__ void __launch_bounds__(256) k_residual(const float* __restrict__ p, const float* __restrict__ y, int R,
+                                                  const double* ab, float* __restrict__ r) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < R) r[i] = (float)((double)p[i] - ab[0] * (double)y[i] - ab[1]);
+}
+
+}  // namespace
+
+cudaError_t launch_residual(Launcher& L, const float* p, const float* y, int R, const double* ab_dev, float* r) {
+    return L(k_residual, dim3((R + 255) / 256), dim3(256), 0, p, y, R, ab_dev, r);
+}
+
+int project_blocks(int nu, int nv) { return ((nu + kTileU - 1) / kTileU) * ((nv + kTileV - 1) / kTileV); }
+int reduce_blocks() { return kReduceBlocks; }
+
+cudaError_t launch_begin(Launcher& L, const float* y, int R, SolveState* st, double* partials,
+                         unsigned int* counter) {
+    return L(k_begin, dim3(kReduceBlocks), dim3(kReduceThreads), 0, y, R, st, partials, counter);
+}
+
+cudaError_t launch_project(Launcher& L, const VolDev& vd, const float* vol_pad, int nch, int K,
+                           const RayGeom* rg, int nu, int nv, float* p, float* q, const float* y,
+                           SolveState* st, double* partials, unsigned int* counter, int phase,
+                           cudaGraphConditionalHandle h, int use_graph) {
+    ProjArgs A{vol_pad, vd, rg, nu, nv, K, p, q, y, st, partials, counter, phase, h, use_graph};
+    dim3 grid((nu + kTileU - 1) / kTileU, (nv + kTileV - 1) / kTileV);
+    switch (nch) {
+        case 1: return L(k_project<1>, grid, dim3(kProjThreads), 0, A);
+        case 4: return L(k_project<4>, grid, dim3(kProjThreads), 0, A);
+        case 8: return L(k_project<8>, grid, dim3(kProjThreads), 0, A);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_regrad(Launcher& L, const float* p, const float* q, const float* y, int R, int K,
+                          SolveState* st, double* partials, unsigned int* counter,
+                          cudaGraphConditionalHandle h, int use_graph) {
+    return L(k_regrad, dim3(kReduceBlocks), dim3(kReduceThreads), 0, p, q, y, R, K, st, partials, counter,
+             h, use_graph);
+}
+
+cudaError_t launch_cost_grad(Launcher& L, const float* p, const float* q, const float* y, int R, int K,
+                             const double* ab_dev, double* partials, unsigned int* counter, double* out) {
+    return L(k_cost_grad, dim3(kReduceBlocks), dim3(kReduceThreads), 0, p, q, y, R, K, ab_dev, partials,
+             counter, out);
+}
+
+cudaError_t launch_tumor(Launcher& L, const ModelDev& m, const double* w_dev, double tol, int max_iter,
+                         const SolveParams* prm, double* xyz_out, int* steps_out) {
+    if (m.storage == 1)
+        return L(k_tumor<__nv_bfloat16>, dim3(1), dim3(32), 0, m.mean,
+                 static_cast<const __nv_bfloat16*>(m.U), m.vd, m.K, w_dev, m.c0[0], m.c0[1], m.c0[2], tol,
+                 max_iter, prm, xyz_out, steps_out);
+    return L(k_tumor<float>, dim3(1), dim3(32), 0, m.mean, static_cast<const float*>(m.U), m.vd, m.K, w_dev,
+             m.c0[0], m.c0[1], m.c0[2], tol, max_iter, prm, xyz_out, steps_out);
+}
+
+}  // namespace pr

@@ -1,0 +1,749 @@
+// C-ABI runtime of pcarecon: contexts, resident patient models with HBM
+// admission, the per-model CUDA graph that runs Section 2.2's whole
+// alternation on the device (a conditional WHILE node whose body is
+// warp -> project -> residual-gradient, with the Armijo and stopping
+// decisions taken in FP64 by the kernels themselves), the host-driven loop
+// used as the plain baseline, and the step-level entry points.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <string>
+
+#include "internal.h"
+#include "pcarecon.h"
+
+using namespace pr;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(PR_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                             \
+    } while (0)
+
+struct Model {
+    int id = 0;
+    pr_volume_desc vol{};
+    pr_geometry geom{};
+    int K = 0, storage = 0, nch = 4;
+    ModelDev md{};
+    int R = 0;
+    // device buffers
+    void* f0p = nullptr;
+    float* mean = nullptr;
+    void* U = nullptr;
+    float* fh = nullptr;    // padded, nch floats per voxel
+    float* fpad = nullptr;  // padded planar f
+    float* p = nullptr;     // [R]
+    float* q = nullptr;     // [K][R]
+    float* y = nullptr;     // [R]
+    float* r = nullptr;     // [R]
+    float* flat = nullptr;  // [N] scratch
+    float* hbuf = nullptr;  // [K][N] scratch (adjoint paths, allocated on first use)
+    double* partials = nullptr;
+    unsigned int* counter = nullptr;
+    SolveState* st = nullptr;
+    double* wdev = nullptr;   // 8 doubles: coefficients of step-level calls
+    double* out = nullptr;    // 16 doubles: reduction outputs; [8..9] = (a, b)
+    RayGeom* rg = nullptr;    // geometry of step-level calls
+    int* steps = nullptr;
+    SolveState* st_host = nullptr;  // pinned
+    size_t bytes = 0;
+    // graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle hloop = 0;
+    int launches_per_solve_min = 0;
+};
+
+}  // namespace
+
+struct pr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t budget = 0, used = 0;
+    int next_id = 1;
+    std::map<int, Model*> models;
+    float* pad = nullptr;  // scratch for pr_project
+    size_t pad_cap = 0;
+    RayGeom* rg = nullptr;
+};
+
+namespace {
+
+size_t pad_voxels(const pr_volume_desc& v) { return (size_t)(v.nx + 2) * (v.ny + 2) * (v.nz + 2); }
+
+bool vol_ok(const pr_volume_desc* v) {
+    return v && v->nx >= 1 && v->ny >= 1 && v->nz >= 1 && v->dx > 0 && v->dy > 0 && v->dz > 0 &&
+           (double)v->nx * v->ny * v->nz < 2.0e9 && isfinite(v->dx) && isfinite(v->dy) && isfinite(v->dz);
+}
+
+bool geom_ok(const pr_geometry* g) {
+    return g && g->nu >= 1 && g->nv >= 1 && g->du > 0 && g->dv > 0 && g->sad > 0 && g->sdd > g->sad &&
+           (double)g->nu * g->nv < 2.0e9 && isfinite(g->sad) && isfinite(g->sdd) && isfinite(g->du) &&
+           isfinite(g->dv) && isfinite(g->ds);
+}
+
+double resolved_ds(const pr_volume_desc& v, const pr_geometry& g) {
+    return g.ds > 0 ? g.ds : 0.5 * fmin(v.dx, fmin(v.dy, v.dz));
+}
+
+VolDev make_vd(const pr_volume_desc& v) {
+    VolDev d;
+    d.nx = v.nx;
+    d.ny = v.ny;
+    d.nz = v.nz;
+    d.nxp = v.nx + 2;
+    d.nyp = v.ny + 2;
+    d.nzp = v.nz + 2;
+    d.dx = (float)v.dx;
+    d.dy = (float)v.dy;
+    d.dz = (float)v.dz;
+    d.inv_dx = (float)(1.0 / v.dx);
+    d.inv_dy = (float)(1.0 / v.dy);
+    d.inv_dz = (float)(1.0 / v.dz);
+    d.n = (long long)v.nx * v.ny * v.nz;
+    d.np = (long long)pad_voxels(v);
+    return d;
+}
+
+// Ray geometry of gantry angle th (computed in FP64, stored in FP32).
+RayGeom make_rg(const pr_volume_desc& v, const pr_geometry& g, double th) {
+    RayGeom r;
+    double st = sin(th), ct = cos(th);
+    double S[3] = {g.sad * st, -g.sad * ct, 0.0};
+    double eh[3] = {-st, ct, 0.0}, uh[3] = {ct, st, 0.0}, vh[3] = {0.0, 0.0, 1.0};
+    double sp[3] = {v.dx, v.dy, v.dz};
+    int n[3] = {v.nx, v.ny, v.nz};
+    double cu = 0.5 * (g.nu - 1), cv = 0.5 * (g.nv - 1);
+    for (int c = 0; c < 3; ++c) {
+        double o = -0.5 * (n[c] - 1) * sp[c];
+        r.a[c] = (float)((S[c] - o) / sp[c]);
+        r.eu[c] = (float)(g.du * uh[c]);
+        r.ev[c] = (float)(g.dv * vh[c]);
+        r.d00[c] = (float)(g.sdd * eh[c] - cu * g.du * uh[c] - cv * g.dv * vh[c]);
+        r.inv_sp[c] = (float)(1.0 / sp[c]);
+        r.nmax[c] = (float)n[c];
+        r.src[c] = (float)S[c];
+        r.ehat[c] = (float)eh[c];
+        r.pu[c] = (float)(uh[c] / g.du);
+        r.pv[c] = (float)(vh[c] / g.dv);
+        r.origin[c] = (float)o;
+        r.sp[c] = (float)sp[c];
+    }
+    r.ds = (float)resolved_ds(v, g);
+    r.nu = g.nu;
+    r.nv = g.nv;
+    r.cu = (float)cu;
+    r.cv = (float)cv;
+    r.sdd = (float)g.sdd;
+    return r;
+}
+
+Model* find(pr_ctx* c, int id) {
+    auto it = c->models.find(id);
+    return it == c->models.end() ? nullptr : it->second;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t bytes, size_t* total) {
+    *total += bytes;
+    return cudaMalloc((void**)p, bytes);
+}
+
+void free_model(Model* m) {
+    if (!m) return;
+    if (m->exec) cudaGraphExecDestroy(m->exec);
+    if (m->graph) cudaGraphDestroy(m->graph);
+    void* bufs[] = {m->f0p, m->mean, m->U, m->fh, m->fpad, m->p, m->q, m->y, m->r, m->flat, m->hbuf,
+                    m->partials, m->counter, m->st, m->wdev, m->out, m->rg, m->steps};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (m->st_host) cudaFreeHost(m->st_host);
+    delete m;
+}
+
+size_t model_bytes(const pr_volume_desc& v, const pr_geometry& g, int K, int storage) {
+    size_t n = (size_t)v.nx * v.ny * v.nz, np = pad_voxels(v), R = (size_t)g.nu * g.nv;
+    size_t ts = storage == PR_BF16 ? 2 : 4;
+    int nch = fh_channels(K);
+    int nb = project_blocks(g.nu, g.nv);
+    int rb = reduce_blocks();
+    size_t rows = (size_t)(nb > rb ? nb : rb);
+    return np * ts + 3 * n * 4 + 3 * (size_t)K * n * ts + np * nch * 4 + np * 4 + R * 4 * (3 + K) + n * 4 +
+           rows * kMaxMom * 8 + 4096;
+}
+
+// Scratch rows for block partials: the largest grid among the reductions.
+size_t partial_rows(const Model& m) {
+    size_t a = project_blocks(m.geom.nu, m.geom.nv), b = reduce_blocks(), c = backproject_blocks(m.md.vd);
+    size_t r = a > b ? a : b;
+    return r > c ? r : c;
+}
+
+int write_params(pr_ctx* c, Model* m, double angle, const pr_solve_opts* o) {
+    SolveParams prm;
+    memset(&prm, 0, sizeof prm);
+    prm.rg = make_rg(m->vol, m->geom, angle);
+    for (int k = 0; k < 8; ++k) prm.w0[k] = (k < m->K && o->cold_start) ? o->w0[k] : 0.0;
+    prm.c1 = o->c1;
+    prm.beta = o->beta;
+    prm.grad_tol = o->grad_tol;
+    prm.step0 = o->step0_mm;
+    prm.tumor_tol = o->tumor_tol;
+    prm.max_iters = o->max_iters;
+    prm.max_bt = o->max_backtracks;
+    prm.tumor_max_iter = o->tumor_max_iter;
+    prm.K = m->K;
+    prm.cold_start = o->cold_start ? 1 : 0;
+    // Pageable source: the copy is staged before cudaMemcpyAsync returns, so
+    // back-to-back asynchronous solves cannot see a later solve's parameters.
+    CK(cudaMemcpyAsync(&m->st->prm, &prm, sizeof prm, cudaMemcpyHostToDevice, c->stream));
+    return PR_OK;
+}
+
+bool opts_ok(const pr_solve_opts* o) {
+    return o->max_iters >= 0 && o->max_iters <= 100000 && o->max_backtracks >= 0 && o->max_backtracks <= 200 &&
+           o->beta > 0 && o->beta < 1 && o->c1 >= 0 && o->c1 < 1 && o->step0_mm > 0 && o->grad_tol >= 0 &&
+           o->tumor_max_iter >= 0 && o->tumor_max_iter <= 100000 && o->tumor_tol >= 0 &&
+           (o->loop_mode == PR_LOOP_GRAPH || o->loop_mode == PR_LOOP_HOST);
+}
+
+// Section 2.2's loop as a CUDA graph: prologue (y moments, f and h at w0,
+// projection and Eq. 4, gradient), a WHILE node over line-search trials, and
+// the Section 2.3 tumor kernel.
+int build_graph(pr_ctx* c, Model* m) {
+    CK(cudaGraphCreate(&m->graph, 0));
+    CK(cudaGraphConditionalHandleCreate(&m->hloop, m->graph, 1, cudaGraphCondAssignDefault));
+    Launcher L;
+    L.graph = m->graph;
+    SolveState* st = m->st;
+    CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
+    CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
+    CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
+                      m->partials, m->counter, kPhaseInit, m->hloop, 1));
+    CK(launch_regrad(L, m->p, m->q, m->y, m->R, m->K, st, m->partials, m->counter, m->hloop, 1));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = m->hloop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cond;
+    CK(cudaGraphAddNode(&cond, m->graph, &L.last, nullptr, 1, &cp));
+    Launcher B;
+    B.graph = cp.conditional.phGraph_out[0];
+    CK(launch_warp(B, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
+    CK(launch_project(B, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
+                      m->partials, m->counter, kPhaseTrial, m->hloop, 1));
+    CK(launch_regrad(B, m->p, m->q, m->y, m->R, m->K, st, m->partials, m->counter, m->hloop, 1));
+    L.last = cond;
+    CK(launch_tumor(L, m->md, st->w, 0.0, 0, &st->prm, st->tumor, &st->tumor_steps));
+    CK(cudaGraphInstantiate(&m->exec, m->graph, 0));
+    return PR_OK;
+}
+
+// The same alternation driven from the host: one device-to-host read of the
+// loop flag per line-search trial (the plain baseline).
+int host_loop(pr_ctx* c, Model* m, int opt_max_iters, int opt_max_bt) {
+    Launcher L;
+    L.stream = c->stream;
+    SolveState* st = m->st;
+    CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
+    CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
+    CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
+                      m->partials, m->counter, kPhaseInit, 0, 0));
+    CK(launch_regrad(L, m->p, m->q, m->y, m->R, m->K, st, m->partials, m->counter, 0, 0));
+    long long guard = 0, bound = (long long)(opt_max_iters + 1) * (opt_max_bt + 1) + 2;
+    for (;;) {
+        CK(cudaMemcpyAsync(&m->st_host->running, &st->running, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (!m->st_host->running) break;
+        if (++guard > bound) return fail(PR_ETIMEOUT, "host loop exceeded its trial bound");
+        CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
+        CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->geom.nu, m->geom.nv, m->p, m->q, m->y,
+                          st, m->partials, m->counter, kPhaseTrial, 0, 0));
+        CK(launch_regrad(L, m->p, m->q, m->y, m->R, m->K, st, m->partials, m->counter, 0, 0));
+    }
+    CK(launch_tumor(L, m->md, st->w, 0.0, 0, &st->prm, st->tumor, &st->tumor_steps));
+    return PR_OK;
+}
+
+void fill_result(const Model* m, const SolveState& s, pr_result* out) {
+    memset(out, 0, sizeof *out);
+    out->K = m->K;
+    for (int k = 0; k < m->K; ++k) {
+        out->w[k] = s.w[k];
+        out->grad[k] = s.g[k];
+    }
+    out->a = s.a;
+    out->b = s.b;
+    out->J = s.J;
+    out->grad_norm = s.gnorm;
+    out->grad_norm0 = s.gnorm0;
+    out->iters = s.iter;
+    out->trials = s.trials;
+    out->backtracks = s.total_bt;
+    out->stop_reason = s.stop;
+    for (int c = 0; c < 3; ++c) out->tumor_xyz[c] = s.tumor[c];
+    out->tumor_steps = s.tumor_steps;
+}
+
+int enqueue_solve(pr_ctx* c, Model* m, double angle, const pr_solve_opts* opts) {
+    pr_solve_opts o;
+    if (opts)
+        o = *opts;
+    else
+        pr_default_opts(&o);
+    if (!opts_ok(&o)) return fail(PR_EINVAL, "invalid solve options");
+    if (!isfinite(angle)) return fail(PR_EINVAL, "angle is not finite");
+    int rc = write_params(c, m, angle, &o);
+    if (rc) return rc;
+    if (o.loop_mode == PR_LOOP_HOST) return host_loop(c, m, o.max_iters, o.max_backtracks);
+    if (!m->exec) {
+        rc = build_graph(c, m);
+        if (rc) return rc;
+    }
+    CK(cudaGraphLaunch(m->exec, c->stream));
+    return PR_OK;
+}
+
+int ensure_hbuf(Model* m) {
+    if (m->hbuf) return PR_OK;
+    CK(dalloc(&m->hbuf, (size_t)m->K * m->md.vd.n * 4, &m->bytes));
+    return PR_OK;
+}
+
+int set_w(pr_ctx* c, Model* m, const double* w) {
+    double buf[8] = {0};
+    for (int k = 0; k < m->K; ++k) {
+        if (!isfinite(w[k])) return fail(PR_EINVAL, "w[%d] is not finite", k);
+        buf[k] = w[k];
+    }
+    CK(cudaMemcpyAsync(m->wdev, buf, sizeof buf, cudaMemcpyHostToDevice, c->stream));
+    return PR_OK;
+}
+
+int set_rg(pr_ctx* c, RayGeom* dst, const pr_volume_desc& v, const pr_geometry& g, double angle) {
+    if (!isfinite(angle)) return fail(PR_EINVAL, "angle is not finite");
+    RayGeom rg = make_rg(v, g, angle);
+    CK(cudaMemcpyAsync(dst, &rg, sizeof rg, cudaMemcpyHostToDevice, c->stream));
+    return PR_OK;
+}
+
+#define TRY(x)                 \
+    do {                       \
+        int rc_ = (x);         \
+        if (rc_) return rc_;   \
+    } while (0)
+
+#define GET_MODEL(c, id, m)                                                    \
+    if (!(c)) return fail(PR_EINVAL, "null context");                          \
+    Model* m = find((c), (id));                                                \
+    if (!m) return fail(PR_ENOMODEL, "unknown model id %d", (int)(id));        \
+    CK(cudaSetDevice((c)->device))
+
+}  // namespace
+
+extern "C" {
+
+const char* pr_version(void) { return "pcarecon 0.1 (sm_103a)"; }
+
+const char* pr_last_error(void) { return g_err.c_str(); }
+
+void pr_default_opts(pr_solve_opts* o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->max_iters = 10;
+    o->grad_tol = 1e-6;
+    o->c1 = 1e-4;
+    o->beta = 0.5;
+    o->max_backtracks = 20;
+    o->step0_mm = 1.0;
+    o->cold_start = 0;
+    o->loop_mode = PR_LOOP_GRAPH;
+    o->tumor_tol = 1e-6;
+    o->tumor_max_iter = 100;
+}
+
+int pr_create(pr_ctx** out, int device, void* stream, size_t hbm_budget_bytes) {
+    if (!out) return fail(PR_EINVAL, "null output pointer");
+    *out = nullptr;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(PR_EINVAL, "device %d out of range (%d devices)", device, ndev);
+    CK(cudaSetDevice(device));
+    pr_ctx* c = new pr_ctx;
+    c->device = device;
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return fail(PR_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        }
+        c->own_stream = true;
+    }
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    c->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.8 * (double)fr);
+    if (cudaMalloc((void**)&c->rg, sizeof(RayGeom)) != cudaSuccess) {
+        pr_destroy(c);
+        return fail(PR_ENOMEM, "cudaMalloc failed");
+    }
+    *out = c;
+    return PR_OK;
+}
+
+void pr_destroy(pr_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->models) free_model(kv.second);
+    c->models.clear();
+    if (c->pad) cudaFree(c->pad);
+    if (c->rg) cudaFree(c->rg);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int pr_load_model(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom, int location, const float* f0,
+                  const float* mean_dvf, const float* U, int K, int storage, const double tumor_ref_xyz[3],
+                  int* model_id) {
+    if (!c || !model_id) return fail(PR_EINVAL, "null context or model_id");
+    if (!vol_ok(vol)) return fail(PR_EINVAL, "invalid volume descriptor");
+    if (!geom_ok(geom)) return fail(PR_EINVAL, "invalid geometry");
+    if (K < 1 || K > PR_MAX_K) return fail(PR_EINVAL, "K=%d outside 1..%d", K, PR_MAX_K);
+    if (storage != PR_F32 && storage != PR_BF16) return fail(PR_EINVAL, "unknown storage %d", storage);
+    if (location != PR_HOST && location != PR_DEVICE) return fail(PR_EINVAL, "unknown location %d", location);
+    if (!f0 || !mean_dvf || !U || !tumor_ref_xyz) return fail(PR_EINVAL, "null input array");
+    CK(cudaSetDevice(c->device));
+    size_t need = model_bytes(*vol, *geom, K, storage);
+    if (c->used + need > c->budget)
+        return fail(PR_EADMIT, "model needs %zu bytes, %zu of %zu budget in use", need, c->used, c->budget);
+
+    Model* m = new Model;
+    m->vol = *vol;
+    m->geom = *geom;
+    m->geom.ds = resolved_ds(*vol, *geom);
+    m->K = K;
+    m->storage = storage;
+    m->nch = fh_channels(K);
+    m->R = geom->nu * geom->nv;
+    VolDev vd = make_vd(*vol);
+    size_t n = (size_t)vd.n, np = (size_t)vd.np, R = (size_t)m->R;
+    size_t ts = storage == PR_BF16 ? 2 : 4;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto** p, size_t bytes) {
+        if (e == cudaSuccess) e = dalloc(p, bytes, &m->bytes);
+    };
+    A(&m->f0p, np * ts);
+    A(&m->mean, 3 * n * 4);
+    A(&m->U, 3 * (size_t)K * n * ts);
+    A(&m->fh, np * m->nch * 4);
+    A(&m->fpad, np * 4);
+    A(&m->p, R * 4);
+    A(&m->q, R * K * 4);
+    A(&m->y, R * 4);
+    A(&m->r, R * 4);
+    A(&m->flat, n * 4);
+    m->md.vd = vd;
+    A(&m->partials, partial_rows(*m) * kMaxMom * 8);
+    A(&m->counter, 64);
+    A(&m->st, sizeof(SolveState));
+    A(&m->wdev, 8 * 8);
+    A(&m->out, 16 * 8);
+    A(&m->rg, sizeof(RayGeom));
+    A(&m->steps, 16);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&m->st_host, sizeof(SolveState), cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        free_model(m);
+        cudaGetLastError();
+        return fail(PR_ENOMEM, "device allocation failed: %s", cudaGetErrorString(e));
+    }
+    m->md.K = K;
+    m->md.storage = storage;
+    m->md.f0p = m->f0p;
+    m->md.mean = m->mean;
+    m->md.U = m->U;
+    for (int i = 0; i < 3; ++i) m->md.c0[i] = tumor_ref_xyz[i];
+
+    // Upload: float32 staging on the device, then conversion / padding kernels.
+    int rc = PR_OK;
+    cudaMemcpyKind kind = location == PR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    cudaStream_t s = c->stream;
+    do {
+        if ((e = cudaMemsetAsync(m->f0p, 0, np * ts, s))) break;
+        if ((e = cudaMemsetAsync(m->fh, 0, np * m->nch * 4, s))) break;
+        if ((e = cudaMemsetAsync(m->fpad, 0, np * 4, s))) break;
+        if ((e = cudaMemsetAsync(m->partials, 0, partial_rows(*m) * kMaxMom * 8, s))) break;
+        if ((e = cudaMemsetAsync(m->counter, 0, 64, s))) break;
+        if ((e = cudaMemsetAsync(m->st, 0, sizeof(SolveState), s))) break;
+        if ((e = cudaMemcpyAsync(m->mean, mean_dvf, 3 * n * 4, kind, s))) break;
+        // f0 -> padded float32 (fpad as staging), then to storage type.
+        if ((e = cudaMemcpyAsync(m->flat, f0, n * 4, kind, s))) break;
+        Launcher L;
+        L.stream = s;
+        if ((e = launch_pad(L, vd, m->flat, m->fpad))) break;
+        if (storage == PR_F32) {
+            if ((e = cudaMemcpyAsync(m->f0p, m->fpad, np * 4, cudaMemcpyDeviceToDevice, s))) break;
+            if ((e = cudaMemcpyAsync(m->U, U, 3 * (size_t)K * n * 4, kind, s))) break;
+        } else {
+            if ((e = launch_to_bf16(L, m->fpad, (__nv_bfloat16*)m->f0p, np))) break;
+            // U converted plane by plane through the float32 scratch
+            for (int pl = 0; pl < 3 * K && e == cudaSuccess; ++pl) {
+                if ((e = cudaMemcpyAsync(m->flat, U + (size_t)pl * n, n * 4, kind, s))) break;
+                e = launch_to_bf16(L, m->flat, (__nv_bfloat16*)m->U + (size_t)pl * n, n);
+            }
+            if (e) break;
+        }
+        if ((e = cudaMemsetAsync(m->fpad, 0, np * 4, s))) break;
+        e = cudaStreamSynchronize(s);
+    } while (0);
+    if (e != cudaSuccess) {
+        rc = fail(PR_ECUDA, "model upload failed: %s", cudaGetErrorString(e));
+        free_model(m);
+        return rc;
+    }
+    m->id = c->next_id++;
+    c->used += m->bytes;
+    c->models[m->id] = m;
+    *model_id = m->id;
+    return PR_OK;
+}
+
+int pr_release_model(pr_ctx* c, int id) {
+    GET_MODEL(c, id, m);
+    CK(cudaStreamSynchronize(c->stream));
+    c->used -= m->bytes;
+    c->models.erase(id);
+    free_model(m);
+    return PR_OK;
+}
+
+int pr_model_footprint(pr_ctx* c, int id, size_t* bytes) {
+    GET_MODEL(c, id, m);
+    if (!bytes) return fail(PR_EINVAL, "null output");
+    *bytes = m->bytes;
+    return PR_OK;
+}
+
+int pr_reconstruct_async(pr_ctx* c, int id, const float* y_dev, double angle, const pr_solve_opts* opts) {
+    GET_MODEL(c, id, m);
+    if (!y_dev) return fail(PR_EINVAL, "null y");
+    if (opts && opts->loop_mode == PR_LOOP_HOST) return fail(PR_EINVAL, "host loop is synchronous; use pr_reconstruct");
+    CK(cudaMemcpyAsync(m->y, y_dev, (size_t)m->R * 4, cudaMemcpyDeviceToDevice, c->stream));
+    return enqueue_solve(c, m, angle, opts);
+}
+
+int pr_fetch_result(pr_ctx* c, int id, pr_result* out) {
+    GET_MODEL(c, id, m);
+    if (!out) return fail(PR_EINVAL, "null result");
+    CK(cudaMemcpyAsync(m->st_host, m->st, sizeof(SolveState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    fill_result(m, *m->st_host, out);
+    return PR_OK;
+}
+
+int pr_reconstruct(pr_ctx* c, int id, const float* y, int y_location, double angle, const pr_solve_opts* opts,
+                   pr_result* out, float* volume_out) {
+    GET_MODEL(c, id, m);
+    if (!y || !out) return fail(PR_EINVAL, "null y or result");
+    if (y_location != PR_HOST && y_location != PR_DEVICE) return fail(PR_EINVAL, "unknown y location");
+    CK(cudaMemcpyAsync(m->y, y, (size_t)m->R * 4,
+                       y_location == PR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+    TRY(enqueue_solve(c, m, angle, opts));
+    if (volume_out) {
+        Launcher L;
+        L.stream = c->stream;
+        CK(launch_warp(L, m->md, m->st->w, kWarpFlatF, nullptr, m->flat, nullptr));
+        CK(cudaMemcpyAsync(volume_out, m->flat, (size_t)m->md.vd.n * 4, cudaMemcpyDeviceToHost, c->stream));
+    }
+    return pr_fetch_result(c, id, out);
+}
+
+int pr_get_state(pr_ctx* c, int id, double* w) {
+    GET_MODEL(c, id, m);
+    if (!w) return fail(PR_EINVAL, "null w");
+    double buf[8];
+    CK(cudaMemcpyAsync(buf, m->st->w, sizeof buf, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < m->K; ++k) w[k] = buf[k];
+    return PR_OK;
+}
+
+int pr_set_state(pr_ctx* c, int id, const double* w) {
+    GET_MODEL(c, id, m);
+    if (!w) return fail(PR_EINVAL, "null w");
+    double buf[8] = {0};
+    for (int k = 0; k < m->K; ++k) {
+        if (!isfinite(w[k])) return fail(PR_EINVAL, "w[%d] is not finite", k);
+        buf[k] = w[k];
+    }
+    CK(cudaMemcpyAsync(m->st->w, buf, sizeof buf, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PR_OK;
+}
+
+int pr_warp(pr_ctx* c, int id, const double* w, float* f_dev, float* h_dev) {
+    GET_MODEL(c, id, m);
+    if (!w) return fail(PR_EINVAL, "null w");
+    TRY(set_w(c, m, w));
+    Launcher L;
+    L.stream = c->stream;
+    CK(launch_warp(L, m->md, m->wdev, h_dev ? kWarpFlatFH : kWarpFlatF, nullptr, f_dev, h_dev));
+    CK(cudaStreamSynchronize(c->stream));
+    return PR_OK;
+}
+
+int pr_project(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom, double angle, const float* f_dev,
+               float* p_dev) {
+    if (!c) return fail(PR_EINVAL, "null context");
+    if (!vol_ok(vol) || !geom_ok(geom)) return fail(PR_EINVAL, "invalid volume or geometry");
+    if (!f_dev || !p_dev) return fail(PR_EINVAL, "null volume or projection");
+    CK(cudaSetDevice(c->device));
+    size_t np = pad_voxels(*vol);
+    if (np > c->pad_cap) {
+        if (c->pad) cudaFree(c->pad);
+        c->pad = nullptr;
+        c->pad_cap = 0;
+        CK(cudaMalloc((void**)&c->pad, np * 4));
+        c->pad_cap = np;
+    }
+    TRY(set_rg(c, c->rg, *vol, *geom, angle));
+    VolDev vd = make_vd(*vol);
+    Launcher L;
+    L.stream = c->stream;
+    CK(cudaMemsetAsync(c->pad, 0, np * 4, c->stream));
+    CK(launch_pad(L, vd, f_dev, c->pad));
+    CK(launch_project(L, vd, c->pad, 1, 0, c->rg, geom->nu, geom->nv, p_dev, nullptr, nullptr, nullptr, nullptr,
+                      nullptr, kPhaseNone, 0, 0));
+    CK(cudaStreamSynchronize(c->stream));
+    return PR_OK;
+}
+
+int pr_backproject(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom, double angle, const float* r_dev,
+                   float* g_dev) {
+    if (!c) return fail(PR_EINVAL, "null context");
+    if (!vol_ok(vol) || !geom_ok(geom)) return fail(PR_EINVAL, "invalid volume or geometry");
+    if (!r_dev || !g_dev) return fail(PR_EINVAL, "null residual or output");
+    CK(cudaSetDevice(c->device));
+    TRY(set_rg(c, c->rg, *vol, *geom, angle));
+    VolDev vd = make_vd(*vol);
+    Launcher L;
+    L.stream = c->stream;
+    CK(launch_backproject(L, vd, c->rg, r_dev, g_dev, nullptr, 0, nullptr, nullptr, nullptr));
+    CK(cudaStreamSynchronize(c->stream));
+    return PR_OK;
+}
+
+int pr_forward(pr_ctx* c, int id, const double* w, double angle, float* p_dev) {
+    GET_MODEL(c, id, m);
+    if (!w || !p_dev) return fail(PR_EINVAL, "null w or projection");
+    TRY(set_w(c, m, w));
+    TRY(set_rg(c, m->rg, m->vol, m->geom, angle));
+    Launcher L;
+    L.stream = c->stream;
+    CK(launch_warp(L, m->md, m->wdev, kWarpFPad, m->fpad, nullptr, nullptr));
+    CK(launch_project(L, m->md.vd, m->fpad, 1, 0, m->rg, m->geom.nu, m->geom.nv, p_dev, nullptr, nullptr, nullptr,
+                      nullptr, nullptr, kPhaseNone, 0, 0));
+    CK(cudaStreamSynchronize(c->stream));
+    return PR_OK;
+}
+
+int pr_vjp(pr_ctx* c, int id, const double* w, double angle, const float* grad_p_dev, double* grad_w) {
+    GET_MODEL(c, id, m);
+    if (!w || !grad_p_dev || !grad_w) return fail(PR_EINVAL, "null argument");
+    TRY(ensure_hbuf(m));
+    TRY(set_w(c, m, w));
+    TRY(set_rg(c, m->rg, m->vol, m->geom, angle));
+    Launcher L;
+    L.stream = c->stream;
+    CK(launch_warp(L, m->md, m->wdev, kWarpFlatFH, nullptr, nullptr, m->hbuf));
+    CK(launch_backproject(L, m->md.vd, m->rg, grad_p_dev, nullptr, m->hbuf, m->K, m->partials, m->counter, m->out));
+    double buf[8];
+    CK(cudaMemcpyAsync(buf, m->out, sizeof(double) * m->K, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < m->K; ++k) grad_w[k] = buf[k];
+    return PR_OK;
+}
+
+int pr_cost_grad(pr_ctx* c, int id, const float* y_dev, double angle, const double* w, double a, double b, int mode,
+                 double* J, double* grad, float* p_dev) {
+    GET_MODEL(c, id, m);
+    if (!y_dev || !w || !J || !grad) return fail(PR_EINVAL, "null argument");
+    if (mode != 0 && mode != 1) return fail(PR_EINVAL, "mode must be 0 (forward) or 1 (adjoint)");
+    if (!isfinite(a) || !isfinite(b)) return fail(PR_EINVAL, "a, b must be finite");
+    TRY(set_w(c, m, w));
+    TRY(set_rg(c, m->rg, m->vol, m->geom, angle));
+    double ab[2] = {a, b};
+    CK(cudaMemcpyAsync(m->out + 8, ab, sizeof ab, cudaMemcpyHostToDevice, c->stream));
+    Launcher L;
+    L.stream = c->stream;
+    const int nu = m->geom.nu, nv = m->geom.nv;
+    double res[8] = {0};
+    if (mode == 0) {
+        CK(launch_warp(L, m->md, m->wdev, kWarpFH, m->fh, nullptr, nullptr));
+        CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, nu, nv, m->p, m->q, nullptr, nullptr, nullptr,
+                          nullptr, kPhaseNone, 0, 0));
+        CK(launch_cost_grad(L, m->p, m->q, y_dev, m->R, m->K, m->out + 8, m->partials, m->counter, m->out));
+        CK(cudaMemcpyAsync(res, m->out, sizeof(double) * (1 + m->K), cudaMemcpyDeviceToHost, c->stream));
+    } else {
+        TRY(ensure_hbuf(m));
+        CK(launch_warp(L, m->md, m->wdev, kWarpFPad, m->fpad, nullptr, nullptr));
+        CK(launch_warp(L, m->md, m->wdev, kWarpFlatFH, nullptr, nullptr, m->hbuf));
+        CK(launch_project(L, m->md.vd, m->fpad, 1, 0, m->rg, nu, nv, m->p, nullptr, nullptr, nullptr, nullptr,
+                          nullptr, kPhaseNone, 0, 0));
+        CK(launch_cost_grad(L, m->p, nullptr, y_dev, m->R, 0, m->out + 8, m->partials, m->counter, m->out));
+        CK(launch_residual(L, m->p, y_dev, m->R, m->out + 8, m->r));
+        CK(cudaMemcpyAsync(res, m->out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(launch_backproject(L, m->md.vd, m->rg, m->r, nullptr, m->hbuf, m->K, m->partials, m->counter,
+                              m->out + 1));
+        CK(cudaMemcpyAsync(res + 1, m->out + 1, sizeof(double) * m->K, cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (p_dev) CK(cudaMemcpyAsync(p_dev, m->p, (size_t)m->R * 4, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *J = res[0];
+    for (int k = 0; k < m->K; ++k) grad[k] = mode == 0 ? res[1 + k] : 2.0 * res[1 + k];
+    return PR_OK;
+}
+
+int pr_tumor(pr_ctx* c, int id, const double* w, double tol, int max_iter, double* xyz, int* steps) {
+    GET_MODEL(c, id, m);
+    if (!w || !xyz) return fail(PR_EINVAL, "null argument");
+    if (!(tol >= 0) || max_iter < 0) return fail(PR_EINVAL, "invalid tol or max_iter");
+    TRY(set_w(c, m, w));
+    Launcher L;
+    L.stream = c->stream;
+    CK(launch_tumor(L, m->md, m->wdev, tol, max_iter, nullptr, m->out, m->steps));
+    double buf[3];
+    int st = 0;
+    CK(cudaMemcpyAsync(buf, m->out, sizeof buf, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&st, m->steps, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < 3; ++i) xyz[i] = buf[i];
+    if (steps) *steps = st;
+    return PR_OK;
+}
+
+}  // extern "C"

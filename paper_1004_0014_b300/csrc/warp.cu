@@ -1,0 +1,219 @@
+// G1: fused DVF synthesis and trilinear warp (Eq. 1, Section 2.2).
+//
+// One thread handles four consecutive voxels of the flat grid. It reads the
+// mean DVF (3 planes) and the K eigenvector fields (3K planes) with 16-byte
+// vector loads (8-byte for bfloat16 storage), forms x = mean + sum_k u_k w_k,
+// pulls back to q = v + x / spacing, and evaluates the zero-padded trilinear
+// interpolant of f0 at q from the padded reference volume. On gradient points
+// it also forms the exact derivative of the interpolant and h_k = (df/dx) . u_k
+// with the eigenvector values already in registers. The pass is HBM-bound:
+// 12 + 12K bytes of field reads per voxel (float32) against 4 bytes of f
+// (+4K of h) written; the f0 taps hit L1/L2.
+#include "internal.h"
+
+namespace pr {
+namespace {
+
+constexpr int kWarpThreads = 256;
+
+template <typename TS>
+struct WarpArgs {
+    const TS* f0p;
+    const float* mean;
+    const TS* U;
+    const double* w;
+    VolDev vd;
+    float* out_pad;  // kWarpFH: interleaved (nch floats per voxel); kWarpFPad: planar
+    float* f_flat;
+    float* h_flat;
+    int vec_ok;      // N % 4 == 0: planes are 16-byte aligned for vector loads
+};
+
+__device__ __forceinline__ float lerp(float a, float b, float t) { return __fmaf_rn(t, b - a, a); }
+
+template <int K, int MODE, typename TS>
+__global__ void __launch_bounds__(kWarpThreads) k_warp(WarpArgs<TS> A) {
+    constexpr bool kH = (MODE == kWarpFH || MODE == kWarpFlatFH);
+    constexpr int kNch = K <= 3 ? 4 : 8;
+    const VolDev& vd = A.vd;
+    long long v0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * 4;
+    if (v0 >= vd.n) return;
+    const long long n = vd.n;
+
+    float w[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) w[k] = (float)A.w[k];
+
+    // Fields of the four voxels: mean (3) and eigenvectors (3K).
+    float mx[3][4];
+    float u[K][3][4];
+    const bool full = A.vec_ok && (v0 + 3 < n);
+    if (full) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ld4(A.mean + c * n + v0, mx[c]);
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ld4(A.U + (3LL * k + c) * n + v0, u[k][c]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            long long v = v0 + e < n ? v0 + e : n - 1;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) mx[c][e] = __ldg(A.mean + c * n + v);
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) u[k][c][e] = ld_val(A.U + (3LL * k + c) * n + v);
+        }
+    }
+
+    long long jk = v0 / vd.nx;
+    int i = (int)(v0 - jk * vd.nx);
+    int j = (int)(jk % vd.ny);
+    int kz = (int)(jk / vd.ny);
+    const long long plane = (long long)vd.nxp * vd.nyp;
+
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (v0 + e < n) {
+            float d0 = mx[0][e], d1 = mx[1][e], d2 = mx[2][e];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                d0 = __fmaf_rn(u[k][0][e], w[k], d0);
+                d1 = __fmaf_rn(u[k][1][e], w[k], d1);
+                d2 = __fmaf_rn(u[k][2][e], w[k], d2);
+            }
+            float qx = __fmaf_rn(d0, vd.inv_dx, (float)i);
+            float qy = __fmaf_rn(d1, vd.inv_dy, (float)j);
+            float qz = __fmaf_rn(d2, vd.inv_dz, (float)kz);
+            float val = 0.0f;
+            float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+            if (qx > -1.0f && qx < (float)vd.nx && qy > -1.0f && qy < (float)vd.ny && qz > -1.0f &&
+                qz < (float)vd.nz) {
+                float fx = floorf(qx), fy = floorf(qy), fz = floorf(qz);
+                float tx = qx - fx, ty = qy - fy, tz = qz - fz;
+                long long base = ((long long)((int)fz + 1) * vd.nyp + ((int)fy + 1)) * vd.nxp + ((int)fx + 1);
+                const TS* c0 = A.f0p + base;
+                float c000 = ld_val(c0), c100 = ld_val(c0 + 1);
+                float c010 = ld_val(c0 + vd.nxp), c110 = ld_val(c0 + vd.nxp + 1);
+                float c001 = ld_val(c0 + plane), c101 = ld_val(c0 + plane + 1);
+                float c011 = ld_val(c0 + plane + vd.nxp), c111 = ld_val(c0 + plane + vd.nxp + 1);
+                float x00 = lerp(c000, c100, tx), x10 = lerp(c010, c110, tx);
+                float x01 = lerp(c001, c101, tx), x11 = lerp(c011, c111, tx);
+                float y0 = lerp(x00, x10, ty), y1 = lerp(x01, x11, ty);
+                val = lerp(y0, y1, tz);
+                if (kH) {
+                    float e00 = c100 - c000, e10 = c110 - c010, e01 = c101 - c001, e11 = c111 - c011;
+                    gx = lerp(lerp(e00, e10, ty), lerp(e01, e11, ty), tz) * vd.inv_dx;
+                    gy = lerp(x10 - x00, x11 - x01, tz) * vd.inv_dy;
+                    gz = (y1 - y0) * vd.inv_dz;
+                }
+            }
+            float h[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                h[k] = kH ? __fmaf_rn(gz, u[k][2][e], __fmaf_rn(gy, u[k][1][e], gx * u[k][0][e])) : 0.0f;
+
+            long long pidx = ((long long)(kz + 1) * vd.nyp + (j + 1)) * vd.nxp + (i + 1);
+            if (MODE == kWarpFH) {
+                float o[kNch];
+                o[0] = val;
+#pragma unroll
+                for (int c = 1; c < kNch; ++c) o[c] = (c - 1 < K) ? h[c - 1 < K ? c - 1 : 0] : 0.0f;
+                float4* dst = reinterpret_cast<float4*>(A.out_pad + pidx * kNch);
+#pragma unroll
+                for (int c4 = 0; c4 < kNch / 4; ++c4)
+                    dst[c4] = make_float4(o[4 * c4], o[4 * c4 + 1], o[4 * c4 + 2], o[4 * c4 + 3]);
+            } else if (MODE == kWarpFPad) {
+                A.out_pad[pidx] = val;
+            } else {
+                if (A.f_flat) A.f_flat[v0 + e] = val;
+                if (kH && A.h_flat)
+#pragma unroll
+                    for (int k = 0; k < K; ++k) A.h_flat[k * n + v0 + e] = h[k];
+            }
+        }
+        // next voxel of the flat order
+        if (++i == vd.nx) {
+            i = 0;
+            if (++j == vd.ny) {
+                j = 0;
+                ++kz;
+            }
+        }
+    }
+}
+
+template <int K, typename TS>
+cudaError_t dispatch_mode(Launcher& L, const ModelDev& m, const double* w, int mode, float* out_pad,
+                          float* f_flat, float* h_flat) {
+    WarpArgs<TS> A;
+    A.f0p = static_cast<const TS*>(m.f0p);
+    A.mean = m.mean;
+    A.U = static_cast<const TS*>(m.U);
+    A.w = w;
+    A.vd = m.vd;
+    A.out_pad = out_pad;
+    A.f_flat = f_flat;
+    A.h_flat = h_flat;
+    A.vec_ok = (m.vd.n % 4 == 0) ? 1 : 0;
+    long long threads = (m.vd.n + 3) / 4;
+    dim3 grid((unsigned)((threads + kWarpThreads - 1) / kWarpThreads));
+    switch (mode) {
+        case kWarpFH: return L(k_warp<K, kWarpFH, TS>, grid, dim3(kWarpThreads), 0, A);
+        case kWarpFPad: return L(k_warp<K, kWarpFPad, TS>, grid, dim3(kWarpThreads), 0, A);
+        case kWarpFlatF: return L(k_warp<K, kWarpFlatF, TS>, grid, dim3(kWarpThreads), 0, A);
+        case kWarpFlatFH: return L(k_warp<K, kWarpFlatFH, TS>, grid, dim3(kWarpThreads), 0, A);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename TS>
+cudaError_t dispatch_k(Launcher& L, const ModelDev& m, const double* w, int mode, float* out_pad,
+                       float* f_flat, float* h_flat) {
+    switch (m.K) {
+        case 1: return dispatch_mode<1, TS>(L, m, w, mode, out_pad, f_flat, h_flat);
+        case 2: return dispatch_mode<2, TS>(L, m, w, mode, out_pad, f_flat, h_flat);
+        case 3: return dispatch_mode<3, TS>(L, m, w, mode, out_pad, f_flat, h_flat);
+        case 4: return dispatch_mode<4, TS>(L, m, w, mode, out_pad, f_flat, h_flat);
+        case 5: return dispatch_mode<5, TS>(L, m, w, mode, out_pad, f_flat, h_flat);
+        case 6: return dispatch_mode<6, TS>(L, m, w, mode, out_pad, f_flat, h_flat);
+        case 7: return dispatch_mode<7, TS>(L, m, w, mode, out_pad, f_flat, h_flat);
+    }
+    return cudaErrorInvalidValue;
+}
+
+__global__ void __launch_bounds__(256) k_pad(VolDev vd, const float* __restrict__ src, float* __restrict__ dst) {
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= vd.n) return;
+    long long jk = v / vd.nx;
+    int i = (int)(v - jk * vd.nx), j = (int)(jk % vd.ny), k = (int)(jk / vd.ny);
+    dst[((long long)(k + 1) * vd.nyp + (j + 1)) * vd.nxp + (i + 1)] = __ldg(src + v);
+}
+
+__global__ void __launch_bounds__(256) k_to_bf16(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst,
+                                                 long long n) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+}  // namespace
+
+cudaError_t launch_to_bf16(Launcher& L, const float* src, __nv_bfloat16* dst, long long n) {
+    dim3 grid((unsigned)((n + 255) / 256));
+    return L(k_to_bf16, grid, dim3(256), 0, src, dst, n);
+}
+
+cudaError_t launch_warp(Launcher& L, const ModelDev& m, const double* w_dev, int mode, float* out_pad,
+                        float* f_flat, float* h_flat) {
+    if (m.storage == 1) return dispatch_k<__nv_bfloat16>(L, m, w_dev, mode, out_pad, f_flat, h_flat);
+    return dispatch_k<float>(L, m, w_dev, mode, out_pad, f_flat, h_flat);
+}
+
+cudaError_t launch_pad(Launcher& L, const VolDev& vd, const float* src, float* dst_pad) {
+    dim3 grid((unsigned)((vd.n + 255) / 256));
+    return L(k_pad, grid, dim3(256), 0, vd, src, dst_pad);
+}
+
+}  // namespace pr
