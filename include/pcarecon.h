@@ -230,6 +230,37 @@ int pr_cost_grad(pr_ctx* ctx, int model_id, const float* y_dev, double angle_rad
 int pr_tumor(pr_ctx* ctx, int model_id, const double* w, double tol, int max_iter, double* xyz,
              int* steps);
 
+/* ---- measurement (no counterpart in the paper; used by benchmarks) ---- */
+
+/* Kernels pr_time_kernel can time. */
+enum {
+    PR_KERNEL_WARP_FH = 0,      /* fused DVF synthesis + warp writing f and h (solver pass) */
+    PR_KERNEL_PROJECT_FH = 1,   /* ray-march projection of (f, h_1..h_K) (solver pass) */
+    PR_KERNEL_REGRAD = 2,       /* residual, cost and gradient over the detector */
+    PR_KERNEL_BACKPROJECT = 3,  /* gather transpose contracted with h (adjoint gradient) */
+    PR_KERNEL_WARP_F = 4,       /* warp writing f only */
+    PR_KERNEL_PROJECT_F = 5     /* ray-march projection of f only */
+};
+
+/* Launch kernel `which` `iters` times back to back on the context stream
+ * at the model's current warm-start w and gantry angle `angle_rad`, and
+ * return the mean device time per launch in *avg_ms (CUDA events recorded on
+ * that stream). Overwrites the model's scratch buffers, not its warm start. */
+int pr_time_kernel(pr_ctx* ctx, int model_id, int which, double angle_rad, int iters, double* avg_ms);
+
+typedef struct {
+    long long solves;   /* solves enqueued on this model since it was loaded */
+    long long trials;   /* line-search trials run by those solves */
+    long long kernels;  /* CUDA kernels those solves launched */
+} pr_stats;
+
+/* Cumulative counters of a model (waits for its enqueued work). */
+int pr_model_stats(pr_ctx* ctx, int model_id, pr_stats* out);
+
+/* Bytes one pr_reconstruct with a host y moves host-to-device (y and the
+ * per-solve parameters) and device-to-host (the result record). */
+int pr_io_bytes(pr_ctx* ctx, int model_id, size_t* h2d, size_t* d2h);
+
 #ifdef __cplusplus
 }
 #endif

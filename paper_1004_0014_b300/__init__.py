@@ -157,6 +157,16 @@ class Context:
     def tumor(self, mid: int, w, tol: float = 1e-6, max_iter: int = 100):
         return capi.pr_tumor(self._ctx, mid, w, tol, max_iter)
 
+    # --- measurement -------------------------------------------------------
+    def time_kernel(self, mid: int, which: int, angle_rad: float = 0.0, iters: int = 20) -> float:
+        return capi.pr_time_kernel(self._ctx, mid, which, angle_rad, iters)
+
+    def stats(self, mid: int) -> dict:
+        return capi.pr_model_stats(self._ctx, mid)
+
+    def io_bytes(self, mid: int):
+        return capi.pr_io_bytes(self._ctx, mid)
+
 
 def default_opts(**overrides) -> SolveOpts:
     return capi.pr_default_opts(**overrides)

@@ -40,8 +40,16 @@ EXPORTED = [
     "pr_version", "pr_last_error", "pr_default_opts", "pr_create", "pr_destroy", "pr_load_model",
     "pr_release_model", "pr_model_footprint", "pr_reconstruct", "pr_reconstruct_async",
     "pr_fetch_result", "pr_get_state", "pr_set_state", "pr_warp", "pr_project", "pr_backproject",
-    "pr_forward", "pr_vjp", "pr_cost_grad", "pr_tumor",
+    "pr_forward", "pr_vjp", "pr_cost_grad", "pr_tumor", "pr_time_kernel", "pr_model_stats",
+    "pr_io_bytes",
 ]
+
+PR_KERNEL_WARP_FH, PR_KERNEL_PROJECT_FH, PR_KERNEL_REGRAD = 0, 1, 2
+PR_KERNEL_BACKPROJECT, PR_KERNEL_WARP_F, PR_KERNEL_PROJECT_F = 3, 4, 5
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("solves", ctypes.c_longlong), ("trials", ctypes.c_longlong), ("kernels", ctypes.c_longlong)]
 
 
 class PcaReconError(RuntimeError):
@@ -125,6 +133,9 @@ def load_library(path: str | None = None):
         "pr_vjp": (_I, [_P, _I, _DP, _D, _P, _DP]),
         "pr_cost_grad": (_I, [_P, _I, _P, _D, _DP, _D, _D, _I, _DP, _DP, _P]),
         "pr_tumor": (_I, [_P, _I, _DP, _D, _I, _DP, ctypes.POINTER(_I)]),
+        "pr_time_kernel": (_I, [_P, _I, _I, _D, _I, _DP]),
+        "pr_model_stats": (_I, [_P, _I, ctypes.POINTER(Stats)]),
+        "pr_io_bytes": (_I, [_P, _I, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -317,3 +328,21 @@ def pr_tumor(ctx, model_id: int, w, tol: float = 1e-6, max_iter: int = 100):
     _check(_lib.pr_tumor(ctx, int(model_id), pw, float(tol), int(max_iter), xyz.ctypes.data_as(_DP),
                          ctypes.byref(steps)))
     return xyz, steps.value
+
+
+def pr_time_kernel(ctx, model_id: int, which: int, angle_rad: float, iters: int) -> float:
+    ms = ctypes.c_double()
+    _check(_lib.pr_time_kernel(ctx, int(model_id), int(which), float(angle_rad), int(iters), ctypes.byref(ms)))
+    return ms.value
+
+
+def pr_model_stats(ctx, model_id: int) -> dict:
+    st = Stats()
+    _check(_lib.pr_model_stats(ctx, int(model_id), ctypes.byref(st)))
+    return dict(solves=st.solves, trials=st.trials, kernels=st.kernels)
+
+
+def pr_io_bytes(ctx, model_id: int):
+    a, b = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(_lib.pr_io_bytes(ctx, int(model_id), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value

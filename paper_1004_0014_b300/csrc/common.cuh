@@ -82,6 +82,7 @@ struct SolveState {
     int iter, bt, trials, total_bt, stop, accepted, need_grad, running;
     double tumor[3];
     int tumor_steps, pad_;
+    long long cum_solves, cum_trials;  // since the model was loaded
 };
 
 // ---------------------------------------------------------------------------

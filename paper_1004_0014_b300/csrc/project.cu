@@ -83,6 +83,7 @@ k_begin(const float* __restrict__ y, int R, SolveState* st, double* partials, un
         st->accepted = 0;
         st->need_grad = 0;
         st->running = 1;
+        st->cum_solves += 1;
     }
 }
 
@@ -168,6 +169,7 @@ __device__ void controller_project(SolveState* st, const double (&tot)[3], int p
         return;
     }
     st->trials += 1;
+    st->cum_trials += 1;
     if (st->trials > (st->prm.max_iters + 1) * (st->prm.max_bt + 1) + 1) {
         st->stop = 6;  // internal guard: more trials than the options allow
         st->need_grad = 0;

@@ -746,4 +746,78 @@ int pr_tumor(pr_ctx* c, int id, const double* w, double tol, int max_iter, doubl
     return PR_OK;
 }
 
+int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double* avg_ms) {
+    GET_MODEL(c, id, m);
+    if (!avg_ms || iters < 1 || iters > 100000) return fail(PR_EINVAL, "invalid iters or output");
+    if (which < PR_KERNEL_WARP_FH || which > PR_KERNEL_PROJECT_F) return fail(PR_EINVAL, "unknown kernel %d", which);
+    TRY(set_rg(c, m->rg, m->vol, m->geom, angle));
+    if (which == PR_KERNEL_BACKPROJECT) TRY(ensure_hbuf(m));
+    Launcher L;
+    L.stream = c->stream;
+    const int nu = m->geom.nu, nv = m->geom.nv;
+    double ab[2] = {1.0, 0.0};
+    CK(cudaMemcpyAsync(m->out + 8, ab, sizeof ab, cudaMemcpyHostToDevice, c->stream));
+    // Inputs the timed kernel reads: f/h at the warm-start w, p and q.
+    CK(launch_warp(L, m->md, m->st->w, kWarpFH, m->fh, nullptr, nullptr));
+    CK(launch_warp(L, m->md, m->st->w, kWarpFPad, m->fpad, nullptr, nullptr));
+    if (which == PR_KERNEL_BACKPROJECT) CK(launch_warp(L, m->md, m->st->w, kWarpFlatFH, nullptr, nullptr, m->hbuf));
+    CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, nu, nv, m->p, m->q, nullptr, nullptr, nullptr, nullptr,
+                      kPhaseNone, 0, 0));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    cudaError_t err = cudaEventRecord(e0, c->stream);
+    for (int i = 0; i < iters && err == cudaSuccess; ++i) {
+        switch (which) {
+            case PR_KERNEL_WARP_FH: err = launch_warp(L, m->md, m->st->w, kWarpFH, m->fh, nullptr, nullptr); break;
+            case PR_KERNEL_PROJECT_FH:
+                err = launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, nu, nv, m->p, m->q, nullptr, nullptr,
+                                     nullptr, nullptr, kPhaseNone, 0, 0);
+                break;
+            case PR_KERNEL_REGRAD:
+                err = launch_cost_grad(L, m->p, m->q, m->p, m->R, m->K, m->out + 8, m->partials, m->counter, m->out);
+                break;
+            case PR_KERNEL_BACKPROJECT:
+                err = launch_backproject(L, m->md.vd, m->rg, m->p, nullptr, m->hbuf, m->K, m->partials, m->counter,
+                                         m->out);
+                break;
+            case PR_KERNEL_WARP_F: err = launch_warp(L, m->md, m->st->w, kWarpFPad, m->fpad, nullptr, nullptr); break;
+            case PR_KERNEL_PROJECT_F:
+                err = launch_project(L, m->md.vd, m->fpad, 1, 0, m->rg, nu, nv, m->r, nullptr, nullptr, nullptr,
+                                     nullptr, nullptr, kPhaseNone, 0, 0);
+                break;
+        }
+    }
+    if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(err);
+    *avg_ms = (double)ms / iters;
+    return PR_OK;
+}
+
+int pr_model_stats(pr_ctx* c, int id, pr_stats* out) {
+    GET_MODEL(c, id, m);
+    if (!out) return fail(PR_EINVAL, "null output");
+    CK(cudaMemcpyAsync(m->st_host, m->st, sizeof(SolveState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    out->solves = m->st_host->cum_solves;
+    out->trials = m->st_host->cum_trials;
+    // per solve: begin, warp, project, residual-gradient, tumor; per trial:
+    // warp, project, residual-gradient (the body of the loop)
+    out->kernels = 5 * out->solves + 3 * out->trials;
+    return PR_OK;
+}
+
+int pr_io_bytes(pr_ctx* c, int id, size_t* h2d, size_t* d2h) {
+    GET_MODEL(c, id, m);
+    if (!h2d || !d2h) return fail(PR_EINVAL, "null output");
+    *h2d = (size_t)m->R * 4 + sizeof(SolveParams);
+    *d2h = sizeof(SolveState);
+    return PR_OK;
+}
+
 }  // extern "C"
