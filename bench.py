@@ -320,9 +320,10 @@ def run_ours(args):
     W, K = args.warmup, args.steps
     frames = list(range(W + K))
     ys = make_targets(ctx, w, f0, frames)
+    torch.cuda.synchronize()  # ys was written on torch's stream; the solves read it on ctx.stream
     angles = [frame_params(w, j)[0] for j in frames]
     opts = default_opts(max_iters=w["max_iters"])
-    stream = torch.cuda.current_stream()
+    stream = ctx.stream  # every library launch of this context is ordered on this stream
 
     # ---------------- device-resident, on-device loop ----------------
     ctx.set_state(mid, np.zeros(w["K"]))

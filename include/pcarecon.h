@@ -106,6 +106,8 @@ typedef struct {
     int loop_mode;       /* PR_LOOP_GRAPH (on-device loop in a CUDA graph) or PR_LOOP_HOST */
     double tumor_tol;    /* fixed-point stop, mm; default 1e-6 */
     int tumor_max_iter;  /* default 100 */
+    double step_growth;  /* first trial step of an iteration = step_growth x the last
+                            accepted step (the first iteration uses step0_mm); default 1.25 */
 } pr_solve_opts;
 
 typedef struct {

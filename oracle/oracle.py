@@ -23,8 +23,9 @@ Readings of the paper where it is silent (the CUDA path uses the same):
     decrease J(w - mu g; a, b) <= J(w; a, b) - c1 mu |g|^2 with c1 = 1e-4,
     backtracking mu <- beta mu with beta = 0.5, at most 20 backtracks. The
     first trial step is mu = step0_mm / |g| (moves w by step0_mm), later ones
-    start from 2 x the last accepted mu. No accepted step: w is kept and the
-    solve stops with stop reason "line search failed".
+    start from step_growth x the last accepted mu (step_growth = 1.25). No
+    accepted step: w is kept and the solve stops with stop reason "line
+    search failed".
   * (a, b) before the first step 1: Eq. 4 at the starting w.
   * Stop (Section 2.2: gradient "sufficiently small" or the iteration cap):
     |g| <= grad_tol * |g_0| or max_iters accepted steps.
@@ -252,6 +253,7 @@ class SolveOptions:
     beta: float = 0.5
     max_backtracks: int = 20
     step0_mm: float = 1.0
+    step_growth: float = 1.25
     tumor_tol: float = 1e-6
     tumor_max_iter: int = 100
 
@@ -295,7 +297,7 @@ def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None) -> 
             stop = STOP_MAX_ITERS
             break
         # Step 1: w <- w - mu g, mu by backtracking from the initial trial.
-        mu = o.step0_mm / gn if mu_prev is None else 2.0 * mu_prev
+        mu = o.step0_mm / gn if mu_prev is None else o.step_growth * mu_prev
         accepted = None
         for bt in range(o.max_backtracks + 1):
             trial = evaluate(model, geom, angle, w - mu * g)

@@ -38,15 +38,18 @@ class Context:
     """One pcarecon context on one CUDA device (wraps pr_create / pr_destroy)."""
 
     def __init__(self, device: int = 0, stream=None, hbm_budget_bytes: int = 0):
+        """stream: a torch.cuda.Stream to run on (default: a new one). All of
+        the context's device work is ordered on it; time it with events
+        recorded on `self.stream`."""
         import torch
 
         if not torch.cuda.is_available():
             raise RuntimeError("pcarecon needs a CUDA device")
         self.device = device
         if stream is None:
-            with torch.cuda.device(device):
-                stream = torch.cuda.current_stream().cuda_stream
-        self._ctx = capi.pr_create(device, stream, hbm_budget_bytes)
+            stream = torch.cuda.Stream(device=device)
+        self.stream = stream
+        self._ctx = capi.pr_create(device, stream.cuda_stream, hbm_budget_bytes)
         self._models = {}
 
     def close(self):

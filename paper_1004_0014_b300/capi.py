@@ -74,7 +74,8 @@ class SolveOpts(ctypes.Structure):
                 ("beta", ctypes.c_double), ("max_backtracks", ctypes.c_int),
                 ("step0_mm", ctypes.c_double), ("cold_start", ctypes.c_int),
                 ("w0", ctypes.c_double * PR_MAX_K), ("loop_mode", ctypes.c_int),
-                ("tumor_tol", ctypes.c_double), ("tumor_max_iter", ctypes.c_int)]
+                ("tumor_tol", ctypes.c_double), ("tumor_max_iter", ctypes.c_int),
+                ("step_growth", ctypes.c_double)]
 
 
 class Result(ctypes.Structure):
@@ -210,6 +211,7 @@ def pr_default_opts(**overrides) -> SolveOpts:
 def pr_create(device: int = 0, stream=None, hbm_budget_bytes: int = 0):
     lib = load_library()
     ctx = ctypes.c_void_p()
+    # A zero handle is the legacy default stream; pass it through as such.
     s = ctypes.c_void_p(stream) if stream else None
     _check(lib.pr_create(ctypes.byref(ctx), int(device), s, int(hbm_budget_bytes)))
     return ctx

@@ -65,7 +65,7 @@ enum Phase : int {
 struct SolveParams {
     RayGeom rg;
     double w0[8];
-    double c1, beta, grad_tol, step0, tumor_tol;
+    double c1, beta, grad_tol, step0, tumor_tol, step_growth;
     int max_iters, max_bt, tumor_max_iter, K;
     int cold_start;  // 1: start from w0; 0: from the state's last accepted w
     int pad_;

@@ -47,10 +47,14 @@ cudaError_t launch_begin(Launcher& L, const float* y, int R, SolveState* st, dou
 // (1 = planar f, 4 or 8 = interleaved f, h). rg: device RayGeom. p: [R];
 // q: [K][R] (channels 1..K, nullable). For phase != kPhaseNone, y, st,
 // partials and counter drive the fused reduction and the controller.
+// order: device permutation of the detector tiles (nullable), see project_tile_order.
 cudaError_t launch_project(Launcher& L, const VolDev& vd, const float* vol_pad, int nch, int K,
-                           const RayGeom* rg, int nu, int nv, float* p, float* q, const float* y,
-                           SolveState* st, double* partials, unsigned int* counter, int phase,
-                           cudaGraphConditionalHandle h, int use_graph);
+                           const RayGeom* rg, const int* order, int nu, int nv, float* p, float* q,
+                           const float* y, SolveState* st, double* partials, unsigned int* counter,
+                           int phase, cudaGraphConditionalHandle h, int use_graph);
+
+// Host: the projector's tile launch order for an nu x nv detector (project_blocks ints).
+void project_tile_order(int nu, int nv, int* order);
 
 // Residual, cost and gradient from stored p and q at the state's (a, b); then
 // the stop test and the next trial step (runs only when the state asks).

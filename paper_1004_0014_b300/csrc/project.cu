@@ -133,11 +133,62 @@ __device__ __forceinline__ void accumulate(const float* __restrict__ vol, const 
     }
 }
 
+// Sample accumulation that keeps the eight corners of the last trilinear cell
+// in registers: consecutive samples 1 mm apart often fall in the same 2-2.5 mm
+// cell, and then no lane that stays in its cell touches L1 for that sample.
+// For 1 or 4 channels per voxel (8 or 32 corner registers).
+template <int NCH>
+struct CellCache {
+    static constexpr int NV = NCH == 1 ? 1 : 4;
+    long long base = -1;
+    float c[8][NV];  // corners: index = dx + 2 dy + 4 dz
+
+    __device__ __forceinline__ void sample(const float* __restrict__ vol, const VolDev& vd, const float q[3],
+                                           float (&acc)[NCH]) {
+        float qx = fminf(fmaxf(q[0], -1.0f), (float)vd.nx);
+        float qy = fminf(fmaxf(q[1], -1.0f), (float)vd.ny);
+        float qz = fminf(fmaxf(q[2], -1.0f), (float)vd.nz);
+        int ix = min((int)floorf(qx), vd.nx - 1);
+        int iy = min((int)floorf(qy), vd.ny - 1);
+        int iz = min((int)floorf(qz), vd.nz - 1);
+        float tx = qx - (float)ix, ty = qy - (float)iy, tz = qz - (float)iz;
+        long long b = ((long long)(iz + 1) * vd.nyp + (iy + 1)) * vd.nxp + (ix + 1);
+        if (b != base) {
+            base = b;
+            const long long plane = (long long)vd.nxp * vd.nyp;
+            const long long off[4] = {0, (long long)vd.nxp, plane, plane + vd.nxp};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (NCH == 1) {
+                    c[2 * k][0] = __ldg(vol + b + off[k]);
+                    c[2 * k + 1][0] = __ldg(vol + b + off[k] + 1);
+                } else {
+                    const float4* p4 = reinterpret_cast<const float4*>(vol + (b + off[k]) * 4);
+                    float4 a0 = __ldg(p4), a1 = __ldg(p4 + 1);
+                    c[2 * k][0] = a0.x, c[2 * k][1] = a0.y, c[2 * k][2] = a0.z, c[2 * k][3] = a0.w;
+                    c[2 * k + 1][0] = a1.x, c[2 * k + 1][1] = a1.y, c[2 * k + 1][2] = a1.z, c[2 * k + 1][3] = a1.w;
+                }
+            }
+        }
+        float wy0 = 1.0f - ty, wz0 = 1.0f - tz;
+        const float wyz[4] = {wy0 * wz0, ty * wz0, wy0 * tz, ty * tz};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float w0 = wyz[k] * (1.0f - tx), w1 = wyz[k] * tx;
+#pragma unroll
+            for (int ch = 0; ch < NV; ++ch)
+                acc[ch] = __fmaf_rn(w1, c[2 * k + 1][ch], __fmaf_rn(w0, c[2 * k][ch], acc[ch]));
+        }
+    }
+};
+
 struct ProjArgs {
     const float* vol;
     VolDev vd;
     const RayGeom* rg;
+    const int* order;  // tile permutation (nullable): long rays first, so the last wave is short
     int nu, nv, K;
+    int ntu;           // tiles along u
     float* p;
     float* q;
     const float* y;
@@ -211,8 +262,11 @@ template <int NCH>
 __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs A) {
     const RayGeom g = *A.rg;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int iu = blockIdx.x * kTileU + (wid & 3) * 8 + (lane & 7);
-    const int iv = blockIdx.y * kTileV + (wid >> 2) * 4 + (lane >> 3);
+    int tile = A.order ? __ldg(A.order + blockIdx.x) : (int)blockIdx.x;
+    if (tile < 0 || tile >= (int)gridDim.x) tile = blockIdx.x;  // a permutation never trips this
+    const int tu = tile % A.ntu, tv = tile / A.ntu;
+    const int iu = tu * kTileU + (wid & 3) * 8 + (lane & 7);
+    const int iv = tv * kTileV + (wid >> 2) * 4 + (lane >> 3);
     const bool valid = iu < A.nu && iv < A.nv;
 
     float b[3];
@@ -234,10 +288,19 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs A) {
     float acc[NCH];
 #pragma unroll
     for (int c = 0; c < NCH; ++c) acc[c] = 0.0f;
-    for (int s = s_lo; s <= s_hi; ++s) {
-        float q[3];
-        sample_pos(g, b, s, q);
-        accumulate<NCH>(A.vol, A.vd, q, acc);
+    if constexpr (NCH <= 4) {
+        CellCache<NCH> cache;
+        for (int s = s_lo; s <= s_hi; ++s) {
+            float q[3];
+            sample_pos(g, b, s, q);
+            cache.sample(A.vol, A.vd, q, acc);
+        }
+    } else {
+        for (int s = s_lo; s <= s_hi; ++s) {
+            float q[3];
+            sample_pos(g, b, s, q);
+            accumulate<NCH>(A.vol, A.vd, q, acc);
+        }
     }
 
     const int R = A.nu * A.nv;
@@ -260,8 +323,8 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs A) {
         v[2] = (double)pv * yv;
     }
     block_sum<3>(v);
-    const int nblocks = gridDim.x * gridDim.y;
-    if (!publish_partials<3>(v, A.partials, blockIdx.y * gridDim.x + blockIdx.x, nblocks, A.counter)) return;
+    const int nblocks = gridDim.x;
+    if (!publish_partials<3>(v, A.partials, tile, nblocks, A.counter)) return;
     double tot[3];
     total_partials<3>(A.partials, nblocks, tot);
     if (threadIdx.x == 0) {
@@ -327,7 +390,7 @@ k_regrad(const float* __restrict__ p, const float* __restrict__ q, const float* 
         set_loop(st, 0, h, use_graph);
         return;
     }
-    st->mu = st->iter == 0 ? st->prm.step0 / gn : 2.0 * st->mu_prev;
+    st->mu = st->iter == 0 ? st->prm.step0 / gn : st->prm.step_growth * st->mu_prev;
     st->bt = 0;
     next_trial(st, K);
     set_loop(st, 1, h, use_graph);
@@ -443,6 +506,32 @@ cudaError_t launch_residual(Launcher& L, const float* p, const float* y, int R, 
 }
 
 int project_blocks(int nu, int nv) { return ((nu + kTileU - 1) / kTileU) * ((nv + kTileV - 1) / kTileV); }
+
+void project_tile_order(int nu, int nv, int* order) {
+    // Detector tiles sorted by the distance of their centre from the detector
+    // centre: central rays cross the most volume, so they start first and the
+    // last, partial wave of blocks holds the short edge tiles.
+    const int ntu = (nu + kTileU - 1) / kTileU, ntv = (nv + kTileV - 1) / kTileV, n = ntu * ntv;
+    const double cu = 0.5 * nu, cv = 0.5 * nv;
+    struct Key { double d; int t; };
+    Key* keys = new Key[n];
+    for (int t = 0; t < n; ++t) {
+        double u = ((t % ntu) + 0.5) * kTileU - cu, v = ((t / ntu) + 0.5) * kTileV - cv;
+        keys[t] = {u * u + v * v, t};
+    }
+    // insertion sort on a stable key (small n; deterministic)
+    for (int i = 1; i < n; ++i) {
+        Key k = keys[i];
+        int j = i - 1;
+        while (j >= 0 && (keys[j].d > k.d || (keys[j].d == k.d && keys[j].t > k.t))) {
+            keys[j + 1] = keys[j];
+            --j;
+        }
+        keys[j + 1] = k;
+    }
+    for (int t = 0; t < n; ++t) order[t] = keys[t].t;
+    delete[] keys;
+}
 int reduce_blocks() { return kReduceBlocks; }
 
 cudaError_t launch_begin(Launcher& L, const float* y, int R, SolveState* st, double* partials,
@@ -451,11 +540,12 @@ cudaError_t launch_begin(Launcher& L, const float* y, int R, SolveState* st, dou
 }
 
 cudaError_t launch_project(Launcher& L, const VolDev& vd, const float* vol_pad, int nch, int K,
-                           const RayGeom* rg, int nu, int nv, float* p, float* q, const float* y,
-                           SolveState* st, double* partials, unsigned int* counter, int phase,
-                           cudaGraphConditionalHandle h, int use_graph) {
-    ProjArgs A{vol_pad, vd, rg, nu, nv, K, p, q, y, st, partials, counter, phase, h, use_graph};
-    dim3 grid((nu + kTileU - 1) / kTileU, (nv + kTileV - 1) / kTileV);
+                           const RayGeom* rg, const int* order, int nu, int nv, float* p, float* q,
+                           const float* y, SolveState* st, double* partials, unsigned int* counter,
+                           int phase, cudaGraphConditionalHandle h, int use_graph) {
+    const int ntu = (nu + kTileU - 1) / kTileU, ntv = (nv + kTileV - 1) / kTileV;
+    ProjArgs A{vol_pad, vd, rg, order, nu, nv, K, ntu, p, q, y, st, partials, counter, phase, h, use_graph};
+    dim3 grid(ntu * ntv);
     switch (nch) {
         case 1: return L(k_project<1>, grid, dim3(kProjThreads), 0, A);
         case 4: return L(k_project<4>, grid, dim3(kProjThreads), 0, A);

@@ -11,6 +11,7 @@
 
 #include <map>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 #include "pcarecon.h"
@@ -66,6 +67,7 @@ struct Model {
     double* out = nullptr;    // 16 doubles: reduction outputs; [8..9] = (a, b)
     RayGeom* rg = nullptr;    // geometry of step-level calls
     int* steps = nullptr;
+    int* order = nullptr;           // projector tile order
     SolveState* st_host = nullptr;  // pinned
     size_t bytes = 0;
     // graph
@@ -176,7 +178,7 @@ void free_model(Model* m) {
     if (m->exec) cudaGraphExecDestroy(m->exec);
     if (m->graph) cudaGraphDestroy(m->graph);
     void* bufs[] = {m->f0p, m->mean, m->U, m->fh, m->fpad, m->p, m->q, m->y, m->r, m->flat, m->hbuf,
-                    m->partials, m->counter, m->st, m->wdev, m->out, m->rg, m->steps};
+                    m->partials, m->counter, m->st, m->wdev, m->out, m->rg, m->steps, m->order};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (m->st_host) cudaFreeHost(m->st_host);
@@ -210,6 +212,7 @@ int write_params(pr_ctx* c, Model* m, double angle, const pr_solve_opts* o) {
     prm.beta = o->beta;
     prm.grad_tol = o->grad_tol;
     prm.step0 = o->step0_mm;
+    prm.step_growth = o->step_growth;
     prm.tumor_tol = o->tumor_tol;
     prm.max_iters = o->max_iters;
     prm.max_bt = o->max_backtracks;
@@ -226,6 +229,7 @@ bool opts_ok(const pr_solve_opts* o) {
     return o->max_iters >= 0 && o->max_iters <= 100000 && o->max_backtracks >= 0 && o->max_backtracks <= 200 &&
            o->beta > 0 && o->beta < 1 && o->c1 >= 0 && o->c1 < 1 && o->step0_mm > 0 && o->grad_tol >= 0 &&
            o->tumor_max_iter >= 0 && o->tumor_max_iter <= 100000 && o->tumor_tol >= 0 &&
+           o->step_growth > 0 && o->step_growth <= 100 &&
            (o->loop_mode == PR_LOOP_GRAPH || o->loop_mode == PR_LOOP_HOST);
 }
 
@@ -240,7 +244,7 @@ int build_graph(pr_ctx* c, Model* m) {
     SolveState* st = m->st;
     CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
     CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
-    CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
+    CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseInit, m->hloop, 1));
     CK(launch_regrad(L, m->p, m->q, m->y, m->R, m->K, st, m->partials, m->counter, m->hloop, 1));
     cudaGraphNodeParams cp = {};
@@ -253,7 +257,7 @@ int build_graph(pr_ctx* c, Model* m) {
     Launcher B;
     B.graph = cp.conditional.phGraph_out[0];
     CK(launch_warp(B, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
-    CK(launch_project(B, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
+    CK(launch_project(B, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseTrial, m->hloop, 1));
     CK(launch_regrad(B, m->p, m->q, m->y, m->R, m->K, st, m->partials, m->counter, m->hloop, 1));
     L.last = cond;
@@ -270,7 +274,7 @@ int host_loop(pr_ctx* c, Model* m, int opt_max_iters, int opt_max_bt) {
     SolveState* st = m->st;
     CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
     CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
-    CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
+    CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseInit, 0, 0));
     CK(launch_regrad(L, m->p, m->q, m->y, m->R, m->K, st, m->partials, m->counter, 0, 0));
     long long guard = 0, bound = (long long)(opt_max_iters + 1) * (opt_max_bt + 1) + 2;
@@ -280,7 +284,7 @@ int host_loop(pr_ctx* c, Model* m, int opt_max_iters, int opt_max_bt) {
         if (!m->st_host->running) break;
         if (++guard > bound) return fail(PR_ETIMEOUT, "host loop exceeded its trial bound");
         CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
-        CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->geom.nu, m->geom.nv, m->p, m->q, m->y,
+        CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y,
                           st, m->partials, m->counter, kPhaseTrial, 0, 0));
         CK(launch_regrad(L, m->p, m->q, m->y, m->R, m->K, st, m->partials, m->counter, 0, 0));
     }
@@ -383,6 +387,7 @@ void pr_default_opts(pr_solve_opts* o) {
     o->loop_mode = PR_LOOP_GRAPH;
     o->tumor_tol = 1e-6;
     o->tumor_max_iter = 100;
+    o->step_growth = 1.25;
 }
 
 int pr_create(pr_ctx** out, int device, void* stream, size_t hbm_budget_bytes) {
@@ -475,6 +480,7 @@ int pr_load_model(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
     A(&m->out, 16 * 8);
     A(&m->rg, sizeof(RayGeom));
     A(&m->steps, 16);
+    A(&m->order, (size_t)project_blocks(geom->nu, geom->nv) * sizeof(int));
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&m->st_host, sizeof(SolveState), cudaHostAllocDefault);
     if (e != cudaSuccess) {
         free_model(m);
@@ -492,6 +498,7 @@ int pr_load_model(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
     int rc = PR_OK;
     cudaMemcpyKind kind = location == PR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     cudaStream_t s = c->stream;
+    std::vector<int> order_host((size_t)project_blocks(geom->nu, geom->nv));  // lives until the sync below
     do {
         if ((e = cudaMemsetAsync(m->f0p, 0, np * ts, s))) break;
         if ((e = cudaMemsetAsync(m->fh, 0, np * m->nch * 4, s))) break;
@@ -500,6 +507,10 @@ int pr_load_model(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
         if ((e = cudaMemsetAsync(m->counter, 0, 64, s))) break;
         if ((e = cudaMemsetAsync(m->st, 0, sizeof(SolveState), s))) break;
         if ((e = cudaMemcpyAsync(m->mean, mean_dvf, 3 * n * 4, kind, s))) break;
+        project_tile_order(geom->nu, geom->nv, order_host.data());
+        if ((e = cudaMemcpyAsync(m->order, order_host.data(), order_host.size() * sizeof(int),
+                                 cudaMemcpyHostToDevice, s)))
+            break;
         // f0 -> padded float32 (fpad as staging), then to storage type.
         if ((e = cudaMemcpyAsync(m->flat, f0, n * 4, kind, s))) break;
         Launcher L;
@@ -636,7 +647,7 @@ int pr_project(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom, do
     L.stream = c->stream;
     CK(cudaMemsetAsync(c->pad, 0, np * 4, c->stream));
     CK(launch_pad(L, vd, f_dev, c->pad));
-    CK(launch_project(L, vd, c->pad, 1, 0, c->rg, geom->nu, geom->nv, p_dev, nullptr, nullptr, nullptr, nullptr,
+    CK(launch_project(L, vd, c->pad, 1, 0, c->rg, nullptr, geom->nu, geom->nv, p_dev, nullptr, nullptr, nullptr, nullptr,
                       nullptr, kPhaseNone, 0, 0));
     CK(cudaStreamSynchronize(c->stream));
     return PR_OK;
@@ -665,7 +676,7 @@ int pr_forward(pr_ctx* c, int id, const double* w, double angle, float* p_dev) {
     Launcher L;
     L.stream = c->stream;
     CK(launch_warp(L, m->md, m->wdev, kWarpFPad, m->fpad, nullptr, nullptr));
-    CK(launch_project(L, m->md.vd, m->fpad, 1, 0, m->rg, m->geom.nu, m->geom.nv, p_dev, nullptr, nullptr, nullptr,
+    CK(launch_project(L, m->md.vd, m->fpad, 1, 0, m->rg, m->order, m->geom.nu, m->geom.nv, p_dev, nullptr, nullptr, nullptr,
                       nullptr, nullptr, kPhaseNone, 0, 0));
     CK(cudaStreamSynchronize(c->stream));
     return PR_OK;
@@ -704,7 +715,7 @@ int pr_cost_grad(pr_ctx* c, int id, const float* y_dev, double angle, const doub
     double res[8] = {0};
     if (mode == 0) {
         CK(launch_warp(L, m->md, m->wdev, kWarpFH, m->fh, nullptr, nullptr));
-        CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, nu, nv, m->p, m->q, nullptr, nullptr, nullptr,
+        CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, m->order, nu, nv, m->p, m->q, nullptr, nullptr, nullptr,
                           nullptr, kPhaseNone, 0, 0));
         CK(launch_cost_grad(L, m->p, m->q, y_dev, m->R, m->K, m->out + 8, m->partials, m->counter, m->out));
         CK(cudaMemcpyAsync(res, m->out, sizeof(double) * (1 + m->K), cudaMemcpyDeviceToHost, c->stream));
@@ -712,7 +723,7 @@ int pr_cost_grad(pr_ctx* c, int id, const float* y_dev, double angle, const doub
         TRY(ensure_hbuf(m));
         CK(launch_warp(L, m->md, m->wdev, kWarpFPad, m->fpad, nullptr, nullptr));
         CK(launch_warp(L, m->md, m->wdev, kWarpFlatFH, nullptr, nullptr, m->hbuf));
-        CK(launch_project(L, m->md.vd, m->fpad, 1, 0, m->rg, nu, nv, m->p, nullptr, nullptr, nullptr, nullptr,
+        CK(launch_project(L, m->md.vd, m->fpad, 1, 0, m->rg, m->order, nu, nv, m->p, nullptr, nullptr, nullptr, nullptr,
                           nullptr, kPhaseNone, 0, 0));
         CK(launch_cost_grad(L, m->p, nullptr, y_dev, m->R, 0, m->out + 8, m->partials, m->counter, m->out));
         CK(launch_residual(L, m->p, y_dev, m->R, m->out + 8, m->r));
@@ -761,7 +772,7 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
     CK(launch_warp(L, m->md, m->st->w, kWarpFH, m->fh, nullptr, nullptr));
     CK(launch_warp(L, m->md, m->st->w, kWarpFPad, m->fpad, nullptr, nullptr));
     if (which == PR_KERNEL_BACKPROJECT) CK(launch_warp(L, m->md, m->st->w, kWarpFlatFH, nullptr, nullptr, m->hbuf));
-    CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, nu, nv, m->p, m->q, nullptr, nullptr, nullptr, nullptr,
+    CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, m->order, nu, nv, m->p, m->q, nullptr, nullptr, nullptr, nullptr,
                       kPhaseNone, 0, 0));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -771,7 +782,7 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
         switch (which) {
             case PR_KERNEL_WARP_FH: err = launch_warp(L, m->md, m->st->w, kWarpFH, m->fh, nullptr, nullptr); break;
             case PR_KERNEL_PROJECT_FH:
-                err = launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, nu, nv, m->p, m->q, nullptr, nullptr,
+                err = launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, m->order, nu, nv, m->p, m->q, nullptr, nullptr,
                                      nullptr, nullptr, kPhaseNone, 0, 0);
                 break;
             case PR_KERNEL_REGRAD:
@@ -783,7 +794,7 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
                 break;
             case PR_KERNEL_WARP_F: err = launch_warp(L, m->md, m->st->w, kWarpFPad, m->fpad, nullptr, nullptr); break;
             case PR_KERNEL_PROJECT_F:
-                err = launch_project(L, m->md.vd, m->fpad, 1, 0, m->rg, nu, nv, m->r, nullptr, nullptr, nullptr,
+                err = launch_project(L, m->md.vd, m->fpad, 1, 0, m->rg, m->order, nu, nv, m->r, nullptr, nullptr, nullptr,
                                      nullptr, nullptr, kPhaseNone, 0, 0);
                 break;
         }
