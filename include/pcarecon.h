@@ -101,7 +101,8 @@ typedef struct {
     double beta;         /* backtracking factor; default 0.5 */
     int max_backtracks;  /* default 20 */
     double step0_mm;     /* first trial step moves w by this many mm; default 1 */
-    int cold_start;      /* 1: start from w0; 0: start from the model's last accepted w */
+    int cold_start;      /* 1: start from w0 with a first trial step of step0_mm;
+                            0: start from the model's last accepted w and step */
     double w0[PR_MAX_K];
     int loop_mode;       /* PR_LOOP_GRAPH (on-device loop in a CUDA graph) or PR_LOOP_HOST */
     double tumor_tol;    /* fixed-point stop, mm; default 1e-6 */
@@ -123,6 +124,8 @@ typedef struct {
     int stop_reason;        /* PR_STOP_* */
     double tumor_xyz[3];    /* mm, Section 2.3 */
     int tumor_steps;
+    double mu;              /* last accepted line-search step; a warm-started solve's first
+                               trial is step_growth x this (0 = none yet) */
 } pr_result;
 
 /* Library version string (static storage). */
@@ -183,7 +186,9 @@ int pr_reconstruct_async(pr_ctx* ctx, int model_id, const float* y_dev, double a
 /* Wait for the model's last enqueued solve and copy its result to *out. */
 int pr_fetch_result(pr_ctx* ctx, int model_id, pr_result* out);
 
-/* Read / overwrite a model's warm-start coefficients (K doubles, host). */
+/* Read / overwrite a model's warm-start coefficients (K doubles, host).
+ * pr_set_state also forgets the warm-start step (the next solve's first
+ * trial moves w by step0_mm). */
 int pr_get_state(pr_ctx* ctx, int model_id, double* w);
 int pr_set_state(pr_ctx* ctx, int model_id, const double* w);
 

@@ -23,7 +23,10 @@ Readings of the paper where it is silent (the CUDA path uses the same):
     decrease J(w - mu g; a, b) <= J(w; a, b) - c1 mu |g|^2 with c1 = 1e-4,
     backtracking mu <- beta mu with beta = 0.5, at most 20 backtracks. The
     first trial step is mu = step0_mm / |g| (moves w by step0_mm), later ones
-    start from step_growth x the last accepted mu (step_growth = 1.25). No
+    start from step_growth x the last accepted mu (step_growth = 1.25); a
+    solve warm-started from the previous frame starts its first trial at
+    step_growth x that frame's last accepted mu, as its w starts from that
+    frame's w (Section 4 initialises each frame from the previous one). No
     accepted step: w is kept and the solve stops with stop reason "line
     search failed".
   * (a, b) before the first step 1: Eq. 4 at the starting w.
@@ -270,12 +273,15 @@ class SolveResult:
     stop_reason: int
     tumor: np.ndarray
     tumor_steps: int
+    mu: float  # last accepted step (the warm-start step of the next frame)
     history: list  # per accepted step: dict(J_after_step1, J_after_step2, mu, w)
 
 
-def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None) -> SolveResult:
+def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None,
+                mu_warm: float | None = None) -> SolveResult:
     """Section 2.2: alternate step 1 (Eq. 3, gradient step with Armijo's rule at
-    fixed a, b) and step 2 (Eq. 4, exact a, b at fixed w), then Section 2.3."""
+    fixed a, b) and step 2 (Eq. 4, exact a, b at fixed w), then Section 2.3.
+    mu_warm: the previous frame's last accepted step (None or 0 = cold)."""
     o = opts or SolveOptions()
     y = np.asarray(y, dtype=np.float64)
     w = np.array(w0, dtype=np.float64)
@@ -297,7 +303,12 @@ def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None) -> 
             stop = STOP_MAX_ITERS
             break
         # Step 1: w <- w - mu g, mu by backtracking from the initial trial.
-        mu = o.step0_mm / gn if mu_prev is None else o.step_growth * mu_prev
+        if mu_prev is not None:
+            mu = o.step_growth * mu_prev
+        elif mu_warm:
+            mu = o.step_growth * mu_warm
+        else:
+            mu = o.step0_mm / gn
         accepted = None
         for bt in range(o.max_backtracks + 1):
             trial = evaluate(model, geom, angle, w - mu * g)
@@ -318,5 +329,6 @@ def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None) -> 
         history.append(dict(J_step1=J_t, J_step2=J, mu=mu, w=w.copy()))
         n += 1
     p_t, steps = tumor(model.vol, model.mean, model.U, w, model.c0, o.tumor_tol, o.tumor_max_iter)
+    mu_last = mu_prev if mu_prev is not None else (mu_warm or 0.0)
     return SolveResult(w=w, a=a, b=b, J=J, grad=g, iters=n, backtracks=backtracks, stop_reason=stop,
-                       tumor=p_t, tumor_steps=steps, history=history)
+                       tumor=p_t, tumor_steps=steps, mu=mu_last, history=history)

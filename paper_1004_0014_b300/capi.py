@@ -84,7 +84,7 @@ class Result(ctypes.Structure):
                 ("grad_norm", ctypes.c_double), ("grad_norm0", ctypes.c_double),
                 ("iters", ctypes.c_int), ("trials", ctypes.c_int), ("backtracks", ctypes.c_int),
                 ("stop_reason", ctypes.c_int), ("tumor_xyz", ctypes.c_double * 3),
-                ("tumor_steps", ctypes.c_int)]
+                ("tumor_steps", ctypes.c_int), ("mu", ctypes.c_double)]
 
     def as_dict(self):
         K = self.K
@@ -92,7 +92,7 @@ class Result(ctypes.Structure):
                     grad=np.array(self.grad[:K]), grad_norm=self.grad_norm,
                     grad_norm0=self.grad_norm0, iters=self.iters, trials=self.trials,
                     backtracks=self.backtracks, stop_reason=self.stop_reason,
-                    tumor=np.array(self.tumor_xyz[:]), tumor_steps=self.tumor_steps)
+                    tumor=np.array(self.tumor_xyz[:]), tumor_steps=self.tumor_steps, mu=self.mu)
 
 
 _lib = None

@@ -83,6 +83,7 @@ struct SolveState {
     double tumor[3];
     int tumor_steps, pad_;
     long long cum_solves, cum_trials;  // since the model was loaded
+    double mu_warm;  // last accepted step, carried to the next warm-started solve (0 = none)
 };
 
 // ---------------------------------------------------------------------------

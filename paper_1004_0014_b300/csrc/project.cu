@@ -84,6 +84,7 @@ k_begin(const float* __restrict__ y, int R, SolveState* st, double* partials, un
         st->need_grad = 0;
         st->running = 1;
         st->cum_solves += 1;
+        if (st->prm.cold_start) st->mu_warm = 0.0;
     }
 }
 
@@ -91,36 +92,82 @@ k_begin(const float* __restrict__ y, int R, SolveState* st, double* partials, un
 // G2 projector
 // ---------------------------------------------------------------------------
 
-// Trilinear accumulation of one sample into acc[0..NCH).
+// Trilinear accumulation of one sample into acc[0..NCH) (1 or 8 channels).
+template <int NCH>
+__device__ __forceinline__ void accumulate(const float* __restrict__ vol, const VolDev& vd, const float q[3],
+                                           float (&acc)[NCH]);
+
+// Cell of a sample: integer corner index i (clamped to [-1, n-1]) and the
+// fraction t in [0, 1]. A point outside the support (-1, n) lands on the zero
+// border with t saturated to 0 or 1, so it contributes exactly zero.
+__device__ __forceinline__ int cell(float q, int n, float& t) {
+    int i = min(max(__float2int_rd(q), -1), n - 1);
+    t = __saturatef(q - (float)i);
+    return i;
+}
+
+// Sample accumulation that keeps the eight corners of the last trilinear cell
+// in registers: consecutive samples 1 mm apart often fall in the same 2-2.5 mm
+// cell, and then a lane that stays in its cell does not touch L1 for that
+// sample. Used for the 4-channel (f, h_1..h_3) volume, where the corners are
+// 32 registers; index arithmetic is 32-bit (volumes below 2^29 padded voxels).
+struct CellCache4 {
+    int base = -1;
+    float c[8][4];  // corners: index = dx + 2 dy + 4 dz
+
+    __device__ __forceinline__ void sample(const float* __restrict__ vol, const VolDev& vd, const float q[3],
+                                           float (&acc)[4]) {
+        float tx, ty, tz;
+        int ix = cell(q[0], vd.nx, tx), iy = cell(q[1], vd.ny, ty), iz = cell(q[2], vd.nz, tz);
+        int b = ((iz + 1) * vd.nyp + (iy + 1)) * vd.nxp + (ix + 1);
+        if (b != base) {
+            base = b;
+            const int plane = vd.nxp * vd.nyp;
+            const int off[4] = {0, vd.nxp, plane, plane + vd.nxp};
+            const float4* v4 = reinterpret_cast<const float4*>(vol);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float4 a0 = __ldg(v4 + b + off[k]), a1 = __ldg(v4 + b + off[k] + 1);
+                c[2 * k][0] = a0.x, c[2 * k][1] = a0.y, c[2 * k][2] = a0.z, c[2 * k][3] = a0.w;
+                c[2 * k + 1][0] = a1.x, c[2 * k + 1][1] = a1.y, c[2 * k + 1][2] = a1.z, c[2 * k + 1][3] = a1.w;
+            }
+        }
+        float wy0 = 1.0f - ty, wz0 = 1.0f - tz;
+        const float wyz[4] = {wy0 * wz0, ty * wz0, wy0 * tz, ty * tz};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float w0 = wyz[k] * (1.0f - tx), w1 = wyz[k] * tx;
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch)
+                acc[ch] = __fmaf_rn(w1, c[2 * k + 1][ch], __fmaf_rn(w0, c[2 * k][ch], acc[ch]));
+        }
+    }
+};
+
 template <int NCH>
 __device__ __forceinline__ void accumulate(const float* __restrict__ vol, const VolDev& vd, const float q[3],
                                            float (&acc)[NCH]) {
-    float qx = fminf(fmaxf(q[0], -1.0f), (float)vd.nx);
-    float qy = fminf(fmaxf(q[1], -1.0f), (float)vd.ny);
-    float qz = fminf(fmaxf(q[2], -1.0f), (float)vd.nz);
-    int ix = min((int)floorf(qx), vd.nx - 1);
-    int iy = min((int)floorf(qy), vd.ny - 1);
-    int iz = min((int)floorf(qz), vd.nz - 1);
-    float tx = qx - (float)ix, ty = qy - (float)iy, tz = qz - (float)iz;
-    long long base = ((long long)(iz + 1) * vd.nyp + (iy + 1)) * vd.nxp + (ix + 1);
-    const long long plane = (long long)vd.nxp * vd.nyp;
-    float wx0 = 1.0f - tx, wy0 = 1.0f - ty, wz0 = 1.0f - tz;
-    float w00 = wy0 * wz0, w10 = ty * wz0, w01 = wy0 * tz, w11 = ty * tz;
-    const long long off[4] = {0, (long long)vd.nxp, plane, plane + vd.nxp};
-    const float wyz[4] = {w00, w10, w01, w11};
+    float tx, ty, tz;
+    int ix = cell(q[0], vd.nx, tx), iy = cell(q[1], vd.ny, ty), iz = cell(q[2], vd.nz, tz);
+    int b = ((iz + 1) * vd.nyp + (iy + 1)) * vd.nxp + (ix + 1);
+    const int plane = vd.nxp * vd.nyp;
+    const int off[4] = {0, vd.nxp, plane, plane + vd.nxp};
+    float wy0 = 1.0f - ty, wz0 = 1.0f - tz;
+    const float wyz[4] = {wy0 * wz0, ty * wz0, wy0 * tz, ty * tz};
     if (NCH == 1) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const float* p = vol + base + off[c];
+        for (int k = 0; k < 4; ++k) {
+            const float* p = vol + b + off[k];
             float a0 = __ldg(p), a1 = __ldg(p + 1);
-            acc[0] = __fmaf_rn(wyz[c], __fmaf_rn(tx, a1 - a0, a0), acc[0]);
+            acc[0] = __fmaf_rn(wyz[k], __fmaf_rn(tx, a1 - a0, a0), acc[0]);
         }
     } else {
         constexpr int NV4 = NCH / 4;
+        const float4* v4 = reinterpret_cast<const float4*>(vol);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const float4* p = reinterpret_cast<const float4*>(vol + (base + off[c]) * NCH);
-            float w0 = wyz[c] * wx0, w1 = wyz[c] * tx;
+        for (int k = 0; k < 4; ++k) {
+            const float4* p = v4 + (size_t)(b + off[k]) * NV4;
+            float w0 = wyz[k] * (1.0f - tx), w1 = wyz[k] * tx;
 #pragma unroll
             for (int h = 0; h < NV4; ++h) {
                 float4 a0 = __ldg(p + h), a1 = __ldg(p + NV4 + h);
@@ -132,55 +179,6 @@ __device__ __forceinline__ void accumulate(const float* __restrict__ vol, const 
         }
     }
 }
-
-// Sample accumulation that keeps the eight corners of the last trilinear cell
-// in registers: consecutive samples 1 mm apart often fall in the same 2-2.5 mm
-// cell, and then no lane that stays in its cell touches L1 for that sample.
-// For 1 or 4 channels per voxel (8 or 32 corner registers).
-template <int NCH>
-struct CellCache {
-    static constexpr int NV = NCH == 1 ? 1 : 4;
-    long long base = -1;
-    float c[8][NV];  // corners: index = dx + 2 dy + 4 dz
-
-    __device__ __forceinline__ void sample(const float* __restrict__ vol, const VolDev& vd, const float q[3],
-                                           float (&acc)[NCH]) {
-        float qx = fminf(fmaxf(q[0], -1.0f), (float)vd.nx);
-        float qy = fminf(fmaxf(q[1], -1.0f), (float)vd.ny);
-        float qz = fminf(fmaxf(q[2], -1.0f), (float)vd.nz);
-        int ix = min((int)floorf(qx), vd.nx - 1);
-        int iy = min((int)floorf(qy), vd.ny - 1);
-        int iz = min((int)floorf(qz), vd.nz - 1);
-        float tx = qx - (float)ix, ty = qy - (float)iy, tz = qz - (float)iz;
-        long long b = ((long long)(iz + 1) * vd.nyp + (iy + 1)) * vd.nxp + (ix + 1);
-        if (b != base) {
-            base = b;
-            const long long plane = (long long)vd.nxp * vd.nyp;
-            const long long off[4] = {0, (long long)vd.nxp, plane, plane + vd.nxp};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (NCH == 1) {
-                    c[2 * k][0] = __ldg(vol + b + off[k]);
-                    c[2 * k + 1][0] = __ldg(vol + b + off[k] + 1);
-                } else {
-                    const float4* p4 = reinterpret_cast<const float4*>(vol + (b + off[k]) * 4);
-                    float4 a0 = __ldg(p4), a1 = __ldg(p4 + 1);
-                    c[2 * k][0] = a0.x, c[2 * k][1] = a0.y, c[2 * k][2] = a0.z, c[2 * k][3] = a0.w;
-                    c[2 * k + 1][0] = a1.x, c[2 * k + 1][1] = a1.y, c[2 * k + 1][2] = a1.z, c[2 * k + 1][3] = a1.w;
-                }
-            }
-        }
-        float wy0 = 1.0f - ty, wz0 = 1.0f - tz;
-        const float wyz[4] = {wy0 * wz0, ty * wz0, wy0 * tz, ty * tz};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float w0 = wyz[k] * (1.0f - tx), w1 = wyz[k] * tx;
-#pragma unroll
-            for (int ch = 0; ch < NV; ++ch)
-                acc[ch] = __fmaf_rn(w1, c[2 * k + 1][ch], __fmaf_rn(w0, c[2 * k][ch], acc[ch]));
-        }
-    }
-};
 
 struct ProjArgs {
     const float* vol;
@@ -234,6 +232,7 @@ __device__ void controller_project(SolveState* st, const double (&tot)[3], int p
         for (int k = 0; k < kMaxK; ++k)
             if (k < K) st->w[k] = st->wt[k];
         st->mu_prev = st->mu;
+        st->mu_warm = st->mu;
         st->iter += 1;
         st->accepted = 1;
         if (fit_ab(st, tot[1], tot[2], &a, &b)) {  // step 2, Eq. 4
@@ -288,8 +287,8 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs A) {
     float acc[NCH];
 #pragma unroll
     for (int c = 0; c < NCH; ++c) acc[c] = 0.0f;
-    if constexpr (NCH <= 4) {
-        CellCache<NCH> cache;
+    if constexpr (NCH == 4) {
+        CellCache4 cache;
         for (int s = s_lo; s <= s_hi; ++s) {
             float q[3];
             sample_pos(g, b, s, q);
@@ -390,7 +389,12 @@ k_regrad(const float* __restrict__ p, const float* __restrict__ q, const float* 
         set_loop(st, 0, h, use_graph);
         return;
     }
-    st->mu = st->iter == 0 ? st->prm.step0 / gn : st->prm.step_growth * st->mu_prev;
+    if (st->iter > 0)
+        st->mu = st->prm.step_growth * st->mu_prev;
+    else if (st->mu_warm > 0.0)  // warm start: the previous frame's last accepted step
+        st->mu = st->prm.step_growth * st->mu_warm;
+    else
+        st->mu = st->prm.step0 / gn;
     st->bt = 0;
     next_trial(st, K);
     set_loop(st, 1, h, use_graph);

@@ -95,9 +95,10 @@ namespace {
 
 size_t pad_voxels(const pr_volume_desc& v) { return (size_t)(v.nx + 2) * (v.ny + 2) * (v.nz + 2); }
 
+// Padded volumes are indexed with 32-bit arithmetic in the projector.
 bool vol_ok(const pr_volume_desc* v) {
     return v && v->nx >= 1 && v->ny >= 1 && v->nz >= 1 && v->dx > 0 && v->dy > 0 && v->dz > 0 &&
-           (double)v->nx * v->ny * v->nz < 2.0e9 && isfinite(v->dx) && isfinite(v->dy) && isfinite(v->dz);
+           (double)(v->nx + 2) * (v->ny + 2) * (v->nz + 2) < 536870912.0 && isfinite(v->dx) && isfinite(v->dy) && isfinite(v->dz);
 }
 
 bool geom_ok(const pr_geometry* g) {
@@ -310,6 +311,7 @@ void fill_result(const Model* m, const SolveState& s, pr_result* out) {
     out->stop_reason = s.stop;
     for (int c = 0; c < 3; ++c) out->tumor_xyz[c] = s.tumor[c];
     out->tumor_steps = s.tumor_steps;
+    out->mu = s.mu_warm;
 }
 
 int enqueue_solve(pr_ctx* c, Model* m, double angle, const pr_solve_opts* opts) {
@@ -612,6 +614,7 @@ int pr_set_state(pr_ctx* c, int id, const double* w) {
         buf[k] = w[k];
     }
     CK(cudaMemcpyAsync(m->st->w, buf, sizeof buf, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(&m->st->mu_warm, 0, sizeof(double), c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return PR_OK;
 }

@@ -310,3 +310,26 @@ def test_invalid_arguments_are_rejected(ctx, small):
                              np.zeros((3,) + vol.shape, np.float32), z, np.zeros(3))
     assert e.value.code == -3
     small_ctx.close()
+
+
+def test_warm_started_frames_match_oracle(ctx, small):
+    # Two frames at different angles: the second starts from the first's w and
+    # last accepted step, on the GPU (model state) and in the oracle (arguments).
+    om, geom, vol = small["om"], small["geom"], small["vol"]
+    from phantom import dvf_analytic
+
+    angles = (0.3, 0.32)
+    ys = []
+    for i, th in enumerate(angles):
+        ft = O.warp(vol, om.f0, dvf_analytic(vol, 1.0 + i / 6.0, 1.5))
+        ys.append(_f32(noisy(O.project(vol, geom, th, ft), 10 + i)))
+    a = ctx.reconstruct(small["mid"], ys[0], angles[0], _opts(max_iters=6, cold_start=1, w0=[0, 0, 0]))
+    b = ctx.reconstruct(small["mid"], ys[1], angles[1], _opts(max_iters=6))
+    oa = O.reconstruct(om, geom, angles[0], _up(ys[0]), np.zeros(3), O.SolveOptions(max_iters=6))
+    ob = O.reconstruct(om, geom, angles[1], _up(ys[1]), oa.w, O.SolveOptions(max_iters=6), mu_warm=oa.mu)
+    report("warm_frames64", w_rel=rel(b["w"], ob.w), mu_rel=abs(b["mu"] - ob.mu) / ob.mu,
+           backtracks=b["backtracks"], oracle_backtracks=ob.backtracks)
+    assert abs(a["mu"] - oa.mu) / oa.mu < 1e-6
+    assert b["backtracks"] == ob.backtracks
+    assert rel(b["w"], ob.w) < TOL_W
+    assert abs(b["J"] - ob.J) / ob.J < TOL_PROJ
