@@ -329,7 +329,9 @@ def test_warm_started_frames_match_oracle(ctx, small):
     ob = O.reconstruct(om, geom, angles[1], _up(ys[1]), oa.w, O.SolveOptions(max_iters=6), mu_warm=oa.mu)
     report("warm_frames64", w_rel=rel(b["w"], ob.w), mu_rel=abs(b["mu"] - ob.mu) / ob.mu,
            backtracks=b["backtracks"], oracle_backtracks=ob.backtracks)
-    assert abs(a["mu"] - oa.mu) / oa.mu < 1e-6
+    # the step is step0 / |grad J| times powers of beta and step_growth, so it
+    # carries the gradient's tolerance
+    assert abs(a["mu"] - oa.mu) / oa.mu < TOL_GRAD
     assert b["backtracks"] == ob.backtracks
     assert rel(b["w"], ob.w) < TOL_W
     assert abs(b["J"] - ob.J) / ob.J < TOL_PROJ
