@@ -237,6 +237,32 @@ int pr_cost_grad(pr_ctx* ctx, int model_id, const float* y_dev, double angle_rad
 int pr_tumor(pr_ctx* ctx, int model_id, const double* w, double tol, int max_iter, double* xyz,
              int* steps);
 
+/* ---- allocation-free cost and gradient (no counterpart in the paper) ----
+ *
+ * For callers that cannot allocate device memory while they run: a real-time
+ * guidance loop that reserves all of its memory at start-up (a cudaMalloc can
+ * synchronise the device and stall a frame), an application whose device
+ * memory belongs to another allocator, or code where allocating is not
+ * allowed at all. It computes, from projections the caller already has,
+ *   out_dev[0]   = J = sum over pixels of (p - a y - b)^2             (Eq. 2)
+ *   out_dev[1+k] = dJ/dw_k = 2 sum over pixels of (p - a y - b) q_k   (the
+ *                  gradient after Eq. 4 in forward form, q_k = P h_k)
+ * with p_dev [R], q_dev [K][R], y_dev [R] float32 and out_dev [1 + K] double,
+ * all device memory of `device`, enqueued on `stream` (a cudaStream_t; NULL =
+ * the legacy default stream) without a host synchronisation. It needs no
+ * pr_ctx and allocates nothing: its scratch (block sums, a completion counter
+ * and the outputs, 49,552 bytes) is one fixed array in the library that every
+ * GPU which loads the library holds until the process exits. Limits: 1 <= K <=
+ * PR_MAX_K (the array holds 1 + 7 sums per block), R >= 1; larger K is
+ * rejected with PR_EINVAL. The first call on a device looks up that array's
+ * device address (one-time set-up); make that first call before any stream
+ * capture. All calls on a device share the array: calls whose work can
+ * overlap on the GPU (different streams without ordering) race and give
+ * wrong results; calls on one stream are safe. Errors: PR_EINVAL, PR_ECUDA,
+ * with pr_last_error(). */
+int pr_cost_grad_static(int device, void* stream, const float* p_dev, const float* q_dev, const float* y_dev,
+                        int R, int K, double a, double b, double* out_dev);
+
 /* ---- measurement (no counterpart in the paper; used by benchmarks) ---- */
 
 /* Kernels pr_time_kernel can time. */

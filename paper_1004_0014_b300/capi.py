@@ -41,7 +41,7 @@ EXPORTED = [
     "pr_release_model", "pr_model_footprint", "pr_reconstruct", "pr_reconstruct_async",
     "pr_fetch_result", "pr_get_state", "pr_set_state", "pr_warp", "pr_project", "pr_backproject",
     "pr_forward", "pr_vjp", "pr_cost_grad", "pr_tumor", "pr_time_kernel", "pr_model_stats",
-    "pr_io_bytes",
+    "pr_io_bytes", "pr_cost_grad_static",
 ]
 
 PR_KERNEL_WARP_FH, PR_KERNEL_PROJECT_FH, PR_KERNEL_REGRAD = 0, 1, 2
@@ -137,6 +137,7 @@ def load_library(path: str | None = None):
         "pr_time_kernel": (_I, [_P, _I, _I, _D, _I, _DP]),
         "pr_model_stats": (_I, [_P, _I, ctypes.POINTER(Stats)]),
         "pr_io_bytes": (_I, [_P, _I, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+        "pr_cost_grad_static": (_I, [_I, _P, _P, _P, _P, _I, _I, _D, _D, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -348,3 +349,13 @@ def pr_io_bytes(ctx, model_id: int):
     a, b = ctypes.c_size_t(), ctypes.c_size_t()
     _check(_lib.pr_io_bytes(ctx, int(model_id), ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def pr_cost_grad_static(device: int, stream, p_dev, q_dev, y_dev, R: int, K: int, a: float, b: float, out_dev):
+    """Allocation-free cost and gradient from projections (see include/pcarecon.h).
+    stream: a cudaStream_t handle (int) or None; all buffers are CUDA tensors."""
+    load_library()
+    s = ctypes.c_void_p(stream) if stream else None
+    _check(_lib.pr_cost_grad_static(int(device), s, _dev(p_dev, "p_dev"), _dev(q_dev, "q_dev"),
+                                    _dev(y_dev, "y_dev"), int(R), int(K), float(a), float(b),
+                                    _dev(out_dev, "out_dev")))

@@ -83,6 +83,9 @@ cudaError_t launch_backproject(Launcher& L, const VolDev& vd, const RayGeom* rg,
                                float* g_flat, const float* h, int K, double* partials,
                                unsigned int* counter, double* out);
 
+// Record msg as the calling thread's pr_last_error() text; returns code.
+int set_last_error(int code, const char* msg);
+
 // Number of blocks the reductions use (size of the partials buffer rows).
 int project_blocks(int nu, int nv);
 int reduce_blocks();

@@ -79,6 +79,8 @@ struct Model {
 
 }  // namespace
 
+int pr::set_last_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 struct pr_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
