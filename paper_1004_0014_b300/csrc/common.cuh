@@ -54,6 +54,37 @@ struct RayGeom {
     float sp[3];      // voxel spacing, mm
 };
 
+// Where a model's warped volume can be nonzero (computed once at load). The
+// warped f and h at voxel v are nonzero only if the pull-back point v + x(v)
+// lies within one cell of a nonzero voxel of f0, so |v_c - u_c| < 1 + |x_c|/dx_c
+// for some nonzero f0 voxel u, and |x_c| <= max|mean_c| + sum_k |w_k| max|u_kc|.
+// A ray sample can be nonzero only one cell further out. Samples outside that
+// box are exact zeros, so clipping rays to it changes no sum.
+struct Support {
+    int lo[3], hi[3];                  // index box of the nonzero f0 voxels (lo > hi: f0 == 0)
+    unsigned int mean_max[3];          // bits of max |mean_c| (non-negative floats order as uints)
+    unsigned int u_max[kMaxK][3];      // bits of max |u_kc|
+};
+
+// Sample box (index space) of a ray march over the warped volume at
+// coefficients w; returns false when the volume is zero everywhere.
+__device__ __forceinline__ bool support_box(const Support& s, const VolDev& vd, const double* w, int K,
+                                            float lo[3], float hi[3]) {
+    const float inv[3] = {vd.inv_dx, vd.inv_dy, vd.inv_dz};
+    const float n[3] = {(float)vd.nx, (float)vd.ny, (float)vd.nz};
+    bool any = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float d = __uint_as_float(s.mean_max[c]);
+        for (int k = 0; k < K; ++k) d += (float)fabs(w[k]) * __uint_as_float(s.u_max[k][c]);
+        d = d * inv[c] * 1.01f + 0.01f;  // margin for float rounding of x and of the bounds
+        lo[c] = fmaxf(-1.0f, (float)s.lo[c] - 2.0f - d);
+        hi[c] = fminf(n[c], (float)s.hi[c] + 2.0f + d);
+        any = any && (s.lo[c] <= s.hi[c]) && (lo[c] < hi[c]);
+    }
+    return any;
+}
+
 // Solver phases handled by the controller in the last block of a reduction.
 enum Phase : int {
     kPhaseNone = 0,   // plain projection, no reduction

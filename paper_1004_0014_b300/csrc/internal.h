@@ -47,11 +47,25 @@ cudaError_t launch_begin(Launcher& L, const float* y, int R, SolveState* st, dou
 // (1 = planar f, 4 or 8 = interleaved f, h). rg: device RayGeom. p: [R];
 // q: [K][R] (channels 1..K, nullable). For phase != kPhaseNone, y, st,
 // partials and counter drive the fused reduction and the controller.
+// Optional clipping of the ray march to the support of a model's warped
+// volume: sup (device) and the coefficients w (device, K doubles) it was warped at.
+struct SupportRef {
+    const Support* sup = nullptr;
+    const double* w = nullptr;
+    int K = 0;
+};
+
 // order: device permutation of the detector tiles (nullable), see project_tile_order.
 cudaError_t launch_project(Launcher& L, const VolDev& vd, const float* vol_pad, int nch, int K,
                            const RayGeom* rg, const int* order, int nu, int nv, float* p, float* q,
                            const float* y, SolveState* st, double* partials, unsigned int* counter,
-                           int phase, cudaGraphConditionalHandle h, int use_graph);
+                           int phase, cudaGraphConditionalHandle h, int use_graph, SupportRef sup = {});
+
+// Support of f0 and the largest |mean_c|, |u_kc| into sup (device); f0, mean, U
+// float32 unpadded (U may be one plane at a time: plane index k*3 + c).
+cudaError_t launch_support_init(Launcher& L, Support* sup);
+cudaError_t launch_support_box(Launcher& L, const VolDev& vd, const float* f0, Support* sup);
+cudaError_t launch_maxabs(Launcher& L, const float* x, long long n, unsigned int* out);
 
 // Host: the projector's tile launch order for an nu x nv detector (project_blocks ints).
 void project_tile_order(int nu, int nv, int* order);

@@ -196,6 +196,7 @@ struct ProjArgs {
     int phase;
     cudaGraphConditionalHandle h;
     int use_graph;
+    SupportRef sup;
 };
 
 __device__ void controller_project(SolveState* st, const double (&tot)[3], int phase,
@@ -257,8 +258,10 @@ __device__ void controller_project(SolveState* st, const double (&tot)[3], int p
     next_trial(st, K);
 }
 
+// Four 256-thread blocks per SM for the (f, h) volume (at most 64 registers):
+// the march is issue-bound and needs the resident warps to hide L1 latency.
 template <int NCH>
-__global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs A) {
+__global__ void __launch_bounds__(kProjThreads, NCH == 4 ? 4 : 1) k_project(ProjArgs A) {
     const RayGeom g = *A.rg;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int tile = A.order ? __ldg(A.order + blockIdx.x) : (int)blockIdx.x;
@@ -270,10 +273,12 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs A) {
 
     float b[3];
     ray_dir_index(g, valid ? iu : 0, valid ? iv : 0, b);
-    const float lo[3] = {-1.0f, -1.0f, -1.0f};
+    float lo[3] = {-1.0f, -1.0f, -1.0f}, hi[3] = {g.nmax[0], g.nmax[1], g.nmax[2]};
+    bool nonzero = true;
+    if (A.sup.sup && A.sup.w) nonzero = support_box(*A.sup.sup, A.vd, A.sup.w, A.sup.K, lo, hi);
     float t0, t1;
     int s_lo = 0x7fffffff, s_hi = -1;
-    if (valid && ray_box(g.a, b, lo, g.nmax, t0, t1)) {
+    if (valid && nonzero && ray_box(g.a, b, lo, hi, t0, t1)) {
         // t0, t1 are bounded by the box; the clamps only keep the int
         // conversion and the loop counter far from overflow.
         s_lo = (int)fminf(fmaxf(ceilf(t0 / g.ds - 0.5f), 0.0f), (float)kMaxSamples);
@@ -343,16 +348,22 @@ k_regrad(const float* __restrict__ p, const float* __restrict__ q, const float* 
          int use_graph) {
     if (!st->need_grad) return;
     const double a = st->a, b = st->b;
-    double v[8];
+    // The residual p - a y - b cancels, so it is formed in FP64; its square and
+    // its products with q_k are FP32 (each thread sums a few rays), and the
+    // sums over threads and blocks are FP64 (B300's FP64 rate is low).
+    float vf[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = 0.0;
+    for (int m = 0; m < 8; ++m) vf[m] = 0.0f;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
-        double res = (double)p[r] - a * (double)y[r] - b;
-        v[0] += res * res;
+        float res = (float)((double)p[r] - fma(a, (double)y[r], b));
+        vf[0] = __fmaf_rn(res, res, vf[0]);
 #pragma unroll
         for (int k = 0; k < kMaxK; ++k)
-            if (k < K) v[1 + k] += res * (double)q[(long long)k * R + r];
+            if (k < K) vf[1 + k] = __fmaf_rn(res, q[(long long)k * R + r], vf[1 + k]);
     }
+    double v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = vf[m];
     block_sum<8>(v);
     if (!publish_partials<8>(v, partials, blockIdx.x, gridDim.x, counter)) return;
     double tot[8];
@@ -431,44 +442,17 @@ k_cost_grad(const float* __restrict__ p, const float* __restrict__ q, const floa
 // DVF (Chen et al.), evaluated at the single point c0: p <- c0 - x(p), with x
 // = mean + U w trilinearly interpolated and clamped to the grid edge. FP64.
 // ---------------------------------------------------------------------------
-template <typename TS>
-__device__ void dvf_at(const float* mean, const TS* U, const VolDev& vd, int K, const double* w,
-                       const double p[3], double out[3]) {
-    const double sp[3] = {(double)vd.dx, (double)vd.dy, (double)vd.dz};
-    const int nn[3] = {vd.nx, vd.ny, vd.nz};
-    int i0[3];
-    double t[3];
-    for (int c = 0; c < 3; ++c) {
-        double o = -0.5 * (nn[c] - 1) * sp[c];
-        double q = (p[c] - o) / sp[c];
-        q = fmin(fmax(q, 0.0), (double)(nn[c] - 1));
-        int i = (int)floor(q);
-        i = max(0, min(i, nn[c] - 2));
-        i0[c] = i;
-        t[c] = q - i;
-    }
-    for (int comp = 0; comp < 3; ++comp) {
-        double acc = 0.0;
-        for (int cz = 0; cz < 2; ++cz)
-            for (int cy = 0; cy < 2; ++cy)
-                for (int cx = 0; cx < 2; ++cx) {
-                    int i = i0[0] + cx, j = i0[1] + cy, k = i0[2] + cz;
-                    if (i >= vd.nx || j >= vd.ny || k >= vd.nz) continue;
-                    long long e = (long long)comp * vd.n + ((long long)k * vd.ny + j) * vd.nx + i;
-                    double xv = mean[e];
-                    for (int m = 0; m < K; ++m) xv += (double)ld_val(U + 3LL * m * vd.n + e) * w[m];
-                    double wt = (cx ? t[0] : 1.0 - t[0]) * (cy ? t[1] : 1.0 - t[1]) * (cz ? t[2] : 1.0 - t[2]);
-                    acc += wt * xv;
-                }
-        out[comp] = acc;
-    }
-}
-
+// One warp: lanes 0..23 each take one (corner, component) pair of the eight
+// trilinear corners and three DVF components, so a fixed-point step costs one
+// round of loads instead of 24 dependent ones. Lane 0's sums are broadcast,
+// so every lane follows the same iterate.
 template <typename TS>
 __global__ void k_tumor(const float* mean, const TS* U, VolDev vd, int K, const double* w, double c0x,
                         double c0y, double c0z, double tol, int max_iter, const SolveParams* prm,
                         double* xyz, int* steps) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (blockIdx.x != 0) return;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x >= 32) return;
     if (prm) {  // per-solve options of an on-device solve
         tol = prm->tumor_tol;
         max_iter = prm->tumor_max_iter;
@@ -476,11 +460,40 @@ __global__ void k_tumor(const float* mean, const TS* U, VolDev vd, int K, const 
     double wl[kMaxK];
     for (int k = 0; k < kMaxK; ++k) wl[k] = k < K ? w[k] : 0.0;
     const double c0[3] = {c0x, c0y, c0z};
+    const double sp[3] = {(double)vd.dx, (double)vd.dy, (double)vd.dz};
+    const int nn[3] = {vd.nx, vd.ny, vd.nz};
+    const int corner = lane / 3, comp = lane % 3;
     double cur[3] = {c0x, c0y, c0z};
     int it = 0;
     while (it < max_iter) {
+        // cell and fractions of the current point (clamped to the grid edge)
+        int i0[3];
+        double t[3];
+        for (int c = 0; c < 3; ++c) {
+            double o = -0.5 * (nn[c] - 1) * sp[c];
+            double q = fmin(fmax((cur[c] - o) / sp[c], 0.0), (double)(nn[c] - 1));
+            int i = max(0, min((int)floor(q), nn[c] - 2));
+            i0[c] = i;
+            t[c] = q - i;
+        }
+        double contrib = 0.0;
+        if (lane < 24) {
+            int cx = corner & 1, cy = (corner >> 1) & 1, cz = corner >> 2;
+            int i = i0[0] + cx, j = i0[1] + cy, k = i0[2] + cz;
+            if (i < vd.nx && j < vd.ny && k < vd.nz) {
+                long long e = (long long)comp * vd.n + ((long long)k * vd.ny + j) * vd.nx + i;
+                double xv = mean[e];
+                for (int m = 0; m < K; ++m) xv += (double)ld_val(U + 3LL * m * vd.n + e) * wl[m];
+                double wt = (cx ? t[0] : 1.0 - t[0]) * (cy ? t[1] : 1.0 - t[1]) * (cz ? t[2] : 1.0 - t[2]);
+                contrib = wt * xv;
+            }
+        }
         double x[3];
-        dvf_at<TS>(mean, U, vd, K, wl, cur, x);
+        for (int c = 0; c < 3; ++c) {
+            double v = (lane < 24 && comp == c) ? contrib : 0.0;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            x[c] = __shfl_sync(0xffffffffu, v, 0);
+        }
         double d2 = 0.0;
         for (int c = 0; c < 3; ++c) {
             double nx = c0[c] - x[c];
@@ -490,10 +503,12 @@ __global__ void k_tumor(const float* mean, const TS* U, VolDev vd, int K, const 
         ++it;
         if (sqrt(d2) < tol) break;
     }
-    xyz[0] = cur[0];
-    xyz[1] = cur[1];
-    xyz[2] = cur[2];
-    *steps = it;
+    if (lane == 0) {
+        xyz[0] = cur[0];
+        xyz[1] = cur[1];
+        xyz[2] = cur[2];
+        *steps = it;
+    }
 }
 
 // r = p - a y - b (ab[0] = a, ab[1] = b), the residual of Eq. 2.
@@ -546,9 +561,9 @@ cudaError_t launch_begin(Launcher& L, const float* y, int R, SolveState* st, dou
 cudaError_t launch_project(Launcher& L, const VolDev& vd, const float* vol_pad, int nch, int K,
                            const RayGeom* rg, const int* order, int nu, int nv, float* p, float* q,
                            const float* y, SolveState* st, double* partials, unsigned int* counter,
-                           int phase, cudaGraphConditionalHandle h, int use_graph) {
+                           int phase, cudaGraphConditionalHandle h, int use_graph, SupportRef sup) {
     const int ntu = (nu + kTileU - 1) / kTileU, ntv = (nv + kTileV - 1) / kTileV;
-    ProjArgs A{vol_pad, vd, rg, order, nu, nv, K, ntu, p, q, y, st, partials, counter, phase, h, use_graph};
+    ProjArgs A{vol_pad, vd, rg, order, nu, nv, K, ntu, p, q, y, st, partials, counter, phase, h, use_graph, sup};
     dim3 grid(ntu * ntv);
     switch (nch) {
         case 1: return L(k_project<1>, grid, dim3(kProjThreads), 0, A);
@@ -579,6 +594,67 @@ cudaError_t launch_tumor(Launcher& L, const ModelDev& m, const double* w_dev, do
                  max_iter, prm, xyz_out, steps_out);
     return L(k_tumor<float>, dim3(1), dim3(32), 0, m.mean, static_cast<const float*>(m.U), m.vd, m.K, w_dev,
              m.c0[0], m.c0[1], m.c0[2], tol, max_iter, prm, xyz_out, steps_out);
+}
+
+// ---------------------------------------------------------------------------
+// Support of a model (once at load)
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void k_support_init(Support* s) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        for (int c = 0; c < 3; ++c) {
+            s->lo[c] = 0x7fffffff;
+            s->hi[c] = -0x7fffffff;
+            s->mean_max[c] = 0u;
+            for (int k = 0; k < kMaxK; ++k) s->u_max[k][c] = 0u;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_support_box(VolDev vd, const float* __restrict__ f0, Support* s) {
+    int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, hi[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < vd.n;
+         v += (long long)gridDim.x * blockDim.x) {
+        if (f0[v] != 0.0f) {
+            long long jk = v / vd.nx;
+            int idx[3] = {(int)(v - jk * vd.nx), (int)(jk % vd.ny), (int)(jk / vd.ny)};
+            for (int c = 0; c < 3; ++c) {
+                lo[c] = min(lo[c], idx[c]);
+                hi[c] = max(hi[c], idx[c]);
+            }
+        }
+    }
+    for (int c = 0; c < 3; ++c) {
+        int a = __reduce_min_sync(0xffffffffu, lo[c]), b = __reduce_max_sync(0xffffffffu, hi[c]);
+        if ((threadIdx.x & 31) == 0 && a <= b) {
+            atomicMin(&s->lo[c], a);
+            atomicMax(&s->hi[c], b);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_maxabs(const float* __restrict__ x, long long n, unsigned int* out) {
+    unsigned int m = 0u;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float a = fabsf(x[i]);
+        if (!(a <= 3.0e38f)) a = 3.0e38f;  // non-finite: the bound becomes huge, the box the whole grid
+        m = max(m, __float_as_uint(a));
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+}  // namespace
+
+cudaError_t launch_support_init(Launcher& L, Support* sup) { return L(k_support_init, dim3(1), dim3(32), 0, sup); }
+
+cudaError_t launch_support_box(Launcher& L, const VolDev& vd, const float* f0, Support* sup) {
+    return L(k_support_box, dim3(1184), dim3(256), 0, vd, f0, sup);
+}
+
+cudaError_t launch_maxabs(Launcher& L, const float* x, long long n, unsigned int* out) {
+    return L(k_maxabs, dim3(1184), dim3(256), 0, x, n, out);
 }
 
 }  // namespace pr

@@ -68,6 +68,7 @@ struct Model {
     RayGeom* rg = nullptr;    // geometry of step-level calls
     int* steps = nullptr;
     int* order = nullptr;           // projector tile order
+    Support* sup = nullptr;         // where the warped volume can be nonzero
     SolveState* st_host = nullptr;  // pinned
     size_t bytes = 0;
     // graph
@@ -181,7 +182,7 @@ void free_model(Model* m) {
     if (m->exec) cudaGraphExecDestroy(m->exec);
     if (m->graph) cudaGraphDestroy(m->graph);
     void* bufs[] = {m->f0p, m->mean, m->U, m->fh, m->fpad, m->p, m->q, m->y, m->r, m->flat, m->hbuf,
-                    m->partials, m->counter, m->st, m->wdev, m->out, m->rg, m->steps, m->order};
+                    m->partials, m->counter, m->st, m->wdev, m->out, m->rg, m->steps, m->order, m->sup};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (m->st_host) cudaFreeHost(m->st_host);
@@ -248,7 +249,7 @@ int build_graph(pr_ctx* c, Model* m) {
     CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
     CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
-                      m->partials, m->counter, kPhaseInit, m->hloop, 1));
+                      m->partials, m->counter, kPhaseInit, m->hloop, 1, SupportRef{m->sup, st->wt, m->K}));
     CK(launch_regrad(L, m->p, m->q, m->y, m->R, m->K, st, m->partials, m->counter, m->hloop, 1));
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
@@ -261,7 +262,7 @@ int build_graph(pr_ctx* c, Model* m) {
     B.graph = cp.conditional.phGraph_out[0];
     CK(launch_warp(B, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
     CK(launch_project(B, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
-                      m->partials, m->counter, kPhaseTrial, m->hloop, 1));
+                      m->partials, m->counter, kPhaseTrial, m->hloop, 1, SupportRef{m->sup, st->wt, m->K}));
     CK(launch_regrad(B, m->p, m->q, m->y, m->R, m->K, st, m->partials, m->counter, m->hloop, 1));
     L.last = cond;
     CK(launch_tumor(L, m->md, st->w, 0.0, 0, &st->prm, st->tumor, &st->tumor_steps));
@@ -278,7 +279,7 @@ int host_loop(pr_ctx* c, Model* m, int opt_max_iters, int opt_max_bt) {
     CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
     CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
-                      m->partials, m->counter, kPhaseInit, 0, 0));
+                      m->partials, m->counter, kPhaseInit, 0, 0, SupportRef{m->sup, st->wt, m->K}));
     CK(launch_regrad(L, m->p, m->q, m->y, m->R, m->K, st, m->partials, m->counter, 0, 0));
     long long guard = 0, bound = (long long)(opt_max_iters + 1) * (opt_max_bt + 1) + 2;
     for (;;) {
@@ -288,7 +289,7 @@ int host_loop(pr_ctx* c, Model* m, int opt_max_iters, int opt_max_bt) {
         if (++guard > bound) return fail(PR_ETIMEOUT, "host loop exceeded its trial bound");
         CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
         CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y,
-                          st, m->partials, m->counter, kPhaseTrial, 0, 0));
+                          st, m->partials, m->counter, kPhaseTrial, 0, 0, SupportRef{m->sup, st->wt, m->K}));
         CK(launch_regrad(L, m->p, m->q, m->y, m->R, m->K, st, m->partials, m->counter, 0, 0));
     }
     CK(launch_tumor(L, m->md, st->w, 0.0, 0, &st->prm, st->tumor, &st->tumor_steps));
@@ -485,6 +486,7 @@ int pr_load_model(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
     A(&m->rg, sizeof(RayGeom));
     A(&m->steps, 16);
     A(&m->order, (size_t)project_blocks(geom->nu, geom->nv) * sizeof(int));
+    A(&m->sup, sizeof(Support));
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&m->st_host, sizeof(SolveState), cudaHostAllocDefault);
     if (e != cudaSuccess) {
         free_model(m);
@@ -519,15 +521,23 @@ int pr_load_model(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
         if ((e = cudaMemcpyAsync(m->flat, f0, n * 4, kind, s))) break;
         Launcher L;
         L.stream = s;
+        if ((e = launch_support_init(L, m->sup))) break;
+        if ((e = launch_support_box(L, vd, m->flat, m->sup))) break;
+        for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = launch_maxabs(L, m->mean + (size_t)c * n, (long long)n, &m->sup->mean_max[c]);
+        if (e) break;
         if ((e = launch_pad(L, vd, m->flat, m->fpad))) break;
         if (storage == PR_F32) {
             if ((e = cudaMemcpyAsync(m->f0p, m->fpad, np * 4, cudaMemcpyDeviceToDevice, s))) break;
             if ((e = cudaMemcpyAsync(m->U, U, 3 * (size_t)K * n * 4, kind, s))) break;
+            for (int pl = 0; pl < 3 * K && e == cudaSuccess; ++pl)
+                e = launch_maxabs(L, (const float*)m->U + (size_t)pl * n, (long long)n, &m->sup->u_max[pl / 3][pl % 3]);
+            if (e) break;
         } else {
             if ((e = launch_to_bf16(L, m->fpad, (__nv_bfloat16*)m->f0p, np))) break;
             // U converted plane by plane through the float32 scratch
             for (int pl = 0; pl < 3 * K && e == cudaSuccess; ++pl) {
                 if ((e = cudaMemcpyAsync(m->flat, U + (size_t)pl * n, n * 4, kind, s))) break;
+                if ((e = launch_maxabs(L, m->flat, (long long)n, &m->sup->u_max[pl / 3][pl % 3]))) break;
                 e = launch_to_bf16(L, m->flat, (__nv_bfloat16*)m->U + (size_t)pl * n, n);
             }
             if (e) break;
@@ -682,7 +692,7 @@ int pr_forward(pr_ctx* c, int id, const double* w, double angle, float* p_dev) {
     L.stream = c->stream;
     CK(launch_warp(L, m->md, m->wdev, kWarpFPad, m->fpad, nullptr, nullptr));
     CK(launch_project(L, m->md.vd, m->fpad, 1, 0, m->rg, m->order, m->geom.nu, m->geom.nv, p_dev, nullptr, nullptr, nullptr,
-                      nullptr, nullptr, kPhaseNone, 0, 0));
+                      nullptr, nullptr, kPhaseNone, 0, 0, SupportRef{m->sup, m->wdev, m->K}));
     CK(cudaStreamSynchronize(c->stream));
     return PR_OK;
 }
@@ -721,7 +731,7 @@ int pr_cost_grad(pr_ctx* c, int id, const float* y_dev, double angle, const doub
     if (mode == 0) {
         CK(launch_warp(L, m->md, m->wdev, kWarpFH, m->fh, nullptr, nullptr));
         CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, m->order, nu, nv, m->p, m->q, nullptr, nullptr, nullptr,
-                          nullptr, kPhaseNone, 0, 0));
+                          nullptr, kPhaseNone, 0, 0, SupportRef{m->sup, m->wdev, m->K}));
         CK(launch_cost_grad(L, m->p, m->q, y_dev, m->R, m->K, m->out + 8, m->partials, m->counter, m->out));
         CK(cudaMemcpyAsync(res, m->out, sizeof(double) * (1 + m->K), cudaMemcpyDeviceToHost, c->stream));
     } else {
@@ -729,7 +739,7 @@ int pr_cost_grad(pr_ctx* c, int id, const float* y_dev, double angle, const doub
         CK(launch_warp(L, m->md, m->wdev, kWarpFPad, m->fpad, nullptr, nullptr));
         CK(launch_warp(L, m->md, m->wdev, kWarpFlatFH, nullptr, nullptr, m->hbuf));
         CK(launch_project(L, m->md.vd, m->fpad, 1, 0, m->rg, m->order, nu, nv, m->p, nullptr, nullptr, nullptr, nullptr,
-                          nullptr, kPhaseNone, 0, 0));
+                          nullptr, kPhaseNone, 0, 0, SupportRef{m->sup, m->wdev, m->K}));
         CK(launch_cost_grad(L, m->p, nullptr, y_dev, m->R, 0, m->out + 8, m->partials, m->counter, m->out));
         CK(launch_residual(L, m->p, y_dev, m->R, m->out + 8, m->r));
         CK(cudaMemcpyAsync(res, m->out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -778,7 +788,7 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
     CK(launch_warp(L, m->md, m->st->w, kWarpFPad, m->fpad, nullptr, nullptr));
     if (which == PR_KERNEL_BACKPROJECT) CK(launch_warp(L, m->md, m->st->w, kWarpFlatFH, nullptr, nullptr, m->hbuf));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, m->order, nu, nv, m->p, m->q, nullptr, nullptr, nullptr, nullptr,
-                      kPhaseNone, 0, 0));
+                      kPhaseNone, 0, 0, SupportRef{m->sup, m->st->w, m->K}));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -788,7 +798,7 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
             case PR_KERNEL_WARP_FH: err = launch_warp(L, m->md, m->st->w, kWarpFH, m->fh, nullptr, nullptr); break;
             case PR_KERNEL_PROJECT_FH:
                 err = launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, m->order, nu, nv, m->p, m->q, nullptr, nullptr,
-                                     nullptr, nullptr, kPhaseNone, 0, 0);
+                                     nullptr, nullptr, kPhaseNone, 0, 0, SupportRef{m->sup, m->st->w, m->K});
                 break;
             case PR_KERNEL_REGRAD:
                 err = launch_cost_grad(L, m->p, m->q, m->p, m->R, m->K, m->out + 8, m->partials, m->counter, m->out);
@@ -800,7 +810,7 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
             case PR_KERNEL_WARP_F: err = launch_warp(L, m->md, m->st->w, kWarpFPad, m->fpad, nullptr, nullptr); break;
             case PR_KERNEL_PROJECT_F:
                 err = launch_project(L, m->md.vd, m->fpad, 1, 0, m->rg, m->order, nu, nv, m->r, nullptr, nullptr, nullptr,
-                                     nullptr, nullptr, kPhaseNone, 0, 0);
+                                     nullptr, nullptr, kPhaseNone, 0, 0, SupportRef{m->sup, m->st->w, m->K});
                 break;
         }
     }
