@@ -416,17 +416,21 @@ __global__ void __launch_bounds__(kReduceThreads)
 k_cost_grad(const float* __restrict__ p, const float* __restrict__ q, const float* __restrict__ y, int R, int K,
             const double* ab, double* partials, unsigned int* counter, double* out) {
     const double a = ab[0], b = ab[1];
-    double v[8];
+    // same arithmetic as k_regrad: FP64 residual, FP32 products, FP64 sums
+    float vf[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = 0.0;
+    for (int m = 0; m < 8; ++m) vf[m] = 0.0f;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
-        double res = (double)p[r] - a * (double)y[r] - b;
-        v[0] += res * res;
+        float res = (float)((double)p[r] - fma(a, (double)y[r], b));
+        vf[0] = __fmaf_rn(res, res, vf[0]);
         if (q)
 #pragma unroll
             for (int k = 0; k < kMaxK; ++k)
-                if (k < K) v[1 + k] += res * (double)q[(long long)k * R + r];
+                if (k < K) vf[1 + k] = __fmaf_rn(res, q[(long long)k * R + r], vf[1 + k]);
     }
+    double v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = vf[m];
     block_sum<8>(v);
     if (!publish_partials<8>(v, partials, blockIdx.x, gridDim.x, counter)) return;
     double tot[8];
