@@ -107,8 +107,12 @@ typedef struct {
     int loop_mode;       /* PR_LOOP_GRAPH (on-device loop in a CUDA graph) or PR_LOOP_HOST */
     double tumor_tol;    /* fixed-point stop, mm; default 1e-6 */
     int tumor_max_iter;  /* default 100 */
-    double step_growth;  /* first trial step of an iteration = step_growth x the last
-                            accepted step (the first iteration uses step0_mm); default 1.25 */
+    double step_growth;    /* next first trial = step_growth x an accepted step that was
+                              accepted at its first trial; default 2 */
+    double step_growth_bt; /* ... = step_growth_bt x an accepted step that needed
+                              backtracking; default 1 */
+    int warm_step;         /* 1: a warm-started solve also starts from the model's next
+                              step (unless the last solve's line search failed); default 1 */
 } pr_solve_opts;
 
 typedef struct {
@@ -124,8 +128,8 @@ typedef struct {
     int stop_reason;        /* PR_STOP_* */
     double tumor_xyz[3];    /* mm, Section 2.3 */
     int tumor_steps;
-    double mu;              /* last accepted line-search step; a warm-started solve's first
-                               trial is step_growth x this (0 = none yet) */
+    double mu;              /* first trial step of the next warm-started solve (0 = none:
+                               it moves w by step0_mm) */
 } pr_result;
 
 /* Library version string (static storage). */

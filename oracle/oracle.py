@@ -22,13 +22,14 @@ Readings of the paper where it is silent (the CUDA path uses the same):
   * Armijo rule (Section 2.2 names it, gives no constants): sufficient
     decrease J(w - mu g; a, b) <= J(w; a, b) - c1 mu |g|^2 with c1 = 1e-4,
     backtracking mu <- beta mu with beta = 0.5, at most 20 backtracks. The
-    first trial step is mu = step0_mm / |g| (moves w by step0_mm), later ones
-    start from step_growth x the last accepted mu (step_growth = 1.25); a
-    solve warm-started from the previous frame starts its first trial at
-    step_growth x that frame's last accepted mu, as its w starts from that
-    frame's w (Section 4 initialises each frame from the previous one). No
-    accepted step: w is kept and the solve stops with stop reason "line
-    search failed".
+    first trial step is mu = step0_mm / |g| (moves w by step0_mm); after an
+    accepted step mu the next first trial is step_growth x mu (2) if mu was
+    accepted at its first trial, else step_growth_bt x mu (1). A solve
+    warm-started from the previous frame starts with that frame's next trial
+    step, as its w starts from that frame's w (Section 4 initialises each
+    frame from the previous one). No accepted step: w is kept, the solve
+    stops with stop reason "line search failed" and the next trial step is
+    forgotten.
   * (a, b) before the first step 1: Eq. 4 at the starting w.
   * Stop (Section 2.2: gradient "sufficiently small" or the iteration cap):
     |g| <= grad_tol * |g_0| or max_iters accepted steps.
@@ -256,7 +257,8 @@ class SolveOptions:
     beta: float = 0.5
     max_backtracks: int = 20
     step0_mm: float = 1.0
-    step_growth: float = 1.25
+    step_growth: float = 2.0
+    step_growth_bt: float = 1.0
     tumor_tol: float = 1e-6
     tumor_max_iter: int = 100
 
@@ -273,15 +275,15 @@ class SolveResult:
     stop_reason: int
     tumor: np.ndarray
     tumor_steps: int
-    mu: float  # last accepted step (the warm-start step of the next frame)
+    mu: float  # first trial step of the next warm-started frame (0 = none)
     history: list  # per accepted step: dict(J_after_step1, J_after_step2, mu, w)
 
 
 def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None,
-                mu_warm: float | None = None) -> SolveResult:
+                mu_next: float | None = None) -> SolveResult:
     """Section 2.2: alternate step 1 (Eq. 3, gradient step with Armijo's rule at
     fixed a, b) and step 2 (Eq. 4, exact a, b at fixed w), then Section 2.3.
-    mu_warm: the previous frame's last accepted step (None or 0 = cold)."""
+    mu_next: the previous frame's next trial step (None or 0 = cold)."""
     o = opts or SolveOptions()
     y = np.asarray(y, dtype=np.float64)
     w = np.array(w0, dtype=np.float64)
@@ -289,7 +291,6 @@ def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None,
     a, b = fit_ab(evaluate(model, geom, angle, w).p, y)
     g, J, _ = gradient(model, geom, angle, w, a, b, y)
     g0 = float(np.linalg.norm(g))
-    mu_prev = None
     n = 0
     backtracks = 0
     stop = STOP_MAX_ITERS
@@ -303,12 +304,7 @@ def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None,
             stop = STOP_MAX_ITERS
             break
         # Step 1: w <- w - mu g, mu by backtracking from the initial trial.
-        if mu_prev is not None:
-            mu = o.step_growth * mu_prev
-        elif mu_warm:
-            mu = o.step_growth * mu_warm
-        else:
-            mu = o.step0_mm / gn
+        mu = mu_next if mu_next else o.step0_mm / gn
         accepted = None
         for bt in range(o.max_backtracks + 1):
             trial = evaluate(model, geom, angle, w - mu * g)
@@ -320,15 +316,15 @@ def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None,
             mu *= o.beta
         if accepted is None:
             stop = STOP_LINESEARCH_FAILED
+            mu_next = 0.0
             break
+        mu_next = (o.step_growth if bt == 0 else o.step_growth_bt) * mu
         w = accepted.w
-        mu_prev = mu
         # Step 2: (a, b) by Eq. 4 at the new w.
         a, b = fit_ab(accepted.p, y)
         g, J, _ = gradient(model, geom, angle, w, a, b, y)
         history.append(dict(J_step1=J_t, J_step2=J, mu=mu, w=w.copy()))
         n += 1
     p_t, steps = tumor(model.vol, model.mean, model.U, w, model.c0, o.tumor_tol, o.tumor_max_iter)
-    mu_last = mu_prev if mu_prev is not None else (mu_warm or 0.0)
     return SolveResult(w=w, a=a, b=b, J=J, grad=g, iters=n, backtracks=backtracks, stop_reason=stop,
-                       tumor=p_t, tumor_steps=steps, mu=mu_last, history=history)
+                       tumor=p_t, tumor_steps=steps, mu=mu_next or 0.0, history=history)

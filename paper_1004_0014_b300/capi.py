@@ -75,7 +75,8 @@ class SolveOpts(ctypes.Structure):
                 ("step0_mm", ctypes.c_double), ("cold_start", ctypes.c_int),
                 ("w0", ctypes.c_double * PR_MAX_K), ("loop_mode", ctypes.c_int),
                 ("tumor_tol", ctypes.c_double), ("tumor_max_iter", ctypes.c_int),
-                ("step_growth", ctypes.c_double)]
+                ("step_growth", ctypes.c_double), ("step_growth_bt", ctypes.c_double),
+                ("warm_step", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):

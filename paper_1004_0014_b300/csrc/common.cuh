@@ -96,10 +96,10 @@ enum Phase : int {
 struct SolveParams {
     RayGeom rg;
     double w0[8];
-    double c1, beta, grad_tol, step0, tumor_tol, step_growth;
+    double c1, beta, grad_tol, step0, tumor_tol, step_growth, step_growth_bt;
     int max_iters, max_bt, tumor_max_iter, K;
     int cold_start;  // 1: start from w0; 0: from the state's last accepted w
-    int pad_;
+    int warm_step;   // 1: a warm start also takes the state's next step
 };
 
 // On-device state of one solve (FP64 scalars; Section 2.2's alternation).
@@ -114,7 +114,7 @@ struct SolveState {
     double tumor[3];
     int tumor_steps, pad_;
     long long cum_solves, cum_trials;  // since the model was loaded
-    double mu_warm;  // last accepted step, carried to the next warm-started solve (0 = none)
+    double mu_next;  // first trial step of the next iteration or warm-started solve (0 = none)
 };
 
 // ---------------------------------------------------------------------------

@@ -84,7 +84,7 @@ k_begin(const float* __restrict__ y, int R, SolveState* st, double* partials, un
         st->need_grad = 0;
         st->running = 1;
         st->cum_solves += 1;
-        if (st->prm.cold_start) st->mu_warm = 0.0;
+        if (st->prm.cold_start || !st->prm.warm_step) st->mu_next = 0.0;
     }
 }
 
@@ -233,7 +233,8 @@ __device__ void controller_project(SolveState* st, const double (&tot)[3], int p
         for (int k = 0; k < kMaxK; ++k)
             if (k < K) st->w[k] = st->wt[k];
         st->mu_prev = st->mu;
-        st->mu_warm = st->mu;
+        // next first trial: grow after a first-try acceptance, else keep
+        st->mu_next = (st->bt == 0 ? st->prm.step_growth : st->prm.step_growth_bt) * st->mu;
         st->iter += 1;
         st->accepted = 1;
         if (fit_ab(st, tot[1], tot[2], &a, &b)) {  // step 2, Eq. 4
@@ -251,6 +252,7 @@ __device__ void controller_project(SolveState* st, const double (&tot)[3], int p
     st->total_bt += 1;
     if (st->bt > st->prm.max_bt) {
         st->stop = 3;  // PR_STOP_LINESEARCH_FAILED: w keeps its last accepted value
+        st->mu_next = 0.0;  // the collapsed step says nothing about the next frame
         set_loop(st, 0, h, use_graph);
         return;
     }
@@ -400,12 +402,9 @@ k_regrad(const float* __restrict__ p, const float* __restrict__ q, const float* 
         set_loop(st, 0, h, use_graph);
         return;
     }
-    if (st->iter > 0)
-        st->mu = st->prm.step_growth * st->mu_prev;
-    else if (st->mu_warm > 0.0)  // warm start: the previous frame's last accepted step
-        st->mu = st->prm.step_growth * st->mu_warm;
-    else
-        st->mu = st->prm.step0 / gn;
+    // after an accepted step (this solve or, warm-started, the previous frame's
+    // last) the next step; otherwise a first trial that moves w by step0 mm
+    st->mu = st->mu_next > 0.0 ? st->mu_next : st->prm.step0 / gn;
     st->bt = 0;
     next_trial(st, K);
     set_loop(st, 1, h, use_graph);

@@ -217,6 +217,8 @@ int write_params(pr_ctx* c, Model* m, double angle, const pr_solve_opts* o) {
     prm.grad_tol = o->grad_tol;
     prm.step0 = o->step0_mm;
     prm.step_growth = o->step_growth;
+    prm.step_growth_bt = o->step_growth_bt;
+    prm.warm_step = o->warm_step ? 1 : 0;
     prm.tumor_tol = o->tumor_tol;
     prm.max_iters = o->max_iters;
     prm.max_bt = o->max_backtracks;
@@ -233,7 +235,7 @@ bool opts_ok(const pr_solve_opts* o) {
     return o->max_iters >= 0 && o->max_iters <= 100000 && o->max_backtracks >= 0 && o->max_backtracks <= 200 &&
            o->beta > 0 && o->beta < 1 && o->c1 >= 0 && o->c1 < 1 && o->step0_mm > 0 && o->grad_tol >= 0 &&
            o->tumor_max_iter >= 0 && o->tumor_max_iter <= 100000 && o->tumor_tol >= 0 &&
-           o->step_growth > 0 && o->step_growth <= 100 &&
+           o->step_growth > 0 && o->step_growth <= 100 && o->step_growth_bt > 0 && o->step_growth_bt <= 100 &&
            (o->loop_mode == PR_LOOP_GRAPH || o->loop_mode == PR_LOOP_HOST);
 }
 
@@ -314,7 +316,7 @@ void fill_result(const Model* m, const SolveState& s, pr_result* out) {
     out->stop_reason = s.stop;
     for (int c = 0; c < 3; ++c) out->tumor_xyz[c] = s.tumor[c];
     out->tumor_steps = s.tumor_steps;
-    out->mu = s.mu_warm;
+    out->mu = s.mu_next;
 }
 
 int enqueue_solve(pr_ctx* c, Model* m, double angle, const pr_solve_opts* opts) {
@@ -392,7 +394,9 @@ void pr_default_opts(pr_solve_opts* o) {
     o->loop_mode = PR_LOOP_GRAPH;
     o->tumor_tol = 1e-6;
     o->tumor_max_iter = 100;
-    o->step_growth = 1.25;
+    o->step_growth = 2.0;
+    o->step_growth_bt = 1.0;
+    o->warm_step = 1;
 }
 
 int pr_create(pr_ctx** out, int device, void* stream, size_t hbm_budget_bytes) {
@@ -626,7 +630,7 @@ int pr_set_state(pr_ctx* c, int id, const double* w) {
         buf[k] = w[k];
     }
     CK(cudaMemcpyAsync(m->st->w, buf, sizeof buf, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemsetAsync(&m->st->mu_warm, 0, sizeof(double), c->stream));
+    CK(cudaMemsetAsync(&m->st->mu_next, 0, sizeof(double), c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return PR_OK;
 }

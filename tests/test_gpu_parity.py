@@ -326,7 +326,7 @@ def test_warm_started_frames_match_oracle(ctx, small):
     a = ctx.reconstruct(small["mid"], ys[0], angles[0], _opts(max_iters=6, cold_start=1, w0=[0, 0, 0]))
     b = ctx.reconstruct(small["mid"], ys[1], angles[1], _opts(max_iters=6))
     oa = O.reconstruct(om, geom, angles[0], _up(ys[0]), np.zeros(3), O.SolveOptions(max_iters=6))
-    ob = O.reconstruct(om, geom, angles[1], _up(ys[1]), oa.w, O.SolveOptions(max_iters=6), mu_warm=oa.mu)
+    ob = O.reconstruct(om, geom, angles[1], _up(ys[1]), oa.w, O.SolveOptions(max_iters=6), mu_next=oa.mu)
     report("warm_frames64", w_rel=rel(b["w"], ob.w), mu_rel=abs(b["mu"] - ob.mu) / ob.mu,
            backtracks=b["backtracks"], oracle_backtracks=ob.backtracks)
     # the step is step0 / |grad J| times powers of beta and step_growth, so it
