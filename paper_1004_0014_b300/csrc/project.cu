@@ -95,7 +95,18 @@ k_begin(const float* __restrict__ y, int R, SolveState* st, double* partials, un
 // Trilinear accumulation of one sample into acc[0..NCH) (1 or 8 channels).
 template <int NCH>
 __device__ __forceinline__ void accumulate(const float* __restrict__ vol, const VolDev& vd, const float q[3],
-                                           float (&acc)[NCH]);
+                                           float (&acc)[NCH], float& comp);
+
+// Compensated (Kahan) addition: the f channel's ray sum is the projection in
+// the cost J, and its float rounding over ~600 samples would otherwise be
+// the largest error in J (large enough to decide line-search tests near
+// convergence); the h channels only feed the gradient direction.
+__device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
+    float y = __fsub_rn(x, comp);
+    float t = __fadd_rn(sum, y);
+    comp = __fsub_rn(__fsub_rn(t, sum), y);
+    sum = t;
+}
 
 // Cell of a sample: integer corner index i (clamped to [-1, n-1]) and the
 // fraction t in [0, 1]. A point outside the support (-1, n) lands on the zero
@@ -134,19 +145,23 @@ struct CellCache4 {
         }
         float wy0 = 1.0f - ty, wz0 = 1.0f - tz;
         const float wyz[4] = {wy0 * wz0, ty * wz0, wy0 * tz, ty * tz};
+        float s0 = 0.0f;  // this sample's f value, added to the ray sum with compensation
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             float w0 = wyz[k] * (1.0f - tx), w1 = wyz[k] * tx;
+            s0 = __fmaf_rn(w1, c[2 * k + 1][0], __fmaf_rn(w0, c[2 * k][0], s0));
 #pragma unroll
-            for (int ch = 0; ch < 4; ++ch)
+            for (int ch = 1; ch < 4; ++ch)
                 acc[ch] = __fmaf_rn(w1, c[2 * k + 1][ch], __fmaf_rn(w0, c[2 * k][ch], acc[ch]));
         }
+        kahan_add(acc[0], comp, s0);
     }
+    float comp = 0.0f;  // running compensation of acc[0]
 };
 
 template <int NCH>
 __device__ __forceinline__ void accumulate(const float* __restrict__ vol, const VolDev& vd, const float q[3],
-                                           float (&acc)[NCH]) {
+                                           float (&acc)[NCH], float& comp) {
     float tx, ty, tz;
     int ix = cell(q[0], vd.nx, tx), iy = cell(q[1], vd.ny, ty), iz = cell(q[2], vd.nz, tz);
     int b = ((iz + 1) * vd.nyp + (iy + 1)) * vd.nxp + (ix + 1);
@@ -154,12 +169,13 @@ __device__ __forceinline__ void accumulate(const float* __restrict__ vol, const 
     const int off[4] = {0, vd.nxp, plane, plane + vd.nxp};
     float wy0 = 1.0f - ty, wz0 = 1.0f - tz;
     const float wyz[4] = {wy0 * wz0, ty * wz0, wy0 * tz, ty * tz};
+    float s0 = 0.0f;  // this sample's f value
     if (NCH == 1) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const float* p = vol + b + off[k];
             float a0 = __ldg(p), a1 = __ldg(p + 1);
-            acc[0] = __fmaf_rn(wyz[k], __fmaf_rn(tx, a1 - a0, a0), acc[0]);
+            s0 = __fmaf_rn(wyz[k], __fmaf_rn(tx, a1 - a0, a0), s0);
         }
     } else {
         constexpr int NV4 = NCH / 4;
@@ -171,13 +187,17 @@ __device__ __forceinline__ void accumulate(const float* __restrict__ vol, const 
 #pragma unroll
             for (int h = 0; h < NV4; ++h) {
                 float4 a0 = __ldg(p + h), a1 = __ldg(p + NV4 + h);
-                acc[4 * h + 0] = __fmaf_rn(w1, a1.x, __fmaf_rn(w0, a0.x, acc[4 * h + 0]));
+                if (h == 0)
+                    s0 = __fmaf_rn(w1, a1.x, __fmaf_rn(w0, a0.x, s0));
+                else
+                    acc[4 * h + 0] = __fmaf_rn(w1, a1.x, __fmaf_rn(w0, a0.x, acc[4 * h + 0]));
                 acc[4 * h + 1] = __fmaf_rn(w1, a1.y, __fmaf_rn(w0, a0.y, acc[4 * h + 1]));
                 acc[4 * h + 2] = __fmaf_rn(w1, a1.z, __fmaf_rn(w0, a0.z, acc[4 * h + 2]));
                 acc[4 * h + 3] = __fmaf_rn(w1, a1.w, __fmaf_rn(w0, a0.w, acc[4 * h + 3]));
             }
         }
     }
+    kahan_add(acc[0], comp, s0);
 }
 
 struct ProjArgs {
@@ -302,10 +322,11 @@ __global__ void __launch_bounds__(kProjThreads, NCH == 4 ? 4 : 1) k_project(Proj
             cache.sample(A.vol, A.vd, q, acc);
         }
     } else {
+        float comp = 0.0f;
         for (int s = s_lo; s <= s_hi; ++s) {
             float q[3];
             sample_pos(g, b, s, q);
-            accumulate<NCH>(A.vol, A.vd, q, acc);
+            accumulate<NCH>(A.vol, A.vd, q, acc, comp);
         }
     }
 

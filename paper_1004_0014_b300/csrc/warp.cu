@@ -84,16 +84,23 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp(WarpArgs<TS> A) {
                 d1 = __fmaf_rn(u[k][1][e], w[k], d1);
                 d2 = __fmaf_rn(u[k][2][e], w[k], d2);
             }
-            float qx = __fmaf_rn(d0, vd.inv_dx, (float)i);
-            float qy = __fmaf_rn(d1, vd.inv_dy, (float)j);
-            float qz = __fmaf_rn(d2, vd.inv_dz, (float)kz);
+            // Pull-back point q = v + x / spacing, split as the integer voxel
+            // index plus the small displacement: cell = v + floor(x/dx) and the
+            // fraction x/dx - floor(x/dx) keep the displacement's precision
+            // instead of that of the full index.
+            float ux = d0 * vd.inv_dx, uy = d1 * vd.inv_dy, uz = d2 * vd.inv_dz;
+            float fux = floorf(ux), fuy = floorf(uy), fuz = floorf(uz);
+            float tx = ux - fux, ty = uy - fuy, tz = uz - fuz;
             float val = 0.0f;
             float gx = 0.0f, gy = 0.0f, gz = 0.0f;
-            if (qx > -1.0f && qx < (float)vd.nx && qy > -1.0f && qy < (float)vd.ny && qz > -1.0f &&
-                qz < (float)vd.nz) {
-                float fx = floorf(qx), fy = floorf(qy), fz = floorf(qz);
-                float tx = qx - fx, ty = qy - fy, tz = qz - fz;
-                long long base = ((long long)((int)fz + 1) * vd.nyp + ((int)fy + 1)) * vd.nxp + ((int)fx + 1);
+            // inside the interpolant's support (-1, n) on every axis; the bounds on
+            // fu keep the int conversion in range for any displacement
+            const bool in_x = fux > -1.0e6f && fux < 1.0e6f, in_y = fuy > -1.0e6f && fuy < 1.0e6f,
+                       in_z = fuz > -1.0e6f && fuz < 1.0e6f;
+            int cx = in_x ? i + (int)fux : -2, cy = in_y ? j + (int)fuy : -2, cz = in_z ? kz + (int)fuz : -2;
+            if ((cx > -1 || (cx == -1 && tx > 0.0f)) && cx < vd.nx && (cy > -1 || (cy == -1 && ty > 0.0f)) &&
+                cy < vd.ny && (cz > -1 || (cz == -1 && tz > 0.0f)) && cz < vd.nz) {
+                long long base = ((long long)(cz + 1) * vd.nyp + (cy + 1)) * vd.nxp + (cx + 1);
                 const TS* c0 = A.f0p + base;
                 float c000 = ld_val(c0), c100 = ld_val(c0 + 1);
                 float c010 = ld_val(c0 + vd.nxp), c110 = ld_val(c0 + vd.nxp + 1);
