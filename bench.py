@@ -219,6 +219,70 @@ def make_targets(ctx, w, f0, frames):
 
 
 # ----------------------------------------------------------------------------
+# roofline helpers
+# ----------------------------------------------------------------------------
+
+# Algorithmic FP32 work per projector sample of an nch-channel volume: the
+# trilinear weights (3 complements, 8 products of 3 factors: 19 flop), one
+# multiply-add per corner and channel (2 * 8 * nch), and the sample position
+# (3 multiply-adds: 6 flop).
+def flops_per_sample(nch: int) -> int:
+    return 2 * 8 * nch + 19 + 6
+
+
+def projector_samples(vol, geom, angle, f0, mean, U, w):
+    """Samples the projector takes at gantry angle `angle` and coefficients w:
+    per ray, the source-anchored samples inside the support box of the warped
+    volume (the nonzero box of f0 dilated by two cells and by the largest
+    displacement w allows), the same clipping as the kernel, in float64."""
+    nzk, nzj, nzi = np.nonzero(f0)
+    if nzk.size == 0:
+        return 0
+    sp = vol.spacing
+    n = np.array([vol.nx, vol.ny, vol.nz], float)
+    lo = np.array([nzi.min(), nzj.min(), nzk.min()], float)
+    hi = np.array([nzi.max(), nzj.max(), nzk.max()], float)
+    d = np.abs(mean).reshape(3, -1).max(axis=1)
+    for k in range(U.shape[0]):
+        d = d + abs(w[k]) * np.abs(U[k]).reshape(3, -1).max(axis=1)
+    d = d / sp * 1.01 + 0.01
+    lo = np.maximum(-1.0, lo - 2.0 - d)
+    hi = np.minimum(n, hi + 2.0 + d)
+    st, ct = math.sin(angle), math.cos(angle)
+    S = np.array([geom.sad * st, -geom.sad * ct, 0.0])
+    eh, uh, vh = np.array([-st, ct, 0.0]), np.array([ct, st, 0.0]), np.array([0.0, 0.0, 1.0])
+    iv, iu = np.meshgrid(np.arange(geom.nv), np.arange(geom.nu), indexing="ij")
+    su = (iu - 0.5 * (geom.nu - 1)) * geom.du
+    sv = (iv - 0.5 * (geom.nv - 1)) * geom.dv
+    dirs = geom.sdd * eh[None, None, :] + su[..., None] * uh + sv[..., None] * vh
+    dirs /= np.linalg.norm(dirs, axis=-1, keepdims=True)
+    a = (S - vol.origin) / sp
+    b = dirs / sp
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ta = (lo - a) / b
+        tb = (hi - a) / b
+    t0 = np.maximum(0.0, np.nanmax(np.minimum(ta, tb), axis=-1))
+    t1 = np.nanmin(np.maximum(ta, tb), axis=-1)
+    s_lo = np.maximum(0, np.ceil(t0 / geom.ds - 0.5))
+    s_hi = np.floor(t1 / geom.ds - 0.5)
+    cnt = np.where(t1 > t0, np.maximum(0, s_hi - s_lo + 1), 0)
+    return int(cnt.sum())
+
+
+def recorded_traffic(kernel: str, source: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, only
+    if the kernel's source file is unchanged since the capture (else None)."""
+    import hashlib
+
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        sha = hashlib.sha256(open(os.path.join(ROOT, "paper_1004_0014_b300", "csrc", source), "rb").read()).hexdigest()
+    except (OSError, ValueError, KeyError):
+        return None
+    return rec["bytes_per_launch"] if rec.get("source_sha256") == sha else None
+
+
+# ----------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on the host cores
 # ----------------------------------------------------------------------------
 
@@ -386,46 +450,53 @@ def run_ours(args):
     if args.adjoint:
         kern["backproject_dot"] = ctx.time_kernel(mid, capi.PR_KERNEL_BACKPROJECT, angles[W], iters=3)
 
-    # Algorithmic bytes per launch (float32 storage, K modes, N voxels, R rays):
-    # warp (f + h): read mean 12 B + U 12K B + f0 4 B, write the nch-float (f, h) voxel;
-    # projection of (f, h): read the nch-channel volume once, write p and q 4(1+K) B per ray.
+    # Dominant kernel: the 4-channel projector, bound by instruction issue and
+    # FP32 arithmetic (ncu: DRAM ~1%, L1 ~70%, issue ~65%), so its roofline is
+    # FP32 flop/s against the FMA peak of 148 SMs x 128 lanes x 2 flop x clock.
+    # The warp kernel is the HBM-bound one; its roofline is reported beside it.
     N, R, Km = vol.n, geom.n_rays, w["K"]
     nch = 4 if Km <= 3 else 8
-    bytes_warp = N * (12 + 12 * Km + 4 + 4 * nch)
-    bytes_proj = N * 4 * nch + R * 4 * (1 + Km)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
+    sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    samples = projector_samples(vol, geom, angles[W], f0, mean, U, w_start)
+    flops = samples * flops_per_sample(nch)
     per_solve_ms = elapsed_ms / K
     trials_per_solve = trials / K
-    # time share of each kernel inside a solve: one prologue pass plus one per trial
-    share_warp = (1 + trials_per_solve) * kern["warp_fh"] / per_solve_ms
     share_proj = (1 + trials_per_solve) * kern["project_fh"] / per_solve_ms
-    dom = "warp_fh" if share_warp >= share_proj else "project_fh"
-    dom_bytes = bytes_warp if dom == "warp_fh" else bytes_proj
-    achieved = dom_bytes / (kern[dom] / 1000.0) / 1e9
-    other = "project_fh" if dom == "warp_fh" else "warp_fh"
-    other_bytes = bytes_proj if dom == "warp_fh" else bytes_warp
-    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None,
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if peaks else "fallback",
-                "algorithmic_bytes_per_launch": dom_bytes,
-                "share_of_solve": {"warp_fh": share_warp, "project_fh": share_proj},
-                "other_kernel": {"name": other, "achieved_gbs": other_bytes / (kern[other] / 1000.0) / 1e9,
-                                 "algorithmic_bytes_per_launch": other_bytes}}
+    share_warp = (1 + trials_per_solve) * kern["warp_fh"] / per_solve_ms
+    proj_tflops = flops / (kern["project_fh"] / 1000.0) / 1e12
+    bytes_proj = N * 4 * nch + R * 4 * (1 + Km)
+    roofline = {"kernel": "k_project<%d> (f, h_1..h_%d)" % (nch, Km), "bound": "alu", "achieved": proj_tflops,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": proj_tflops / fp32_peak,
+                "traffic": recorded_traffic("k_project<4>", "project.cu"),
+                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (FMA peak)" % sm_mhz,
+                "samples_per_launch": samples, "flops_per_sample": flops_per_sample(nch),
+                "algorithmic_flops_per_launch": flops, "share_of_solve": share_proj,
+                "algorithmic_bytes_per_launch": bytes_proj,
+                "achieved_gbs": bytes_proj / (kern["project_fh"] / 1000.0) / 1e9}
+    bytes_warp = N * (12 + 12 * Km + 4 + 4 * nch)
+    warp_gbs = bytes_warp / (kern["warp_fh"] / 1000.0) / 1e9
+    roofline_warp = {"kernel": "k_warp<%d, f+h, float>" % Km, "bound": "hbm", "achieved": warp_gbs,
+                     "peak": hbm_peak, "unit": "GB/s", "frac": warp_gbs / hbm_peak,
+                     "traffic": recorded_traffic("k_warp<3,FH,float>", "warp.cu"),
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if peaks else "fallback",
+                     "algorithmic_bytes_per_launch": bytes_warp, "share_of_solve": share_warp}
 
     # ---------------- CPU baseline (rank 0, N = 1) ----------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_eval, t_grad = oracle_sample(w, f0, mean, U, c0, W)
-        iters = last["iters"]
+        iters = (st1["iters"] - st0["iters"]) / K
         sec = oracle_recon_seconds(t_eval, t_grad, iters, trials_per_solve)
         cpu = {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "one FP64 oracle trial evaluation (warp + projection, %.2f s) and one gradient "
-                         "evaluation (%.2f s) of frame %d, scaled by this run's %.2f trials and %d iterations "
+                         "evaluation (%.2f s) of frame %d, scaled by this run's %.2f trials and %.2f iterations "
                          "per reconstruction" % (t_eval, t_grad, W, trials_per_solve, iters)}
 
     if rank == 0:
@@ -451,11 +522,13 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "path": "pr_reconstruct with pinned host y, result copied back every step"},
             "gpu_launches": int(launches),
-            "solver": {"iters_last": last["iters"], "trials_per_solve": trials_per_solve,
+            "solver": {"iters_per_solve": (st1["iters"] - st0["iters"]) / K, "trials_per_solve": trials_per_solve,
+                       "line_search_failures": st1["line_search_failures"] - st0["line_search_failures"],
                        "stop_reason_last": last["stop_reason"], "J_last": last["J"],
                        "w_last": [float(x) for x in last["w"]], "tumor_last_mm": [float(x) for x in last["tumor"]]},
             "kernel_ms": kern,
             "roofline": roofline,
+            "roofline_warp": roofline_warp,
             "clocks": clk.summary(),
             "paper_context": {"s_per_projection": 0.24, "hardware": "Tesla C1060",
                               "workload": "NCAT 256x256x120, K=3, 200x150 projections (context only)"},

@@ -99,7 +99,7 @@ typedef struct {
     double grad_tol;     /* relative gradient-norm stop; default 1e-6 */
     double c1;           /* Armijo sufficient-decrease constant; default 1e-4 */
     double beta;         /* backtracking factor; default 0.5 */
-    int max_backtracks;  /* default 20 */
+    int max_backtracks;  /* default 8 */
     double step0_mm;     /* first trial step moves w by this many mm; default 1 */
     int cold_start;      /* 1: start from w0 with a first trial step of step0_mm;
                             0: start from the model's last accepted w and step */
@@ -289,6 +289,8 @@ typedef struct {
     long long solves;   /* solves enqueued on this model since it was loaded */
     long long trials;   /* line-search trials run by those solves */
     long long kernels;  /* CUDA kernels those solves launched */
+    long long iters;    /* accepted steps of those solves */
+    long long line_search_failures;  /* those solves that stopped on a failed line search */
 } pr_stats;
 
 /* Cumulative counters of a model (waits for its enqueued work). */

@@ -21,7 +21,7 @@ Functions and the passages they follow:
 Readings of the paper where it is silent (the CUDA path uses the same):
   * Armijo rule (Section 2.2 names it, gives no constants): sufficient
     decrease J(w - mu g; a, b) <= J(w; a, b) - c1 mu |g|^2 with c1 = 1e-4,
-    backtracking mu <- beta mu with beta = 0.5, at most 20 backtracks. The
+    backtracking mu <- beta mu with beta = 0.5, at most 8 backtracks. The
     first trial step is mu = step0_mm / |g| (moves w by step0_mm); after an
     accepted step mu the next first trial is step_growth x mu (2) if mu was
     accepted at its first trial, else step_growth_bt x mu (1). A solve
@@ -255,7 +255,7 @@ class SolveOptions:
     grad_tol: float = 1e-6
     c1: float = 1e-4
     beta: float = 0.5
-    max_backtracks: int = 20
+    max_backtracks: int = 8
     step0_mm: float = 1.0
     step_growth: float = 2.0
     step_growth_bt: float = 1.0

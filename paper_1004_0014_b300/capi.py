@@ -49,7 +49,8 @@ PR_KERNEL_BACKPROJECT, PR_KERNEL_WARP_F, PR_KERNEL_PROJECT_F = 3, 4, 5
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [("solves", ctypes.c_longlong), ("trials", ctypes.c_longlong), ("kernels", ctypes.c_longlong)]
+    _fields_ = [("solves", ctypes.c_longlong), ("trials", ctypes.c_longlong), ("kernels", ctypes.c_longlong),
+                ("iters", ctypes.c_longlong), ("line_search_failures", ctypes.c_longlong)]
 
 
 class PcaReconError(RuntimeError):
@@ -343,7 +344,8 @@ def pr_time_kernel(ctx, model_id: int, which: int, angle_rad: float, iters: int)
 def pr_model_stats(ctx, model_id: int) -> dict:
     st = Stats()
     _check(_lib.pr_model_stats(ctx, int(model_id), ctypes.byref(st)))
-    return dict(solves=st.solves, trials=st.trials, kernels=st.kernels)
+    return dict(solves=st.solves, trials=st.trials, kernels=st.kernels, iters=st.iters,
+                line_search_failures=st.line_search_failures)
 
 
 def pr_io_bytes(ctx, model_id: int):

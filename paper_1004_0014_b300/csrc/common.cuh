@@ -113,7 +113,7 @@ struct SolveState {
     int iter, bt, trials, total_bt, stop, accepted, need_grad, running;
     double tumor[3];
     int tumor_steps, pad_;
-    long long cum_solves, cum_trials;  // since the model was loaded
+    long long cum_solves, cum_trials, cum_iters, cum_lsf;  // since the model was loaded
     double mu_next;  // first trial step of the next iteration or warm-started solve (0 = none)
 };
 

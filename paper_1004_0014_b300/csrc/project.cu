@@ -256,6 +256,7 @@ __device__ void controller_project(SolveState* st, const double (&tot)[3], int p
         // next first trial: grow after a first-try acceptance, else keep
         st->mu_next = (st->bt == 0 ? st->prm.step_growth : st->prm.step_growth_bt) * st->mu;
         st->iter += 1;
+        st->cum_iters += 1;
         st->accepted = 1;
         if (fit_ab(st, tot[1], tot[2], &a, &b)) {  // step 2, Eq. 4
             st->a = a;
@@ -272,6 +273,7 @@ __device__ void controller_project(SolveState* st, const double (&tot)[3], int p
     st->total_bt += 1;
     if (st->bt > st->prm.max_bt) {
         st->stop = 3;  // PR_STOP_LINESEARCH_FAILED: w keeps its last accepted value
+        st->cum_lsf += 1;
         st->mu_next = 0.0;  // the collapsed step says nothing about the next frame
         set_loop(st, 0, h, use_graph);
         return;

@@ -388,7 +388,7 @@ void pr_default_opts(pr_solve_opts* o) {
     o->grad_tol = 1e-6;
     o->c1 = 1e-4;
     o->beta = 0.5;
-    o->max_backtracks = 20;
+    o->max_backtracks = 8;
     o->step0_mm = 1.0;
     o->cold_start = 0;
     o->loop_mode = PR_LOOP_GRAPH;
@@ -839,6 +839,8 @@ int pr_model_stats(pr_ctx* c, int id, pr_stats* out) {
     // per solve: begin, warp, project, residual-gradient, tumor; per trial:
     // warp, project, residual-gradient (the body of the loop)
     out->kernels = 5 * out->solves + 3 * out->trials;
+    out->iters = m->st_host->cum_iters;
+    out->line_search_failures = m->st_host->cum_lsf;
     return PR_OK;
 }
 

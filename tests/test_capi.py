@@ -77,7 +77,8 @@ def test_defaults_and_version(lib):
     from paper_1004_0014_b300 import capi
 
     o = capi.pr_default_opts()
-    assert (o.max_iters, o.c1, o.beta, o.max_backtracks, o.step0_mm) == (10, 1e-4, 0.5, 20, 1.0)
+    assert (o.max_iters, o.c1, o.beta, o.max_backtracks, o.step0_mm) == (10, 1e-4, 0.5, 8, 1.0)
+    assert (o.step_growth, o.step_growth_bt, o.warm_step) == (2.0, 1.0, 1)
     assert "sm_103a" in capi.pr_version()
 
 
