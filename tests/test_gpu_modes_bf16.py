@@ -1,0 +1,124 @@
+"""K = 5 models (two float4 channels per voxel) in float32 and bfloat16
+storage, and the autograd Function. For bfloat16 the oracle runs on the
+bfloat16-rounded inputs (upcast exactly), which isolates arithmetic error; the
+quantisation error against the float32 inputs is reported, not asserted."""
+
+import numpy as np
+import pytest
+
+from gpu_util import TOL_GRAD, TOL_PROJ, TOL_TUMOR_MM, TOL_W, noisy, rel, report
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).float().numpy()
+
+
+@pytest.fixture(scope="module")
+def k5():
+    import torch
+
+    from paper_1004_0014_b300 import PR_BF16, PR_F32, Context
+    from phantom import build_pca, dvf_analytic, phantom_volume, training_dvfs, tumor_centre, workload_small
+
+    w = workload_small(K=5)
+    vol, geom = w["vol"], w["geom"]
+    f0 = phantom_volume(vol).astype(np.float32)
+    pca = build_pca(training_dvfs(vol), 5)
+    mean, U = pca.mean.astype(np.float32), pca.U.astype(np.float32)
+    c0 = tumor_centre(vol)
+    ctx = Context(0)
+    models = {}
+    for name, storage, f0s, Us in (("f32", PR_F32, f0, U), ("bf16", PR_BF16, _bf16(f0), _bf16(U))):
+        mid = ctx.load_model(vol, geom, f0, mean, U, c0, storage=storage)
+        om = O.Model(vol, f0s.astype(np.float64), mean.astype(np.float64), Us.astype(np.float64), c0)
+        models[name] = (mid, om)
+    om32 = models["f32"][1]
+    th = 0.4
+    ft = O.warp(vol, om32.f0, dvf_analytic(vol, 1.0, 1.5))
+    y = noisy(O.project(vol, geom, th, ft), 0).astype(np.float32)
+    yield dict(ctx=ctx, vol=vol, geom=geom, models=models, th=th, y=y, yd=torch.from_numpy(y).cuda(),
+               sigma=pca.sigma, pca=pca)
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["f32", "bf16"])
+def test_k5_warp_cost_gradient(k5, name):
+    mid, om = k5["models"][name]
+    ctx, vol = k5["ctx"], k5["vol"]
+    w = np.array([0.5, -0.2, 0.1, 0.05, -0.03])
+    f, h = ctx.warp(mid, w)
+    x = O.dvf(vol, om.mean, om.U, w)
+    ef = rel(f.cpu().numpy(), O.warp(vol, om.f0, x))
+    assert ef < 1e-5
+    go, Jo, _ = O.gradient(om, k5["geom"], k5["th"], w, 1.01, -0.002, k5["y"].astype(np.float64))
+    for mode in (0, 1):
+        J, g = ctx.cost_grad(mid, k5["yd"], k5["th"], w, 1.01, -0.002, mode)
+        report("k5_cost_grad_" + name, mode=mode, f_rel=ef, J_rel=abs(J - Jo) / Jo, g_rel=rel(g, go))
+        assert abs(J - Jo) / Jo < TOL_PROJ
+        assert rel(g, go) < TOL_GRAD
+
+
+@pytest.mark.parametrize("name", ["f32", "bf16"])
+def test_k5_solve(k5, name):
+    from paper_1004_0014_b300 import default_opts
+
+    mid, om = k5["models"][name]
+    res = k5["ctx"].reconstruct(mid, k5["y"], k5["th"], default_opts(max_iters=12, cold_start=1))
+    ores = O.reconstruct(om, k5["geom"], k5["th"], k5["y"].astype(np.float64), np.zeros(5),
+                         O.SolveOptions(max_iters=12))
+    et = float(np.max(np.abs(res["tumor"] - ores.tumor)))
+    report("k5_solve_" + name, w_rel=rel(res["w"], ores.w), J_rel=abs(res["J"] - ores.J) / ores.J, tumor_mm=et,
+           backtracks=res["backtracks"], oracle_backtracks=ores.backtracks)
+    assert res["iters"] == ores.iters
+    assert abs(res["J"] - ores.J) / ores.J < TOL_PROJ
+    assert rel(res["w"], ores.w) < TOL_W
+    assert et < TOL_TUMOR_MM
+    if name == "bf16":  # quantisation error of the bfloat16 model (reported)
+        om32 = k5["models"]["f32"][1]
+        o32 = O.reconstruct(om32, k5["geom"], k5["th"], k5["y"].astype(np.float64), np.zeros(5),
+                            O.SolveOptions(max_iters=12))
+        report("k5_bf16_quantisation", w_rel=rel(res["w"], o32.w), J_rel=abs(res["J"] - o32.J) / o32.J,
+               tumor_mm=float(np.max(np.abs(res["tumor"] - o32.tumor))))
+
+
+def test_autograd_matches_finite_differences_and_oracle(k5):
+    """32 seeded draws w ~ N(0, sigma_k): the autograd gradient of a random
+    linear functional of p equals the oracle's (P^T c) . h_k within the
+    gradient tolerance, and central differences with h = 1e-3 within the
+    finite-difference error."""
+    import torch
+
+    from paper_1004_0014_b300.autograd import proj_warp
+
+    mid, om = k5["models"]["bf16"]
+    ctx, vol, geom, th = k5["ctx"], k5["vol"], k5["geom"], k5["th"]
+    rng = np.random.default_rng(2024)
+    c = torch.from_numpy(rng.standard_normal((geom.nv, geom.nu)).astype(np.float32)).cuda()
+    worst_o, worst_fd = 0.0, 0.0
+    for i in range(32):
+        wv = rng.standard_normal(5) * k5["sigma"]
+        w = torch.tensor(wv, dtype=torch.float64, requires_grad=True)
+        p = proj_warp(ctx, mid, w, th)
+        (p * c).sum().backward()
+        g = w.grad.numpy()
+        x = O.dvf(vol, om.mean, om.U, wv)
+        hk = O.warp_jac(vol, om.f0, x, om.U)
+        bp = O.backproject(vol, geom, th, c.cpu().numpy().astype(np.float64))
+        go = np.array([np.sum(bp * hk[k]) for k in range(5)])
+        worst_o = max(worst_o, rel(g, go))
+        fd = np.empty(5)
+        for k in range(5):
+            e = np.zeros(5)
+            e[k] = 1e-3
+            lp = float((ctx.forward(mid, wv + e, th).double() * c.double()).sum())
+            lm = float((ctx.forward(mid, wv - e, th).double() * c.double()).sum())
+            fd[k] = (lp - lm) / 2e-3
+        worst_fd = max(worst_fd, rel(g, fd))
+    report("autograd_32", oracle_rel_max=worst_o, fd_rel_max=worst_fd)
+    assert worst_o < TOL_GRAD
+    assert worst_fd < 1e-2

@@ -1,0 +1,70 @@
+"""Parity at the paper-scale sizes (256x256x120 at 2x2x2.5 mm, K=3, 512x384
+detector at 0.776 mm, 1 mm ray step), in the configuration the benchmark
+times: the FP64 oracle computes the whole projection and gradient here (a few
+seconds each), and a short on-device solve is checked against the oracle's."""
+
+import math
+
+import numpy as np
+import pytest
+
+from gpu_util import TOL_GRAD, TOL_PROJ, TOL_TUMOR_MM, TOL_W, rel, report
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def paper():
+    import torch
+
+    from paper_1004_0014_b300 import Context
+    from phantom import (build_pca, dvf_analytic, phantom_volume, standard_normal, training_dvfs,
+                         tumor_centre, workload_paper)
+
+    w = workload_paper()
+    vol, geom = w["vol"], w["geom"]
+    f0 = phantom_volume(vol).astype(np.float32)
+    pca = build_pca(training_dvfs(vol), w["K"])
+    mean, U = pca.mean.astype(np.float32), pca.U.astype(np.float32)
+    c0 = tumor_centre(vol)
+    om = O.Model(vol, f0.astype(np.float64), mean.astype(np.float64), U.astype(np.float64), c0)
+    j = 7
+    th, t = math.radians(w["frame_angle_deg"](j)), w["frame_time"](j)
+    pt = O.project(vol, geom, th, O.warp(vol, om.f0, dvf_analytic(vol, t, w["scale"])))
+    y = (pt + 0.01 * pt * standard_normal(w["frame_seed"](j), pt.shape)).astype(np.float32)
+    ctx = Context(0)
+    mid = ctx.load_model(vol, geom, f0, mean, U, c0)
+    yield dict(w=w, vol=vol, geom=geom, om=om, th=th, y=y, yd=torch.from_numpy(y).cuda(), ctx=ctx, mid=mid)
+    ctx.close()
+
+
+def test_paper_scale_cost_and_gradient(paper):
+    p = paper
+    w, a, b = np.array([-1.0, 0.2, 0.05]), 1.01, -0.005
+    go, Jo, po = O.gradient(p["om"], p["geom"], p["th"], w, a, b, p["y"].astype(np.float64))
+    for mode in (0, 1):
+        J, g, pd = p["ctx"].cost_grad(p["mid"], p["yd"], p["th"], w, a, b, mode, return_p=True)
+        ep = rel(pd.cpu().numpy(), po)
+        report("paper_cost_grad", mode=mode, p_rel=ep, J_rel=abs(J - Jo) / Jo, g_rel=rel(g, go))
+        assert ep < TOL_PROJ
+        assert abs(J - Jo) / Jo < TOL_PROJ
+        assert rel(g, go) < TOL_GRAD
+
+
+def test_paper_scale_solve(paper):
+    from paper_1004_0014_b300 import default_opts
+
+    p = paper
+    it = 5
+    res = p["ctx"].reconstruct(p["mid"], p["y"], p["th"], default_opts(max_iters=it, cold_start=1))
+    ores = O.reconstruct(p["om"], p["geom"], p["th"], p["y"].astype(np.float64), np.zeros(3),
+                         O.SolveOptions(max_iters=it))
+    et = float(np.max(np.abs(res["tumor"] - ores.tumor)))
+    report("paper_solve", iters=res["iters"], J_rel=abs(res["J"] - ores.J) / ores.J, w_rel=rel(res["w"], ores.w),
+           tumor_mm=et, trials=res["trials"], oracle_backtracks=ores.backtracks, backtracks=res["backtracks"])
+    assert res["iters"] == ores.iters == it
+    assert res["backtracks"] == ores.backtracks
+    assert abs(res["J"] - ores.J) / ores.J < TOL_PROJ
+    assert rel(res["w"], ores.w) < TOL_W
+    assert et < TOL_TUMOR_MM
