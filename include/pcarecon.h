@@ -190,6 +190,47 @@ int pr_reconstruct_async(pr_ctx* ctx, int model_id, const float* y_dev, double a
 /* Wait for the model's last enqueued solve and copy its result to *out. */
 int pr_fetch_result(pr_ctx* ctx, int model_id, pr_result* out);
 
+/* ---- serving: continuous submission of frames from many patients ----
+ *
+ * Requests are admitted into `slots` concurrent solve slots (one CUDA stream
+ * each) as soon as a slot frees up and no earlier frame of the same model is
+ * still in flight; different models' solves then overlap on the GPU, and each
+ * model's frames run in submission order, each warm-started from the previous
+ * (Section 4). Models are admitted to the device by pr_load_model's HBM
+ * budget check (PR_EADMIT) and can be loaded and released while serving. The
+ * serving worker is a host thread of the context; while it runs, the
+ * synchronous calls (pr_reconstruct, pr_warp, ...) must not be used on a
+ * model that has submitted frames outstanding. */
+typedef struct {
+    uint64_t tag;       /* the caller's tag from pr_submit */
+    int model_id;
+    int status;         /* PR_OK or the error of this solve */
+    pr_result result;
+    double queue_ms;    /* submit to dispatch into a slot (host clock) */
+    double gpu_ms;      /* the solve's device time on its slot stream (CUDA events) */
+    double latency_ms;  /* submit to completion (host clock) */
+} pr_served;
+
+/* Start the serving worker with `slots` (1..64) concurrent solve streams
+ * (after pr_serve_stop this restarts it; results not yet polled are dropped). */
+int pr_serve_start(pr_ctx* ctx, int slots);
+
+/* Queue one frame: y [nv][nu] float32 (host, copied before return), gantry
+ * angle, options (NULL = defaults; the host loop mode is not allowed), and a
+ * tag returned with the result. Errors: PR_EINVAL, PR_ENOMODEL, PR_ECUDA
+ * (an earlier device error of the worker). */
+int pr_submit(pr_ctx* ctx, int model_id, const float* y, double angle_rad, const pr_solve_opts* opts,
+              uint64_t tag);
+
+/* Take one finished frame: waits up to timeout_ms (0 = do not wait, < 0 =
+ * wait indefinitely while frames are outstanding). PR_OK with *out filled,
+ * PR_ETIMEOUT if none finished in time, PR_EINVAL if nothing is outstanding. */
+int pr_poll(pr_ctx* ctx, int timeout_ms, pr_served* out);
+
+/* Wait for every submitted frame to finish (results stay pollable) and stop
+ * the worker. */
+int pr_serve_stop(pr_ctx* ctx);
+
 /* Read / overwrite a model's warm-start coefficients (K doubles, host).
  * pr_set_state also forgets the warm-start step (the next solve's first
  * trial moves w by step0_mm). */

@@ -160,6 +160,19 @@ class Context:
     def tumor(self, mid: int, w, tol: float = 1e-6, max_iter: int = 100):
         return capi.pr_tumor(self._ctx, mid, w, tol, max_iter)
 
+    # --- serving -------------------------------------------------------------
+    def serve_start(self, slots: int = 4):
+        capi.pr_serve_start(self._ctx, slots)
+
+    def submit(self, mid: int, y, angle_rad: float, opts: SolveOpts | None = None, tag: int = 0):
+        capi.pr_submit(self._ctx, mid, y, angle_rad, opts, tag)
+
+    def poll(self, timeout_ms: int = -1):
+        return capi.pr_poll(self._ctx, timeout_ms)
+
+    def serve_stop(self):
+        capi.pr_serve_stop(self._ctx)
+
     # --- measurement -------------------------------------------------------
     def time_kernel(self, mid: int, which: int, angle_rad: float = 0.0, iters: int = 20) -> float:
         return capi.pr_time_kernel(self._ctx, mid, which, angle_rad, iters)

@@ -41,7 +41,7 @@ EXPORTED = [
     "pr_release_model", "pr_model_footprint", "pr_reconstruct", "pr_reconstruct_async",
     "pr_fetch_result", "pr_get_state", "pr_set_state", "pr_warp", "pr_project", "pr_backproject",
     "pr_forward", "pr_vjp", "pr_cost_grad", "pr_tumor", "pr_time_kernel", "pr_model_stats",
-    "pr_io_bytes", "pr_cost_grad_static",
+    "pr_io_bytes", "pr_cost_grad_static", "pr_serve_start", "pr_submit", "pr_poll", "pr_serve_stop",
 ]
 
 PR_KERNEL_WARP_FH, PR_KERNEL_PROJECT_FH, PR_KERNEL_REGRAD = 0, 1, 2
@@ -97,6 +97,18 @@ class Result(ctypes.Structure):
                     tumor=np.array(self.tumor_xyz[:]), tumor_steps=self.tumor_steps, mu=self.mu)
 
 
+class Served(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("model_id", ctypes.c_int), ("status", ctypes.c_int),
+                ("result", Result), ("queue_ms", ctypes.c_double), ("gpu_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        d = self.result.as_dict()
+        d.update(tag=self.tag, model_id=self.model_id, status=self.status, queue_ms=self.queue_ms,
+                 gpu_ms=self.gpu_ms, latency_ms=self.latency_ms)
+        return d
+
+
 _lib = None
 _P = ctypes.c_void_p
 _D = ctypes.c_double
@@ -140,6 +152,10 @@ def load_library(path: str | None = None):
         "pr_model_stats": (_I, [_P, _I, ctypes.POINTER(Stats)]),
         "pr_io_bytes": (_I, [_P, _I, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
         "pr_cost_grad_static": (_I, [_I, _P, _P, _P, _P, _I, _I, _D, _D, _P]),
+        "pr_serve_start": (_I, [_P, _I]),
+        "pr_submit": (_I, [_P, _I, _P, _D, ctypes.POINTER(SolveOpts), ctypes.c_uint64]),
+        "pr_poll": (_I, [_P, _I, ctypes.POINTER(Served)]),
+        "pr_serve_stop": (_I, [_P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -362,3 +378,27 @@ def pr_cost_grad_static(device: int, stream, p_dev, q_dev, y_dev, R: int, K: int
     _check(_lib.pr_cost_grad_static(int(device), s, _dev(p_dev, "p_dev"), _dev(q_dev, "q_dev"),
                                     _dev(y_dev, "y_dev"), int(R), int(K), float(a), float(b),
                                     _dev(out_dev, "out_dev")))
+
+
+def pr_serve_start(ctx, slots: int = 4):
+    _check(_lib.pr_serve_start(ctx, int(slots)))
+
+
+def pr_submit(ctx, model_id: int, y, angle_rad: float, opts: SolveOpts | None = None, tag: int = 0):
+    y = np.ascontiguousarray(np.asarray(y, dtype=np.float32))
+    _check(_lib.pr_submit(ctx, int(model_id), ctypes.c_void_p(y.ctypes.data), float(angle_rad),
+                          ctypes.byref(opts) if opts is not None else None, ctypes.c_uint64(tag)))
+
+
+def pr_poll(ctx, timeout_ms: int = -1):
+    """Next finished frame as a dict, or None on timeout."""
+    out = Served()
+    rc = _lib.pr_poll(ctx, int(timeout_ms), ctypes.byref(out))
+    if rc == PR_ETIMEOUT:
+        return None
+    _check(rc)
+    return out.as_dict()
+
+
+def pr_serve_stop(ctx):
+    _check(_lib.pr_serve_stop(ctx))

@@ -9,8 +9,14 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <chrono>
+#include <condition_variable>
+#include <deque>
 #include <map>
+#include <mutex>
+#include <set>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -82,8 +88,49 @@ struct Model {
 
 int pr::set_last_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
+namespace {
+
+// Serving: requests wait in a FIFO; a worker thread moves each into a free slot
+// (its own CUDA stream) as soon as one frees up and no earlier frame of the
+// same patient is still in flight, so different patients' solves overlap on
+// the GPU while each patient's frames stay in order for the warm start.
+struct ServeRequest {
+    int model = 0;
+    uint64_t tag = 0;
+    double angle = 0.0;
+    pr_solve_opts opts{};
+    std::vector<float> y;
+    std::chrono::steady_clock::time_point t_submit;
+};
+
+struct ServeSlot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t start = nullptr, done = nullptr;
+    SolveState* host_state = nullptr;  // pinned
+    bool busy = false;
+    ServeRequest req;
+    std::chrono::steady_clock::time_point t_dispatch;
+};
+
+struct Serve {
+    std::thread worker;
+    std::condition_variable cv_work, cv_done;
+    std::deque<ServeRequest> pending;
+    std::deque<pr_served> done;
+    std::vector<ServeSlot> slots;
+    std::set<int> in_flight;  // models with a dispatched solve
+    long long outstanding = 0;  // submitted and not yet polled into `done`
+    bool stop = false;
+    int error = 0;
+    std::string error_msg;
+};
+
+}  // namespace
+
 struct pr_ctx {
     int device = 0;
+    std::mutex mu;           // models map and serving state (the worker thread reads both)
+    Serve* serve = nullptr;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     size_t budget = 0, used = 0;
@@ -207,7 +254,7 @@ size_t partial_rows(const Model& m) {
     return r > c ? r : c;
 }
 
-int write_params(pr_ctx* c, Model* m, double angle, const pr_solve_opts* o) {
+int write_params(pr_ctx* c, Model* m, double angle, const pr_solve_opts* o, cudaStream_t stream) {
     SolveParams prm;
     memset(&prm, 0, sizeof prm);
     prm.rg = make_rg(m->vol, m->geom, angle);
@@ -227,7 +274,7 @@ int write_params(pr_ctx* c, Model* m, double angle, const pr_solve_opts* o) {
     prm.cold_start = o->cold_start ? 1 : 0;
     // Pageable source: the copy is staged before cudaMemcpyAsync returns, so
     // back-to-back asynchronous solves cannot see a later solve's parameters.
-    CK(cudaMemcpyAsync(&m->st->prm, &prm, sizeof prm, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(&m->st->prm, &prm, sizeof prm, cudaMemcpyHostToDevice, stream));
     return PR_OK;
 }
 
@@ -327,7 +374,7 @@ int enqueue_solve(pr_ctx* c, Model* m, double angle, const pr_solve_opts* opts) 
         pr_default_opts(&o);
     if (!opts_ok(&o)) return fail(PR_EINVAL, "invalid solve options");
     if (!isfinite(angle)) return fail(PR_EINVAL, "angle is not finite");
-    int rc = write_params(c, m, angle, &o);
+    int rc = write_params(c, m, angle, &o, c->stream);
     if (rc) return rc;
     if (o.loop_mode == PR_LOOP_HOST) return host_loop(c, m, o.max_iters, o.max_backtracks);
     if (!m->exec) {
@@ -372,6 +419,124 @@ int set_rg(pr_ctx* c, RayGeom* dst, const pr_volume_desc& v, const pr_geometry& 
     Model* m = find((c), (id));                                                \
     if (!m) return fail(PR_ENOMODEL, "unknown model id %d", (int)(id));        \
     CK(cudaSetDevice((c)->device))
+
+double ms_between(std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+// Worker: retire finished slots, then fill free slots with the oldest request
+// whose model has nothing in flight. Runs until stopped and idle.
+void serve_loop(pr_ctx* c) {
+    cudaSetDevice(c->device);
+    Serve* sv = c->serve;
+    std::unique_lock<std::mutex> lock(c->mu);
+    for (;;) {
+        bool busy = false, progressed = false;
+        for (ServeSlot& sl : sv->slots) {
+            if (!sl.busy) continue;
+            cudaError_t q = cudaEventQuery(sl.done);
+            if (q == cudaErrorNotReady) {
+                busy = true;
+                continue;
+            }
+            pr_served out;
+            memset(&out, 0, sizeof out);
+            out.tag = sl.req.tag;
+            out.model_id = sl.req.model;
+            Model* m = find(c, sl.req.model);
+            if (q != cudaSuccess) {
+                out.status = PR_ECUDA;
+                sv->error = PR_ECUDA;
+                sv->error_msg = std::string("served solve failed: ") + cudaGetErrorString(q);
+            } else if (m) {
+                fill_result(m, *sl.host_state, &out.result);
+                float g = 0.0f;
+                cudaEventElapsedTime(&g, sl.start, sl.done);
+                out.gpu_ms = g;
+            }
+            auto now = std::chrono::steady_clock::now();
+            out.queue_ms = ms_between(sl.req.t_submit, sl.t_dispatch);
+            out.latency_ms = ms_between(sl.req.t_submit, now);
+            sv->in_flight.erase(sl.req.model);
+            sl.busy = false;
+            sl.req.y.clear();
+            sv->done.push_back(out);
+            sv->cv_done.notify_all();
+            progressed = true;
+        }
+        for (ServeSlot& sl : sv->slots) {
+            if (sl.busy || sv->error) continue;
+            auto it = sv->pending.begin();
+            while (it != sv->pending.end() && sv->in_flight.count(it->model)) ++it;
+            if (it == sv->pending.end()) break;
+            Model* m = find(c, it->model);
+            sl.req = std::move(*it);
+            sv->pending.erase(it);
+            sl.t_dispatch = std::chrono::steady_clock::now();
+            cudaError_t e = cudaSuccess;
+            if (!m) {
+                e = cudaErrorInvalidValue;
+            } else {
+                e = cudaEventRecord(sl.start, sl.stream);
+                if (!e) e = cudaMemcpyAsync(m->y, sl.req.y.data(), (size_t)m->R * 4, cudaMemcpyHostToDevice, sl.stream);
+                if (!e && write_params(c, m, sl.req.angle, &sl.req.opts, sl.stream) != PR_OK) e = cudaErrorUnknown;
+                if (!e) e = cudaGraphLaunch(m->exec, sl.stream);
+                if (!e) e = cudaMemcpyAsync(sl.host_state, m->st, sizeof(SolveState), cudaMemcpyDeviceToHost, sl.stream);
+                if (!e) e = cudaEventRecord(sl.done, sl.stream);
+            }
+            if (e) {
+                sv->error = PR_ECUDA;
+                sv->error_msg = std::string("dispatch failed: ") + cudaGetErrorString(e);
+                pr_served out;
+                memset(&out, 0, sizeof out);
+                out.tag = sl.req.tag;
+                out.model_id = sl.req.model;
+                out.status = PR_ECUDA;
+                sv->done.push_back(out);
+                sv->cv_done.notify_all();
+                continue;
+            }
+            sv->in_flight.insert(sl.req.model);
+            sl.busy = true;
+            busy = true;
+            progressed = true;
+        }
+        if (sv->stop && !busy && sv->pending.empty()) break;
+        if (busy && !progressed) {
+            // a solve is running: poll its event again shortly
+            lock.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            lock.lock();
+        } else if (!busy && !progressed) {
+            sv->cv_work.wait_for(lock, std::chrono::milliseconds(50));
+        }
+    }
+}
+
+int serve_stop(pr_ctx* c) {
+    if (!c->serve) return PR_OK;
+    {
+        std::lock_guard<std::mutex> lock(c->mu);
+        c->serve->stop = true;
+    }
+    c->serve->cv_work.notify_all();
+    if (c->serve->worker.joinable()) c->serve->worker.join();
+    return PR_OK;
+}
+
+void serve_free(pr_ctx* c) {
+    if (!c->serve) return;
+    serve_stop(c);
+    for (ServeSlot& sl : c->serve->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.start) cudaEventDestroy(sl.start);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.host_state) cudaFreeHost(sl.host_state);
+    }
+    delete c->serve;
+    c->serve = nullptr;
+}
 
 }  // namespace
 
@@ -432,6 +597,7 @@ int pr_create(pr_ctx** out, int device, void* stream, size_t hbm_budget_bytes) {
 void pr_destroy(pr_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
+    serve_free(c);
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto& kv : c->models) free_model(kv.second);
     c->models.clear();
@@ -453,8 +619,13 @@ int pr_load_model(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
     if (!f0 || !mean_dvf || !U || !tumor_ref_xyz) return fail(PR_EINVAL, "null input array");
     CK(cudaSetDevice(c->device));
     size_t need = model_bytes(*vol, *geom, K, storage);
-    if (c->used + need > c->budget)
-        return fail(PR_EADMIT, "model needs %zu bytes, %zu of %zu budget in use", need, c->used, c->budget);
+    size_t used_now;
+    {
+        std::lock_guard<std::mutex> lock(c->mu);
+        used_now = c->used;
+    }
+    if (used_now + need > c->budget)
+        return fail(PR_EADMIT, "model needs %zu bytes, %zu of %zu budget in use", need, used_now, c->budget);
 
     Model* m = new Model;
     m->vol = *vol;
@@ -554,6 +725,7 @@ int pr_load_model(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
         free_model(m);
         return rc;
     }
+    std::lock_guard<std::mutex> lock(c->mu);
     m->id = c->next_id++;
     c->used += m->bytes;
     c->models[m->id] = m;
@@ -564,8 +736,16 @@ int pr_load_model(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
 int pr_release_model(pr_ctx* c, int id) {
     GET_MODEL(c, id, m);
     CK(cudaStreamSynchronize(c->stream));
-    c->used -= m->bytes;
-    c->models.erase(id);
+    {
+        std::lock_guard<std::mutex> lock(c->mu);
+        if (c->serve) {
+            bool queued = c->serve->in_flight.count(id) > 0;
+            for (const ServeRequest& r : c->serve->pending) queued = queued || r.model == id;
+            if (queued) return fail(PR_EINVAL, "model %d has served frames outstanding", id);
+        }
+        c->used -= m->bytes;
+        c->models.erase(id);
+    }
     free_model(m);
     return PR_OK;
 }
@@ -850,6 +1030,86 @@ int pr_io_bytes(pr_ctx* c, int id, size_t* h2d, size_t* d2h) {
     *h2d = (size_t)m->R * 4 + sizeof(SolveParams);
     *d2h = sizeof(SolveState);
     return PR_OK;
+}
+
+int pr_serve_start(pr_ctx* c, int slots) {
+    if (!c) return fail(PR_EINVAL, "null context");
+    if (slots < 1 || slots > 64) return fail(PR_EINVAL, "slots must be 1..64");
+    if (c->serve && !c->serve->stop) return fail(PR_EINVAL, "serving already started");
+    if (c->serve) serve_free(c);  // restart after pr_serve_stop: untaken results are dropped
+    CK(cudaSetDevice(c->device));
+    Serve* sv = new Serve;
+    sv->slots.resize(slots);
+    for (ServeSlot& sl : sv->slots) {
+        cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        if (!e) e = cudaEventCreate(&sl.start);
+        if (!e) e = cudaEventCreate(&sl.done);
+        if (!e) e = cudaHostAlloc((void**)&sl.host_state, sizeof(SolveState), cudaHostAllocDefault);
+        if (e) {
+            c->serve = sv;
+            serve_free(c);
+            return fail(PR_ECUDA, "serving set-up failed: %s", cudaGetErrorString(e));
+        }
+    }
+    c->serve = sv;
+    sv->worker = std::thread(serve_loop, c);
+    return PR_OK;
+}
+
+int pr_submit(pr_ctx* c, int id, const float* y, double angle, const pr_solve_opts* opts, uint64_t tag) {
+    GET_MODEL(c, id, m);
+    if (!c->serve) return fail(PR_EINVAL, "serving not started (pr_serve_start)");
+    if (!y) return fail(PR_EINVAL, "null y");
+    pr_solve_opts o;
+    if (opts)
+        o = *opts;
+    else
+        pr_default_opts(&o);
+    if (!opts_ok(&o) || o.loop_mode != PR_LOOP_GRAPH) return fail(PR_EINVAL, "invalid solve options for serving");
+    if (!isfinite(angle)) return fail(PR_EINVAL, "angle is not finite");
+    if (!m->exec) TRY(build_graph(c, m));
+    ServeRequest r;
+    r.model = id;
+    r.tag = tag;
+    r.angle = angle;
+    r.opts = o;
+    r.y.assign(y, y + m->R);
+    r.t_submit = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lock(c->mu);
+        if (c->serve->error) return fail(c->serve->error, "%s", c->serve->error_msg.c_str());
+        c->serve->pending.push_back(std::move(r));
+        c->serve->outstanding += 1;
+    }
+    c->serve->cv_work.notify_all();
+    return PR_OK;
+}
+
+int pr_poll(pr_ctx* c, int timeout_ms, pr_served* out) {
+    if (!c || !out) return fail(PR_EINVAL, "null argument");
+    if (!c->serve) return fail(PR_EINVAL, "serving not started (pr_serve_start)");
+    std::unique_lock<std::mutex> lock(c->mu);
+    Serve* sv = c->serve;
+    if (sv->done.empty() && sv->outstanding == 0) return fail(PR_EINVAL, "no frames outstanding");
+    auto ready = [&] { return !sv->done.empty(); };
+    if (timeout_ms < 0)
+        sv->cv_done.wait(lock, ready);
+    else if (timeout_ms > 0)
+        sv->cv_done.wait_for(lock, std::chrono::milliseconds(timeout_ms), ready);
+    if (sv->done.empty()) return fail(PR_ETIMEOUT, "no frame finished within %d ms", timeout_ms);
+    *out = sv->done.front();
+    sv->done.pop_front();
+    sv->outstanding -= 1;
+    return out->status == PR_OK ? PR_OK : fail(out->status, "%s", sv->error_msg.c_str());
+}
+
+int pr_serve_stop(pr_ctx* c) {
+    if (!c) return fail(PR_EINVAL, "null context");
+    if (!c->serve) return fail(PR_EINVAL, "serving not started");
+    serve_stop(c);
+    // the worker is gone; results stay pollable, so keep the structure but
+    // allow a restart only after the remaining results are taken
+    return c->serve->error ? fail(c->serve->error, "%s", c->serve->error_msg.c_str()) : PR_OK;
 }
 
 }  // extern "C"

@@ -1,0 +1,115 @@
+"""Serving: frames of several patients (different volume sizes) submitted
+together run concurrently in stream slots; every frame's result must be the
+same as when that patient's frames are solved alone, one after the other
+(the kernels' reductions are deterministic, so the same means bitwise)."""
+
+import numpy as np
+import pytest
+
+from gpu_util import noisy
+from oracle import oracle as O
+from phantom import Geometry, Volume, build_pca, dvf_analytic, phantom_volume, training_dvfs, tumor_centre
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(48, 48, 40), (64, 64, 64), (40, 36, 30)]
+GEOM = Geometry(1000.0, 1500.0, 96, 80, 2.0, 2.0, 0.0)
+FRAMES = 6
+
+
+def _patient(i):
+    nx, ny, nz = SHAPES[i]
+    vol = Volume(nx, ny, nz, 4.0, 4.0, 5.0)
+    f0 = phantom_volume(vol).astype(np.float32)
+    pca = build_pca(training_dvfs(vol), 3)
+    frames = []
+    for j in range(FRAMES):
+        th, t = np.deg2rad(7.0 * j + 30 * i), 0.5 + j / 6.0
+        ft = O.warp(vol, f0.astype(np.float64), dvf_analytic(vol, t, 1.5))
+        g = Geometry(GEOM.sad, GEOM.sdd, GEOM.nu, GEOM.nv, GEOM.du, GEOM.dv, 0.5 * min(vol.dx, vol.dy, vol.dz))
+        frames.append((th, noisy(O.project(vol, g, th, ft), 100 * i + j).astype(np.float32)))
+    return dict(vol=vol, f0=f0, mean=pca.mean.astype(np.float32), U=pca.U.astype(np.float32),
+                c0=tumor_centre(vol), frames=frames)
+
+
+@pytest.fixture(scope="module")
+def patients():
+    return [_patient(i) for i in range(len(SHAPES))]
+
+
+def _opts():
+    from paper_1004_0014_b300 import default_opts
+
+    return default_opts(max_iters=6)
+
+
+def test_served_results_equal_solo_results(patients):
+    from paper_1004_0014_b300 import Context
+
+    ctx = Context(0)
+    try:
+        mids = [ctx.load_model(p["vol"], GEOM, p["f0"], p["mean"], p["U"], p["c0"]) for p in patients]
+        solo = {}
+        for i, (mid, p) in enumerate(zip(mids, patients)):
+            ctx.set_state(mid, np.zeros(3))
+            for j, (th, y) in enumerate(p["frames"]):
+                solo[(i, j)] = ctx.reconstruct(mid, y, th, _opts())
+        for mid in mids:
+            ctx.set_state(mid, np.zeros(3))
+        ctx.serve_start(slots=3)
+        # interleave the patients' frames as they would arrive
+        for j in range(FRAMES):
+            for i, (mid, p) in enumerate(zip(mids, patients)):
+                th, y = p["frames"][j]
+                ctx.submit(mid, y, th, _opts(), tag=1000 * i + j)
+        served = {}
+        while len(served) < len(solo):
+            r = ctx.poll(timeout_ms=60000)
+            assert r is not None and r["status"] == 0
+            served[(r["tag"] // 1000, r["tag"] % 1000)] = r
+            assert r["latency_ms"] >= r["gpu_ms"] * 0.999 >= 0.0
+        ctx.serve_stop()
+        for key, a in solo.items():
+            b = served[key]
+            for k in ("w", "a", "b", "J", "tumor", "iters", "trials"):
+                assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), (key, k)
+    finally:
+        ctx.close()
+
+
+def test_admission_and_release_rules(patients):
+    from paper_1004_0014_b300 import Context, PcaReconError
+
+    p0, p1 = patients[0], patients[1]
+    probe = Context(0)
+    mid = probe.load_model(p0["vol"], GEOM, p0["f0"], p0["mean"], p0["U"], p0["c0"])
+    need0 = probe.footprint(mid)
+    probe.close()
+    # a budget that holds patient 0 but not patient 0 and 1 together
+    ctx = Context(0, hbm_budget_bytes=int(need0 * 1.5))
+    try:
+        a = ctx.load_model(p0["vol"], GEOM, p0["f0"], p0["mean"], p0["U"], p0["c0"])
+        with pytest.raises(PcaReconError) as e:
+            ctx.load_model(p1["vol"], GEOM, p1["f0"], p1["mean"], p1["U"], p1["c0"])
+        assert e.value.code == -3
+        ctx.serve_start(slots=2)
+        with pytest.raises(PcaReconError):
+            ctx.poll(timeout_ms=0)  # nothing outstanding
+        th, y = p0["frames"][0]
+        ctx.submit(a, y, th, _opts(), tag=7)
+        with pytest.raises(PcaReconError) as e:
+            ctx.release_model(a)  # frames outstanding
+        assert e.value.code == -1
+        r = ctx.poll(timeout_ms=60000)
+        assert r["tag"] == 7 and r["status"] == 0
+        ctx.serve_stop()
+        ctx.release_model(a)
+        # the freed budget admits the other patient
+        b = ctx.load_model(p1["vol"], GEOM, p1["f0"], p1["mean"], p1["U"], p1["c0"])
+        ctx.serve_start(slots=2)
+        th, y = p1["frames"][0]
+        ctx.submit(b, y, th, _opts(), tag=8)
+        assert ctx.poll(timeout_ms=60000)["tag"] == 8
+        ctx.serve_stop()
+    finally:
+        ctx.close()
