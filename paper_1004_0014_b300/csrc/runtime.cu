@@ -236,22 +236,25 @@ void free_model(Model* m) {
     delete m;
 }
 
-size_t model_bytes(const pr_volume_desc& v, const pr_geometry& g, int K, int storage) {
-    size_t n = (size_t)v.nx * v.ny * v.nz, np = pad_voxels(v), R = (size_t)g.nu * g.nv;
-    size_t ts = storage == PR_BF16 ? 2 : 4;
-    int nch = fh_channels(K);
-    int nb = project_blocks(g.nu, g.nv);
-    int rb = reduce_blocks();
-    size_t rows = (size_t)(nb > rb ? nb : rb);
-    return np * ts + 3 * n * 4 + 3 * (size_t)K * n * ts + np * nch * 4 + np * 4 + R * 4 * (3 + K) + n * 4 +
-           rows * kMaxMom * 8 + 4096;
-}
-
 // Scratch rows for block partials: the largest grid among the reductions.
-size_t partial_rows(const Model& m) {
-    size_t a = project_blocks(m.geom.nu, m.geom.nv), b = reduce_blocks(), c = backproject_blocks(m.md.vd);
+size_t partial_rows(const pr_geometry& g, const VolDev& vd) {
+    size_t a = project_blocks(g.nu, g.nv), b = reduce_blocks(), c = backproject_blocks(vd);
     size_t r = a > b ? a : b;
     return r > c ? r : c;
+}
+size_t partial_rows(const Model& m) { return partial_rows(m.geom, m.md.vd); }
+
+// Device bytes pr_load_model allocates for a model (the admission check uses
+// this before allocating; the gradient-adjoint scratch of K x N floats is
+// allocated on first use and added to the footprint then).
+size_t model_bytes(const pr_volume_desc& v, const pr_geometry& g, int K, int storage) {
+    VolDev vd = make_vd(v);
+    size_t n = (size_t)vd.n, np = (size_t)vd.np, R = (size_t)g.nu * g.nv;
+    size_t ts = storage == PR_BF16 ? 2 : 4;
+    size_t nch = (size_t)fh_channels(K);
+    return np * ts + 3 * n * 4 + 3 * (size_t)K * n * ts + np * nch * 4 + np * 4 + R * 4 + R * K * 4 + R * 4 +
+           R * 4 + n * 4 + partial_rows(g, vd) * kMaxMom * 8 + 64 + sizeof(SolveState) + 64 + 128 +
+           sizeof(RayGeom) + 16 + (size_t)project_blocks(g.nu, g.nv) * sizeof(int) + sizeof(Support);
 }
 
 int write_params(pr_ctx* c, Model* m, double angle, const pr_solve_opts* o, cudaStream_t stream) {

@@ -82,11 +82,12 @@ def test_admission_and_release_rules(patients):
 
     p0, p1 = patients[0], patients[1]
     probe = Context(0)
-    mid = probe.load_model(p0["vol"], GEOM, p0["f0"], p0["mean"], p0["U"], p0["c0"])
-    need0 = probe.footprint(mid)
+    need0 = probe.footprint(probe.load_model(p0["vol"], GEOM, p0["f0"], p0["mean"], p0["U"], p0["c0"]))
+    need1 = probe.footprint(probe.load_model(p1["vol"], GEOM, p1["f0"], p1["mean"], p1["U"], p1["c0"]))
     probe.close()
-    # a budget that holds patient 0 but not patient 0 and 1 together
-    ctx = Context(0, hbm_budget_bytes=int(need0 * 1.5))
+    # a budget that holds either patient alone but not both together
+    budget = max(need0, need1) + min(need0, need1) // 2
+    ctx = Context(0, hbm_budget_bytes=budget)
     try:
         a = ctx.load_model(p0["vol"], GEOM, p0["f0"], p0["mean"], p0["U"], p0["c0"])
         with pytest.raises(PcaReconError) as e:
@@ -95,13 +96,13 @@ def test_admission_and_release_rules(patients):
         ctx.serve_start(slots=2)
         with pytest.raises(PcaReconError):
             ctx.poll(timeout_ms=0)  # nothing outstanding
-        th, y = p0["frames"][0]
-        ctx.submit(a, y, th, _opts(), tag=7)
+        for j, (th, y) in enumerate(p0["frames"]):  # one patient's frames run in order
+            ctx.submit(a, y, th, _opts(), tag=j)
         with pytest.raises(PcaReconError) as e:
             ctx.release_model(a)  # frames outstanding
         assert e.value.code == -1
-        r = ctx.poll(timeout_ms=60000)
-        assert r["tag"] == 7 and r["status"] == 0
+        tags = sorted(ctx.poll(timeout_ms=60000)["tag"] for _ in p0["frames"])
+        assert tags == list(range(len(p0["frames"])))
         ctx.serve_stop()
         ctx.release_model(a)
         # the freed budget admits the other patient
