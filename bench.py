@@ -43,7 +43,7 @@ if ROOT not in sys.path:
 
 METRIC = "reconstructions/s and p50/p99 ms per projection (256²×120, K=3) vs plain FP32 path"
 UNIT = "reconstructions/s"
-WORKLOAD = "paper-scale plain method, FP32: 256x256x120 @ 2x2x2.5 mm, K=3, 512x384 @ 0.776 mm, 10 iterations"
+WORKLOAD = "paper-scale plain method, FP32: 256x256x120 @ 2x2x2.5 mm, K=3, %s detector, 10 iterations"
 # Line-search trials per accepted step of this library's Armijo rule on this
 # workload (measured on the GPU arm); used only to scale the oracle's per-step
 # sample to a whole reconstruction in the reference arm.
@@ -169,10 +169,10 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 
 
-def build_model_inputs():
+def build_model_inputs(detector: str = "512x384"):
     from phantom import build_pca, phantom_volume, training_dvfs, tumor_centre, workload_paper
 
-    w = workload_paper()
+    w = workload_paper(detector=detector)
     vol = w["vol"]
     f0 = phantom_volume(vol).astype(np.float32)
     pca = build_pca(training_dvfs(vol), w["K"])
@@ -330,7 +330,7 @@ def run_reference(args):
     from oracle import oracle as O
     from phantom import dvf_analytic
 
-    w, f0, mean, U, c0 = build_model_inputs()
+    w, f0, mean, U, c0 = build_model_inputs(args.detector)
     vol, geom = w["vol"], w["geom"]
     O.build_oracle()
     m_f0 = f0.astype(np.float64)
@@ -355,7 +355,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sec,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic phantom (seeded)",
-        "config": {"workload": WORKLOAD, "frames": "j = 0..; angle j deg, t = j/6 s"},
+        "config": {"workload": WORKLOAD % args.detector, "frames": "j = 0..; angle j deg, t = j/6 s"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "per step: one FP64 oracle trial evaluation (warp + projection) of frame j; "
                                    "a reconstruction = (1 + %d x %.1f) evaluations + %d gradients "
@@ -377,7 +377,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dist = dist_init(world)
 
-    w, f0, mean, U, c0 = build_model_inputs()
+    w, f0, mean, U, c0 = build_model_inputs(args.detector)
     vol, geom = w["vol"], w["geom"]
     ctx = Context(local)
     mid = ctx.load_model(vol, geom, f0, mean, U, c0)
@@ -506,7 +506,7 @@ def run_ours(args):
             "ms_per_step": max_ms / K, "p50_ms": float(q[0]), "p99_ms": float(q[1]),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic phantom (seeded), measured projections synthesised on the device",
-            "config": {"workload": WORKLOAD, "volume": [vol.nx, vol.ny, vol.nz],
+            "config": {"workload": WORKLOAD % args.detector, "volume": [vol.nx, vol.ny, vol.nz],
                        "spacing_mm": [vol.dx, vol.dy, vol.dz], "K": Km, "detector": [geom.nu, geom.nv],
                        "pixel_mm": geom.du, "ray_step_mm": geom.ds, "iterations": w["max_iters"],
                        "frames": "j = %d..%d: angle j deg, t = j/6 s, 1%% noise seed j, warm start from j-1"
@@ -550,6 +550,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--adjoint", action="store_true", help="also time the gather-adjoint gradient kernel")
+    ap.add_argument("--detector", default="512x384", choices=["512x384", "200x150", "1000x750"],
+                    help="detector sampling of the 40x30 cm panel")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

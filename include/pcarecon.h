@@ -113,6 +113,9 @@ typedef struct {
                               backtracking; default 1 */
     int warm_step;         /* 1: a warm-started solve also starts from the model's next
                               step (unless the last solve's line search failed); default 1 */
+    int predict;           /* 1: a warm-started solve starts from 2 w(j-1) - w(j-2), the
+                              linear prediction from the last two solves' final w
+                              (Section 5's predicted coefficients); default 0 */
 } pr_solve_opts;
 
 typedef struct {
@@ -233,7 +236,7 @@ int pr_serve_stop(pr_ctx* ctx);
 
 /* Read / overwrite a model's warm-start coefficients (K doubles, host).
  * pr_set_state also forgets the warm-start step (the next solve's first
- * trial moves w by step0_mm). */
+ * trial moves w by step0_mm) and the history used by `predict`. */
 int pr_get_state(pr_ctx* ctx, int model_id, double* w);
 int pr_set_state(pr_ctx* ctx, int model_id, const double* w);
 

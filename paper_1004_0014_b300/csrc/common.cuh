@@ -100,6 +100,7 @@ struct SolveParams {
     int max_iters, max_bt, tumor_max_iter, K;
     int cold_start;  // 1: start from w0; 0: from the state's last accepted w
     int warm_step;   // 1: a warm start also takes the state's next step
+    int predict;     // 1: a warm start extrapolates w linearly from the last two solves
 };
 
 // On-device state of one solve (FP64 scalars; Section 2.2's alternation).
@@ -115,6 +116,8 @@ struct SolveState {
     int tumor_steps, pad_;
     long long cum_solves, cum_trials, cum_iters, cum_lsf;  // since the model was loaded
     double mu_next;  // first trial step of the next iteration or warm-started solve (0 = none)
+    double w_prev[8];  // final w of the solve before the last one (for the predictor)
+    int history;       // warm-started solves in a row with a known final w (0, 1, >= 2)
 };
 
 // ---------------------------------------------------------------------------

@@ -67,12 +67,20 @@ k_begin(const float* __restrict__ y, int R, SolveState* st, double* partials, un
         st->sy = tot[0];
         st->syy = tot[1];
         st->R = (double)R;
+        // Starting point: w0 (cold start), the last solve's w (warm start), or,
+        // with prediction and two earlier solves, the linear extrapolation
+        // 2 w(j-1) - w(j-2) from their final w.
+        const bool cold = st->prm.cold_start != 0;
+        const bool predict = !cold && st->prm.predict && st->history >= 2;
         for (int k = 0; k < kMaxK; ++k) {
-            double w0 = k < K ? (st->prm.cold_start ? st->prm.w0[k] : st->w[k]) : 0.0;
+            double last = st->w[k];
+            double w0 = k < K ? (cold ? st->prm.w0[k] : (predict ? 2.0 * last - st->w_prev[k] : last)) : 0.0;
+            st->w_prev[k] = cold ? 0.0 : last;
             st->w[k] = w0;
             st->wt[k] = w0;
             st->g[k] = 0.0;
         }
+        st->history = cold ? 1 : min(st->history + 1, 2);
         st->a = 1.0;
         st->b = 0.0;
         st->J = st->Jt = 0.0;

@@ -269,6 +269,7 @@ int write_params(pr_ctx* c, Model* m, double angle, const pr_solve_opts* o, cuda
     prm.step_growth = o->step_growth;
     prm.step_growth_bt = o->step_growth_bt;
     prm.warm_step = o->warm_step ? 1 : 0;
+    prm.predict = o->predict ? 1 : 0;
     prm.tumor_tol = o->tumor_tol;
     prm.max_iters = o->max_iters;
     prm.max_bt = o->max_backtracks;
@@ -814,6 +815,7 @@ int pr_set_state(pr_ctx* c, int id, const double* w) {
     }
     CK(cudaMemcpyAsync(m->st->w, buf, sizeof buf, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemsetAsync(&m->st->mu_next, 0, sizeof(double), c->stream));
+    CK(cudaMemsetAsync(&m->st->history, 0, sizeof(int), c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return PR_OK;
 }

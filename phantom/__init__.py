@@ -26,4 +26,5 @@ from .generate import (  # noqa: F401
     workload_paper,
     workload_mixed,
     MIXED_SHAPES,
+    DETECTORS,
 )

@@ -346,14 +346,20 @@ def workload_small(K: int = 3):
                 angle_deg=0.0, t=1.0, scale=1.5, seed=0, max_iters=30)
 
 
-def workload_paper(K: int = 3):
-    """Paper scale (Section 3): 256x256x120 at 2x2x2.5 mm, K modes, 512x384
-    detector at 0.776 mm (the 40x30 cm panel), ray step 1 mm. Projection j is at
-    gantry angle j deg and breathing time j/6 s (one-minute rotation, 360
-    projections, 6 Hz), noise seed j, 10 iterations, warm start from j - 1."""
+# Detector variants of the 40x30 cm panel (Section 3 down-samples to 200x150 at
+# 2 mm; Section 5 compares 1000x750 at 0.4 mm).
+DETECTORS = {"512x384": (512, 384, 0.776), "200x150": (200, 150, 2.0), "1000x750": (1000, 750, 0.4)}
+
+
+def workload_paper(K: int = 3, detector: str = "512x384"):
+    """Paper scale (Section 3): 256x256x120 at 2x2x2.5 mm, K modes, the 40x30 cm
+    panel at 512x384 (0.776 mm; or one of DETECTORS), ray step 1 mm. Projection
+    j is at gantry angle j deg and breathing time j/6 s (one-minute rotation,
+    360 projections, 6 Hz), noise seed j, 10 iterations, warm start from j - 1."""
     vol = Volume(256, 256, 120, 2.0, 2.0, 2.5)
-    geom = Geometry(1000.0, 1500.0, 512, 384, 0.776, 0.776, 1.0)
-    return dict(name="phantom 256x256x120 @ 2x2x2.5 mm, K=%d, 512x384 detector" % K, vol=vol,
+    nu, nv, pitch = DETECTORS[detector]
+    geom = Geometry(1000.0, 1500.0, nu, nv, pitch, pitch, 1.0)
+    return dict(name="phantom 256x256x120 @ 2x2x2.5 mm, K=%d, %s detector" % (K, detector), vol=vol,
                 geom=geom, K=K, scale=1.5, max_iters=10,
                 frame_angle_deg=lambda j: float(j % 360), frame_time=lambda j: j / 6.0,
                 frame_seed=lambda j: int(j))

@@ -68,3 +68,32 @@ def test_paper_scale_solve(paper):
     assert abs(res["J"] - ores.J) / ores.J < TOL_PROJ
     assert rel(res["w"], ores.w) < TOL_W
     assert et < TOL_TUMOR_MM
+
+
+@pytest.mark.parametrize("detector", ["200x150", "1000x750"])
+def test_detector_resolution_variants(paper, detector):
+    """The paper's down-sampled 200x150 panel at 2 mm and the 1000x750 panel at
+    0.4 mm (Sections 3 and 5): projection, cost and gradient against the oracle."""
+    from phantom import DETECTORS, Geometry, standard_normal
+
+    p = paper
+    nu, nv, pitch = DETECTORS[detector]
+    geom = Geometry(1000.0, 1500.0, nu, nv, pitch, pitch, 1.0)
+    om = p["om"]
+    w = np.array([0.8, -0.1, 0.03])
+    po = O.evaluate(om, geom, p["th"], w).p
+    y = (po * (1.0 + 0.01 * standard_normal(5, po.shape))).astype(np.float32)
+    ctx = p["ctx"]
+    vol = p["vol"]
+    mid = ctx.load_model(vol, geom, om.f0.astype(np.float32), om.mean.astype(np.float32),
+                         om.U.astype(np.float32), om.c0)
+    import torch
+
+    J, g, pd = ctx.cost_grad(mid, torch.from_numpy(y).cuda(), p["th"], w, 1.0, 0.0, 0, return_p=True)
+    go, Jo, _ = O.gradient(om, geom, p["th"], w, 1.0, 0.0, y.astype(np.float64))
+    ep = rel(pd.cpu().numpy(), po)
+    report("detector_" + detector, p_rel=ep, J_rel=abs(J - Jo) / Jo, g_rel=rel(g, go))
+    ctx.release_model(mid)
+    assert ep < TOL_PROJ
+    assert abs(J - Jo) / Jo < TOL_PROJ
+    assert rel(g, go) < TOL_GRAD

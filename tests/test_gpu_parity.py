@@ -335,3 +335,32 @@ def test_warm_started_frames_match_oracle(ctx, small):
     assert b["backtracks"] == ob.backtracks
     assert rel(b["w"], ob.w) < TOL_W
     assert abs(b["J"] - ob.J) / ob.J < TOL_PROJ
+
+
+def test_predicted_start_matches_oracle_chain(ctx, small):
+    # Four frames with the linear predictor: the oracle chain starts frame j
+    # from 2 w(j-1) - w(j-2) of its own earlier solves (and the warm step).
+    from phantom import dvf_analytic
+
+    om, geom, vol = small["om"], small["geom"], small["vol"]
+    frames = []
+    for j in range(4):
+        th = 0.2 + 0.02 * j
+        ft = O.warp(vol, om.f0, dvf_analytic(vol, 0.6 + j / 6.0, 1.5))
+        frames.append((th, _f32(noisy(O.project(vol, geom, th, ft), 40 + j))))
+    gpu = []
+    for j, (th, y) in enumerate(frames):
+        kw = dict(max_iters=5, predict=1)
+        if j == 0:
+            kw.update(cold_start=1, w0=[0, 0, 0])
+        gpu.append(ctx.reconstruct(small["mid"], y, th, _opts(**kw)))
+    ws, mu = [], None
+    for j, (th, y) in enumerate(frames):
+        w0 = np.zeros(3) if j == 0 else (ws[-1] if j == 1 else 2 * ws[-1] - ws[-2])
+        r = O.reconstruct(om, geom, th, _up(y), w0, O.SolveOptions(max_iters=5), mu_next=mu)
+        ws.append(r.w)
+        mu = r.mu
+        report("predict_chain64", frame=j, w_rel=rel(gpu[j]["w"], r.w), backtracks=gpu[j]["backtracks"],
+               oracle_backtracks=r.backtracks)
+        assert gpu[j]["backtracks"] == r.backtracks
+        assert rel(gpu[j]["w"], r.w) < TOL_W
