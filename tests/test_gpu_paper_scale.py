@@ -80,9 +80,12 @@ def test_detector_resolution_variants(paper, detector):
     nu, nv, pitch = DETECTORS[detector]
     geom = Geometry(1000.0, 1500.0, nu, nv, pitch, pitch, 1.0)
     om = p["om"]
-    w = np.array([0.8, -0.1, 0.03])
+    # measured frame at w_true; cost and gradient away from it, where the
+    # gradient is signal rather than the cancellation of pure noise
+    w_true, w = np.array([0.8, -0.1, 0.03]), np.array([0.3, 0.15, -0.02])
+    pt = O.evaluate(om, geom, p["th"], w_true).p
+    y = (pt * (1.0 + 0.01 * standard_normal(5, pt.shape))).astype(np.float32)
     po = O.evaluate(om, geom, p["th"], w).p
-    y = (po * (1.0 + 0.01 * standard_normal(5, po.shape))).astype(np.float32)
     ctx = p["ctx"]
     vol = p["vol"]
     mid = ctx.load_model(vol, geom, om.f0.astype(np.float32), om.mean.astype(np.float32),
