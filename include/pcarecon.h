@@ -317,7 +317,7 @@ int pr_cost_grad_static(int device, void* stream, const float* p_dev, const floa
 enum {
     PR_KERNEL_WARP_FH = 0,      /* fused DVF synthesis + warp writing f and h (solver pass) */
     PR_KERNEL_PROJECT_FH = 1,   /* ray-march projection of (f, h_1..h_K) (solver pass) */
-    PR_KERNEL_REGRAD = 2,       /* residual, cost and gradient over the detector */
+    PR_KERNEL_REGRAD = 2,       /* residual, cost and gradient over the detector (pr_cost_grad) */
     PR_KERNEL_BACKPROJECT = 3,  /* gather transpose contracted with h (adjoint gradient) */
     PR_KERNEL_WARP_F = 4,       /* warp writing f only */
     PR_KERNEL_PROJECT_F = 5     /* ray-march projection of f only */

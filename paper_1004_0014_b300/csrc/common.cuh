@@ -13,7 +13,8 @@
 namespace pr {
 
 constexpr int kMaxK = 7;
-constexpr int kMaxMom = 12;  // doubles per block partial row
+constexpr int kMaxMom = 12;  // doubles per block partial row of the reductions
+constexpr int kProjMom = 24; // doubles per block partial row of the projector's moments (3 + 3 x 7)
 
 // Voxel grid of a model. Device volumes are stored with a one-voxel zero border
 // ("padded"): element (i, j, k), -1 <= i <= nx, sits at
@@ -111,7 +112,7 @@ struct SolveState {
     double g[8];   // dJ/dw at (w, a, b)
     double a, b, J, Jt, mu, mu_prev, gnorm, gnorm0;
     double sy, syy, R;
-    int iter, bt, trials, total_bt, stop, accepted, need_grad, running;
+    int iter, bt, trials, total_bt, stop, accepted, pad1_, running;
     double tumor[3];
     int tumor_steps, pad_;
     long long cum_solves, cum_trials, cum_iters, cum_lsf;  // since the model was loaded
@@ -200,13 +201,13 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
 // Write this block's NV partial sums (thread 0 holds them), then report whether
 // this block is the last of `nblocks` to finish. The last block may then read
 // every row with ldcg and must reset *counter to 0.
-template <int NV>
+template <int NV, int STRIDE = kMaxMom>
 __device__ __forceinline__ bool publish_partials(const double (&v)[NV], double* partials, int block,
                                                  int nblocks, unsigned int* counter) {
     __shared__ int s_last;
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int m = 0; m < NV; ++m) partials[(size_t)block * kMaxMom + m] = v[m];
+        for (int m = 0; m < NV; ++m) partials[(size_t)block * STRIDE + m] = v[m];
         __threadfence();
         unsigned int prev = atomicAdd(counter, 1u);
         s_last = (prev == (unsigned int)(nblocks - 1));
@@ -218,13 +219,13 @@ __device__ __forceinline__ bool publish_partials(const double (&v)[NV], double* 
 }
 
 // In the last block: total of NV partial rows over nblocks, fixed order.
-template <int NV>
+template <int NV, int STRIDE = kMaxMom>
 __device__ __forceinline__ void total_partials(const double* partials, int nblocks, double (&tot)[NV]) {
 #pragma unroll
     for (int m = 0; m < NV; ++m) tot[m] = 0.0;
     for (int r = threadIdx.x; r < nblocks; r += blockDim.x)
 #pragma unroll
-        for (int m = 0; m < NV; ++m) tot[m] += __ldcg(partials + (size_t)r * kMaxMom + m);
+        for (int m = 0; m < NV; ++m) tot[m] += __ldcg(partials + (size_t)r * STRIDE + m);
     block_sum<NV>(tot);
 }
 

@@ -70,12 +70,6 @@ cudaError_t launch_maxabs(Launcher& L, const float* x, long long n, unsigned int
 // Host: the projector's tile launch order for an nu x nv detector (project_blocks ints).
 void project_tile_order(int nu, int nv, int* order);
 
-// Residual, cost and gradient from stored p and q at the state's (a, b); then
-// the stop test and the next trial step (runs only when the state asks).
-cudaError_t launch_regrad(Launcher& L, const float* p, const float* q, const float* y, int R, int K,
-                          SolveState* st, double* partials, unsigned int* counter,
-                          cudaGraphConditionalHandle h, int use_graph);
-
 // Generic cost / gradient for explicit (w, a, b) from stored p, q: out[0] = J,
 // out[1 + k] = 2 sum r q_k.
 cudaError_t launch_cost_grad(Launcher& L, const float* p, const float* q, const float* y, int R, int K,

@@ -89,7 +89,6 @@ k_begin(const float* __restrict__ y, int R, SolveState* st, double* partials, un
         st->iter = st->bt = st->trials = st->total_bt = 0;
         st->stop = tot[2] > 0.0 ? 4 : 0;  // PR_STOP_NONFINITE
         st->accepted = 0;
-        st->need_grad = 0;
         st->running = 1;
         st->cum_solves += 1;
         if (st->prm.cold_start || !st->prm.warm_step) st->mu_next = 0.0;
@@ -227,22 +226,80 @@ struct ProjArgs {
     SupportRef sup;
 };
 
-__device__ void controller_project(SolveState* st, const double (&tot)[3], int phase,
-                                   cudaGraphConditionalHandle h, int use_graph) {
+// Moments of one projection pass, summed in FP64 over rays (products of two
+// floats are exact in FP64): [0] sum p^2, [1] sum p y, [2] sum p,
+// [3 + k] sum p q_k, [3 + KM + k] sum y q_k, [3 + 2 KM + k] sum q_k, with
+// KM = 3 or 7 the channel capacity. From them J and dJ/dw follow for any
+// (a, b) without another pass over the detector:
+//   J(a, b)   = Spp - 2a Spy - 2b Sp + a^2 Syy + 2ab Sy + b^2 R        (Eq. 2)
+//   g_k(a, b) = 2 (Spq_k - a Syq_k - b Sq_k)      (gradient after Eq. 4,
+//               forward form: 2 sum_rays r (P h_k), r = p - a y - b)
+template <int KM>
+__device__ double cost_at(const SolveState* st, const double* m, double a, double b) {
+    return m[0] - 2.0 * a * m[1] - 2.0 * b * m[2] + a * a * st->syy + 2.0 * a * b * st->sy + b * b * st->R;
+}
+
+// Cost and gradient at the state's (a, b) from the moments, then the stopping
+// rule (Section 2.2) and, if the solve goes on, the first trial of the next
+// step. Thread 0 of the last block.
+template <int KM>
+__device__ void finish_point(SolveState* st, const double* m, int K, cudaGraphConditionalHandle h,
+                             int use_graph) {
+    const double a = st->a, b = st->b;
+    st->J = cost_at<KM>(st, m, a, b);
+    double gn2 = 0.0;
+    for (int k = 0; k < kMaxK; ++k) {
+        double gk = k < K ? 2.0 * (m[3 + k] - a * m[3 + KM + k] - b * m[3 + 2 * KM + k]) : 0.0;
+        st->g[k] = gk;
+        gn2 += gk * gk;
+    }
+    double gn = sqrt(gn2);
+    st->gnorm = gn;
+    if (st->iter == 0) st->gnorm0 = gn;
+    if (st->stop != 0) {
+        set_loop(st, 0, h, use_graph);
+        return;
+    }
+    if (!isfinite(st->J) || !isfinite(gn)) {
+        st->stop = 4;
+        set_loop(st, 0, h, use_graph);
+        return;
+    }
+    if (gn <= st->prm.grad_tol * st->gnorm0 || gn == 0.0) {
+        st->stop = 1;  // PR_STOP_GRAD_TOL
+        set_loop(st, 0, h, use_graph);
+        return;
+    }
+    if (st->iter >= st->prm.max_iters) {
+        st->stop = 2;  // PR_STOP_MAX_ITERS
+        set_loop(st, 0, h, use_graph);
+        return;
+    }
+    // after an accepted step (this solve or, warm-started, the previous frame's
+    // last) the next step; otherwise a first trial that moves w by step0 mm
+    st->mu = st->mu_next > 0.0 ? st->mu_next : st->prm.step0 / gn;
+    st->bt = 0;
+    next_trial(st, K);
+    set_loop(st, 1, h, use_graph);
+}
+
+template <int KM>
+__device__ void controller_project(SolveState* st, const double* m, int phase, cudaGraphConditionalHandle h,
+                                   int use_graph) {
     const int K = st->prm.K;
     double a, b;
     if (phase == kPhaseInit) {
-        if (st->stop == 0 && !fit_ab(st, tot[1], tot[2], &a, &b)) st->stop = 5;  // singular fit
+        // Eq. 4 at the starting w, then the cost and gradient there
+        if (st->stop == 0 && !fit_ab(st, m[2], m[1], &a, &b)) st->stop = 5;  // singular fit
         if (st->stop == 0) {
             st->a = a;
             st->b = b;
         }
-        st->need_grad = 1;  // the residual kernel computes J, g and decides whether to run
+        finish_point<KM>(st, m, K, h, use_graph);
         return;
     }
     // kPhaseTrial: Armijo's sufficient-decrease test at fixed (a, b) (Section 2.2).
     if (st->stop != 0) {
-        st->need_grad = 0;
         set_loop(st, 0, h, use_graph);
         return;
     }
@@ -250,11 +307,10 @@ __device__ void controller_project(SolveState* st, const double (&tot)[3], int p
     st->cum_trials += 1;
     if (st->trials > (st->prm.max_iters + 1) * (st->prm.max_bt + 1) + 1) {
         st->stop = 6;  // internal guard: more trials than the options allow
-        st->need_grad = 0;
         set_loop(st, 0, h, use_graph);
         return;
     }
-    double Jt = tot[0];
+    double Jt = cost_at<KM>(st, m, st->a, st->b);
     st->Jt = Jt;
     bool ok = isfinite(Jt) && Jt <= st->J - st->prm.c1 * st->mu * st->gnorm * st->gnorm;
     if (ok) {
@@ -266,17 +322,16 @@ __device__ void controller_project(SolveState* st, const double (&tot)[3], int p
         st->iter += 1;
         st->cum_iters += 1;
         st->accepted = 1;
-        if (fit_ab(st, tot[1], tot[2], &a, &b)) {  // step 2, Eq. 4
+        if (fit_ab(st, m[2], m[1], &a, &b)) {  // step 2, Eq. 4
             st->a = a;
             st->b = b;
         } else {
             st->stop = 5;
         }
-        st->need_grad = 1;
+        finish_point<KM>(st, m, K, h, use_graph);
         return;
     }
     st->accepted = 0;
-    st->need_grad = 0;
     st->bt += 1;
     st->total_bt += 1;
     if (st->bt > st->prm.max_bt) {
@@ -350,95 +405,39 @@ __global__ void __launch_bounds__(kProjThreads, NCH == 4 ? 4 : 1) k_project(Proj
     }
     if (A.phase == kPhaseNone) return;
 
-    // Epilogue: J_trial = sum (p - a y - b)^2, sum p, sum p y (FP64 from here on).
-    double v[3] = {0.0, 0.0, 0.0};
+    // Epilogue: this pass's moments (FP64; see cost_at), block sums, and the
+    // controller in the last block to finish.
+    constexpr int KM = NCH == 8 ? 7 : 3;
+    constexpr int NV = 3 + 3 * KM;
+    double m[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) m[i] = 0.0;
     if (valid) {
-        double yv = A.y[r];
-        double res = (double)pv - A.st->a * yv - A.st->b;
-        v[0] = res * res;
-        v[1] = pv;
-        v[2] = (double)pv * yv;
+        const double pd = (double)pv, yd = (double)A.y[r];
+        m[0] = pd * pd;
+        m[1] = pd * yd;
+        m[2] = pd;
+        if constexpr (NCH > 1) {
+#pragma unroll
+            for (int k = 0; k < KM; ++k) {
+                if (k < A.K) {
+                    const double qd = (double)(acc[1 + k] * g.ds);
+                    m[3 + k] = pd * qd;
+                    m[3 + KM + k] = yd * qd;
+                    m[3 + 2 * KM + k] = qd;
+                }
+            }
+        }
     }
-    block_sum<3>(v);
+    block_sum<NV>(m);
     const int nblocks = gridDim.x;
-    if (!publish_partials<3>(v, A.partials, tile, nblocks, A.counter)) return;
-    double tot[3];
-    total_partials<3>(A.partials, nblocks, tot);
+    if (!publish_partials<NV, kProjMom>(m, A.partials, tile, nblocks, A.counter)) return;
+    double tot[NV];
+    total_partials<NV, kProjMom>(A.partials, nblocks, tot);
     if (threadIdx.x == 0) {
         *A.counter = 0;
-        controller_project(A.st, tot, A.phase, A.h, A.use_graph);
+        controller_project<KM>(A.st, tot, A.phase, A.h, A.use_graph);
     }
-}
-
-// ---------------------------------------------------------------------------
-// Residual, cost and gradient from stored p, q (forward-mode form of the
-// gradient formula after Eq. 4: dJ/dw_k = 2 sum_rays r (P h_k)), then the stop
-// test and the next trial step.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kReduceThreads)
-k_regrad(const float* __restrict__ p, const float* __restrict__ q, const float* __restrict__ y, int R, int K,
-         SolveState* st, double* partials, unsigned int* counter, cudaGraphConditionalHandle h,
-         int use_graph) {
-    if (!st->need_grad) return;
-    const double a = st->a, b = st->b;
-    // The residual p - a y - b cancels, so it is formed in FP64; its square and
-    // its products with q_k are FP32 (each thread sums a few rays), and the
-    // sums over threads and blocks are FP64 (B300's FP64 rate is low).
-    float vf[8];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) vf[m] = 0.0f;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
-        float res = (float)((double)p[r] - fma(a, (double)y[r], b));
-        vf[0] = __fmaf_rn(res, res, vf[0]);
-#pragma unroll
-        for (int k = 0; k < kMaxK; ++k)
-            if (k < K) vf[1 + k] = __fmaf_rn(res, q[(long long)k * R + r], vf[1 + k]);
-    }
-    double v[8];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = vf[m];
-    block_sum<8>(v);
-    if (!publish_partials<8>(v, partials, blockIdx.x, gridDim.x, counter)) return;
-    double tot[8];
-    total_partials<8>(partials, gridDim.x, tot);
-    if (threadIdx.x != 0) return;
-    *counter = 0;
-    st->need_grad = 0;
-    st->J = tot[0];
-    double gn2 = 0.0;
-    for (int k = 0; k < kMaxK; ++k) {
-        double gk = k < K ? 2.0 * tot[1 + k] : 0.0;
-        st->g[k] = gk;
-        gn2 += gk * gk;
-    }
-    double gn = sqrt(gn2);
-    st->gnorm = gn;
-    if (st->iter == 0) st->gnorm0 = gn;
-    if (st->stop != 0) {
-        set_loop(st, 0, h, use_graph);
-        return;
-    }
-    if (!isfinite(st->J) || !isfinite(gn)) {
-        st->stop = 4;
-        set_loop(st, 0, h, use_graph);
-        return;
-    }
-    if (gn <= st->prm.grad_tol * st->gnorm0 || gn == 0.0) {
-        st->stop = 1;  // PR_STOP_GRAD_TOL
-        set_loop(st, 0, h, use_graph);
-        return;
-    }
-    if (st->iter >= st->prm.max_iters) {
-        st->stop = 2;  // PR_STOP_MAX_ITERS
-        set_loop(st, 0, h, use_graph);
-        return;
-    }
-    // after an accepted step (this solve or, warm-started, the previous frame's
-    // last) the next step; otherwise a first trial that moves w by step0 mm
-    st->mu = st->mu_next > 0.0 ? st->mu_next : st->prm.step0 / gn;
-    st->bt = 0;
-    next_trial(st, K);
-    set_loop(st, 1, h, use_graph);
 }
 
 // Cost and gradient at explicit (a, b) (ab_dev[0..1]) for the step-level entry.
@@ -446,7 +445,7 @@ __global__ void __launch_bounds__(kReduceThreads)
 k_cost_grad(const float* __restrict__ p, const float* __restrict__ q, const float* __restrict__ y, int R, int K,
             const double* ab, double* partials, unsigned int* counter, double* out) {
     const double a = ab[0], b = ab[1];
-    // same arithmetic as k_regrad: FP64 residual, FP32 products, FP64 sums
+    // FP64 residual (it cancels), FP32 products per thread, FP64 sums
     float vf[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) vf[m] = 0.0f;
@@ -605,13 +604,6 @@ cudaError_t launch_project(Launcher& L, const VolDev& vd, const float* vol_pad, 
         case 8: return L(k_project<8>, grid, dim3(kProjThreads), 0, A);
     }
     return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_regrad(Launcher& L, const float* p, const float* q, const float* y, int R, int K,
-                          SolveState* st, double* partials, unsigned int* counter,
-                          cudaGraphConditionalHandle h, int use_graph) {
-    return L(k_regrad, dim3(kReduceBlocks), dim3(kReduceThreads), 0, p, q, y, R, K, st, partials, counter,
-             h, use_graph);
 }
 
 cudaError_t launch_cost_grad(Launcher& L, const float* p, const float* q, const float* y, int R, int K,

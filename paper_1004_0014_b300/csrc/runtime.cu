@@ -242,7 +242,13 @@ size_t partial_rows(const pr_geometry& g, const VolDev& vd) {
     size_t r = a > b ? a : b;
     return r > c ? r : c;
 }
-size_t partial_rows(const Model& m) { return partial_rows(m.geom, m.md.vd); }
+
+// Doubles of the block-partial buffer: the reductions' rows and the
+// projector's wider moment rows.
+size_t partial_doubles(const pr_geometry& g, const VolDev& vd) {
+    size_t a = partial_rows(g, vd) * kMaxMom, b = (size_t)project_blocks(g.nu, g.nv) * kProjMom;
+    return a > b ? a : b;
+}
 
 // Device bytes pr_load_model allocates for a model (the admission check uses
 // this before allocating; the gradient-adjoint scratch of K x N floats is
@@ -253,7 +259,7 @@ size_t model_bytes(const pr_volume_desc& v, const pr_geometry& g, int K, int sto
     size_t ts = storage == PR_BF16 ? 2 : 4;
     size_t nch = (size_t)fh_channels(K);
     return np * ts + 3 * n * 4 + 3 * (size_t)K * n * ts + np * nch * 4 + np * 4 + R * 4 + R * K * 4 + R * 4 +
-           R * 4 + n * 4 + partial_rows(g, vd) * kMaxMom * 8 + 64 + sizeof(SolveState) + 64 + 128 +
+           R * 4 + n * 4 + partial_doubles(g, vd) * 8 + 64 + sizeof(SolveState) + 64 + 128 +
            sizeof(RayGeom) + 16 + (size_t)project_blocks(g.nu, g.nv) * sizeof(int) + sizeof(Support);
 }
 
@@ -290,9 +296,11 @@ bool opts_ok(const pr_solve_opts* o) {
            (o->loop_mode == PR_LOOP_GRAPH || o->loop_mode == PR_LOOP_HOST);
 }
 
-// Section 2.2's loop as a CUDA graph: prologue (y moments, f and h at w0,
-// projection and Eq. 4, gradient), a WHILE node over line-search trials, and
-// the Section 2.3 tumor kernel.
+// Section 2.2's loop as a CUDA graph: prologue (y moments; f and h at w0;
+// projection, whose last block fits Eq. 4 and forms the cost and gradient), a
+// WHILE node whose body is one line-search trial (warp, then projection with
+// the Armijo test, Eq. 4, cost, gradient and stopping rule in its last
+// block), and the Section 2.3 tumor kernel.
 int build_graph(pr_ctx* c, Model* m) {
     CK(cudaGraphCreate(&m->graph, 0));
     CK(cudaGraphConditionalHandleCreate(&m->hloop, m->graph, 1, cudaGraphCondAssignDefault));
@@ -303,7 +311,6 @@ int build_graph(pr_ctx* c, Model* m) {
     CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseInit, m->hloop, 1, SupportRef{m->sup, st->wt, m->K}));
-    CK(launch_regrad(L, m->p, m->q, m->y, m->R, m->K, st, m->partials, m->counter, m->hloop, 1));
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = m->hloop;
@@ -316,7 +323,6 @@ int build_graph(pr_ctx* c, Model* m) {
     CK(launch_warp(B, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
     CK(launch_project(B, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseTrial, m->hloop, 1, SupportRef{m->sup, st->wt, m->K}));
-    CK(launch_regrad(B, m->p, m->q, m->y, m->R, m->K, st, m->partials, m->counter, m->hloop, 1));
     L.last = cond;
     CK(launch_tumor(L, m->md, st->w, 0.0, 0, &st->prm, st->tumor, &st->tumor_steps));
     CK(cudaGraphInstantiate(&m->exec, m->graph, 0));
@@ -333,7 +339,6 @@ int host_loop(pr_ctx* c, Model* m, int opt_max_iters, int opt_max_bt) {
     CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseInit, 0, 0, SupportRef{m->sup, st->wt, m->K}));
-    CK(launch_regrad(L, m->p, m->q, m->y, m->R, m->K, st, m->partials, m->counter, 0, 0));
     long long guard = 0, bound = (long long)(opt_max_iters + 1) * (opt_max_bt + 1) + 2;
     for (;;) {
         CK(cudaMemcpyAsync(&m->st_host->running, &st->running, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -343,8 +348,7 @@ int host_loop(pr_ctx* c, Model* m, int opt_max_iters, int opt_max_bt) {
         CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
         CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y,
                           st, m->partials, m->counter, kPhaseTrial, 0, 0, SupportRef{m->sup, st->wt, m->K}));
-        CK(launch_regrad(L, m->p, m->q, m->y, m->R, m->K, st, m->partials, m->counter, 0, 0));
-    }
+        }
     CK(launch_tumor(L, m->md, st->w, 0.0, 0, &st->prm, st->tumor, &st->tumor_steps));
     return PR_OK;
 }
@@ -657,7 +661,7 @@ int pr_load_model(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
     A(&m->r, R * 4);
     A(&m->flat, n * 4);
     m->md.vd = vd;
-    A(&m->partials, partial_rows(*m) * kMaxMom * 8);
+    A(&m->partials, partial_doubles(m->geom, m->md.vd) * 8);
     A(&m->counter, 64);
     A(&m->st, sizeof(SolveState));
     A(&m->wdev, 8 * 8);
@@ -688,7 +692,7 @@ int pr_load_model(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
         if ((e = cudaMemsetAsync(m->f0p, 0, np * ts, s))) break;
         if ((e = cudaMemsetAsync(m->fh, 0, np * m->nch * 4, s))) break;
         if ((e = cudaMemsetAsync(m->fpad, 0, np * 4, s))) break;
-        if ((e = cudaMemsetAsync(m->partials, 0, partial_rows(*m) * kMaxMom * 8, s))) break;
+        if ((e = cudaMemsetAsync(m->partials, 0, partial_doubles(m->geom, m->md.vd) * 8, s))) break;
         if ((e = cudaMemsetAsync(m->counter, 0, 64, s))) break;
         if ((e = cudaMemsetAsync(m->st, 0, sizeof(SolveState), s))) break;
         if ((e = cudaMemcpyAsync(m->mean, mean_dvf, 3 * n * 4, kind, s))) break;
@@ -1021,9 +1025,9 @@ int pr_model_stats(pr_ctx* c, int id, pr_stats* out) {
     CK(cudaStreamSynchronize(c->stream));
     out->solves = m->st_host->cum_solves;
     out->trials = m->st_host->cum_trials;
-    // per solve: begin, warp, project, residual-gradient, tumor; per trial:
-    // warp, project, residual-gradient (the body of the loop)
-    out->kernels = 5 * out->solves + 3 * out->trials;
+    // per solve: begin, warp, project, tumor; per trial: warp, project (the
+    // body of the loop)
+    out->kernels = 4 * out->solves + 2 * out->trials;
     out->iters = m->st_host->cum_iters;
     out->line_search_failures = m->st_host->cum_lsf;
     return PR_OK;
