@@ -198,6 +198,52 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
     __syncthreads();
 }
 
+// Float-float (unevaluated hi + lo) arithmetic for exact-enough sums without
+// the FP64 pipe, which is narrow on B300: a product of two floats is exactly
+// hi + lo (TwoProduct with an FMA), and TwoSum keeps the rounding error of
+// each addition, so a warp's sum of 32 such terms keeps ~48 bits.
+__device__ __forceinline__ void ff_prod(float a, float b, float& hi, float& lo) {
+    hi = __fmul_rn(a, b);
+    lo = __fmaf_rn(a, b, -hi);
+}
+
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float bhi, float blo) {
+    float s = __fadd_rn(hi, bhi);
+    float bb = __fsub_rn(s, hi);
+    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(bhi, bb));
+    e = __fadd_rn(e, __fadd_rn(lo, blo));
+    float t = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(t, s));
+    hi = t;
+}
+
+// Block sum of NV float-float values in a fixed order: float-float within
+// each warp, FP64 across the warps; thread 0 gets the totals in out.
+template <int NV>
+__device__ __forceinline__ void block_sum_ff(float (&hi)[NV], float (&lo)[NV], double (&out)[NV]) {
+    __shared__ double sh[32][NV];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int m = 0; m < NV; ++m) {
+            float bh = __shfl_down_sync(0xffffffffu, hi[m], o), bl = __shfl_down_sync(0xffffffffu, lo[m], o);
+            ff_add(hi[m], lo[m], bh, bl);
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int m = 0; m < NV; ++m) sh[wid][m] = (double)hi[m] + (double)lo[m];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int m = 0; m < NV; ++m) {
+            double x = lane < nw ? sh[lane][m] : 0.0;
+            out[m] = warp_sum(x);
+        }
+    }
+    __syncthreads();
+}
+
 // Write this block's NV partial sums (thread 0 holds them), then report whether
 // this block is the last of `nblocks` to finish. The last block may then read
 // every row with ldcg and must reset *counter to 0.

@@ -407,29 +407,32 @@ __global__ void __launch_bounds__(kProjThreads, NCH == 4 ? 4 : 1) k_project(Proj
 
     // Epilogue: this pass's moments (FP64; see cost_at), block sums, and the
     // controller in the last block to finish.
+    // Products of two floats are exact as float-float pairs, and the sums run
+    // in float-float within a warp and in FP64 across warps and blocks.
     constexpr int KM = NCH == 8 ? 7 : 3;
     constexpr int NV = 3 + 3 * KM;
-    double m[NV];
+    float mh[NV], ml[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) m[i] = 0.0;
+    for (int i = 0; i < NV; ++i) mh[i] = ml[i] = 0.0f;
     if (valid) {
-        const double pd = (double)pv, yd = (double)A.y[r];
-        m[0] = pd * pd;
-        m[1] = pd * yd;
-        m[2] = pd;
+        const float yv = A.y[r];
+        ff_prod(pv, pv, mh[0], ml[0]);
+        ff_prod(pv, yv, mh[1], ml[1]);
+        mh[2] = pv;
         if constexpr (NCH > 1) {
 #pragma unroll
             for (int k = 0; k < KM; ++k) {
                 if (k < A.K) {
-                    const double qd = (double)(acc[1 + k] * g.ds);
-                    m[3 + k] = pd * qd;
-                    m[3 + KM + k] = yd * qd;
-                    m[3 + 2 * KM + k] = qd;
+                    const float qv = acc[1 + k] * g.ds;
+                    ff_prod(pv, qv, mh[3 + k], ml[3 + k]);
+                    ff_prod(yv, qv, mh[3 + KM + k], ml[3 + KM + k]);
+                    mh[3 + 2 * KM + k] = qv;
                 }
             }
         }
     }
-    block_sum<NV>(m);
+    double m[NV];
+    block_sum_ff<NV>(mh, ml, m);
     const int nblocks = gridDim.x;
     if (!publish_partials<NV, kProjMom>(m, A.partials, tile, nblocks, A.counter)) return;
     double tot[NV];
