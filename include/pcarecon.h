@@ -107,15 +107,20 @@ typedef struct {
     int loop_mode;       /* PR_LOOP_GRAPH (on-device loop in a CUDA graph) or PR_LOOP_HOST */
     double tumor_tol;    /* fixed-point stop, mm; default 1e-6 */
     int tumor_max_iter;  /* default 100 */
-    double step_growth;    /* next first trial = step_growth x an accepted step that was
-                              accepted at its first trial; default 2 */
-    double step_growth_bt; /* ... = step_growth_bt x an accepted step that needed
-                              backtracking; default 1 */
+    double step_growth;    /* cap of the next first trial: step_growth x the accepted step
+                              (step_model 0: used after a first-try acceptance); default 2 */
+    double step_growth_bt; /* step_model 0: next first trial = step_growth_bt x an accepted
+                              step that needed backtracking; default 1 */
     int warm_step;         /* 1: a warm-started solve also starts from the model's next
                               step (unless the last solve's line search failed); default 1 */
     int predict;           /* 1: a warm-started solve starts from 2 w(j-1) - w(j-2), the
                               linear prediction from the last two solves' final w
                               (Section 5's predicted coefficients); default 0 */
+    int step_model;        /* 1: each trial measures the curvature of J along -g; a rejected
+                              trial backtracks to the quadratic model's minimiser (within
+                              [0.1, beta] x mu) and the next first trial is that minimiser
+                              (at most step_growth x mu); 0: backtrack by beta, growth
+                              factors only; default 1 */
 } pr_solve_opts;
 
 typedef struct {

@@ -22,9 +22,14 @@ Readings of the paper where it is silent (the CUDA path uses the same):
   * Armijo rule (Section 2.2 names it, gives no constants): sufficient
     decrease J(w - mu g; a, b) <= J(w; a, b) - c1 mu |g|^2 with c1 = 1e-4,
     backtracking mu <- beta mu with beta = 0.5, at most 8 backtracks. The
-    first trial step is mu = step0_mm / |g| (moves w by step0_mm); after an
-    accepted step mu the next first trial is step_growth x mu (2) if mu was
-    accepted at its first trial, else step_growth_bt x mu (1). A solve
+    first trial step is mu = step0_mm / |g| (moves w by step0_mm). Each trial
+    at mu measures the curvature of J along -g, curv = 2 (J(mu) - J + mu |g|^2)
+    / mu^2. With step_model 1 (default) a rejected trial backtracks to the
+    minimiser |g|^2 / curv of that quadratic model, kept within [0.1 mu,
+    beta mu], and after an accepted step the next first trial is
+    min(step_growth x mu, |g|^2 / curv) (step_growth = 2); with step_model 0
+    backtracking is mu <- beta mu and the next first trial is step_growth x mu
+    if mu was accepted at its first trial, else step_growth_bt x mu. A solve
     warm-started from the previous frame starts with that frame's next trial
     step, as its w starts from that frame's w (Section 4 initialises each
     frame from the previous one). No accepted step: w is kept, the solve
@@ -259,6 +264,7 @@ class SolveOptions:
     step0_mm: float = 1.0
     step_growth: float = 2.0
     step_growth_bt: float = 1.0
+    step_model: int = 1
     tumor_tol: float = 1e-6
     tumor_max_iter: int = 100
 
@@ -309,16 +315,24 @@ def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None,
         for bt in range(o.max_backtracks + 1):
             trial = evaluate(model, geom, angle, w - mu * g)
             J_t = cost(trial.p, y, a, b)
+            # curvature of J along -g from this trial: J(mu) ~ J - mu |g|^2 + (curv/2) mu^2
+            curv = 2.0 * (J_t - J + mu * gn * gn) / (mu * mu)
             if J_t <= J - o.c1 * mu * gn * gn:
                 accepted = trial
                 break
             backtracks += 1
-            mu *= o.beta
+            if o.step_model == 1 and curv > 0:  # minimiser of the quadratic model, safeguarded
+                mu = min(o.beta * mu, max(0.1 * mu, gn * gn / curv))
+            else:
+                mu *= o.beta
         if accepted is None:
             stop = STOP_LINESEARCH_FAILED
             mu_next = 0.0
             break
-        mu_next = (o.step_growth if bt == 0 else o.step_growth_bt) * mu
+        if o.step_model == 1:
+            mu_next = o.step_growth * mu if curv <= 0 else min(o.step_growth * mu, gn * gn / curv)
+        else:
+            mu_next = (o.step_growth if bt == 0 else o.step_growth_bt) * mu
         w = accepted.w
         # Step 2: (a, b) by Eq. 4 at the new w.
         a, b = fit_ab(accepted.p, y)

@@ -77,7 +77,7 @@ class SolveOpts(ctypes.Structure):
                 ("w0", ctypes.c_double * PR_MAX_K), ("loop_mode", ctypes.c_int),
                 ("tumor_tol", ctypes.c_double), ("tumor_max_iter", ctypes.c_int),
                 ("step_growth", ctypes.c_double), ("step_growth_bt", ctypes.c_double),
-                ("warm_step", ctypes.c_int), ("predict", ctypes.c_int)]
+                ("warm_step", ctypes.c_int), ("predict", ctypes.c_int), ("step_model", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):

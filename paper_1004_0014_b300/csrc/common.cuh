@@ -102,6 +102,8 @@ struct SolveParams {
     int cold_start;  // 1: start from w0; 0: from the state's last accepted w
     int warm_step;   // 1: a warm start also takes the state's next step
     int predict;     // 1: a warm start extrapolates w linearly from the last two solves
+    int step_model;  // 1: curvature-informed first trial and quadratic backtracking
+    int pad2_;
 };
 
 // On-device state of one solve (FP64 scalars; Section 2.2's alternation).

@@ -312,13 +312,22 @@ __device__ void controller_project(SolveState* st, const double* m, int phase, c
     }
     double Jt = cost_at<KM>(st, m, st->a, st->b);
     st->Jt = Jt;
-    bool ok = isfinite(Jt) && Jt <= st->J - st->prm.c1 * st->mu * st->gnorm * st->gnorm;
+    const double mu = st->mu, gn2 = st->gnorm * st->gnorm;
+    // curvature of J along -g from this trial: J(mu) ~ J - mu |g|^2 + (curv/2) mu^2
+    const double curv = 2.0 * (Jt - st->J + mu * gn2) / (mu * mu);
+    const bool model = st->prm.step_model == 1 && curv > 0.0 && isfinite(curv);
+    bool ok = isfinite(Jt) && Jt <= st->J - st->prm.c1 * mu * gn2;
     if (ok) {
         for (int k = 0; k < kMaxK; ++k)
             if (k < K) st->w[k] = st->wt[k];
-        st->mu_prev = st->mu;
-        // next first trial: grow after a first-try acceptance, else keep
-        st->mu_next = (st->bt == 0 ? st->prm.step_growth : st->prm.step_growth_bt) * st->mu;
+        st->mu_prev = mu;
+        // next first trial: the quadratic model's minimiser, at most
+        // step_growth x mu; without the model, grow after a first-try
+        // acceptance and keep after backtracking
+        if (st->prm.step_model == 1)
+            st->mu_next = model ? fmin(st->prm.step_growth * mu, gn2 / curv) : st->prm.step_growth * mu;
+        else
+            st->mu_next = (st->bt == 0 ? st->prm.step_growth : st->prm.step_growth_bt) * mu;
         st->iter += 1;
         st->cum_iters += 1;
         st->accepted = 1;
@@ -341,7 +350,8 @@ __device__ void controller_project(SolveState* st, const double* m, int phase, c
         set_loop(st, 0, h, use_graph);
         return;
     }
-    st->mu *= st->prm.beta;
+    // backtrack: to the quadratic model's minimiser within [0.1 mu, beta mu], or by beta
+    st->mu = model ? fmin(st->prm.beta * mu, fmax(0.1 * mu, gn2 / curv)) : st->prm.beta * mu;
     next_trial(st, K);
 }
 

@@ -276,6 +276,7 @@ int write_params(pr_ctx* c, Model* m, double angle, const pr_solve_opts* o, cuda
     prm.step_growth_bt = o->step_growth_bt;
     prm.warm_step = o->warm_step ? 1 : 0;
     prm.predict = o->predict ? 1 : 0;
+    prm.step_model = o->step_model;
     prm.tumor_tol = o->tumor_tol;
     prm.max_iters = o->max_iters;
     prm.max_bt = o->max_backtracks;
@@ -293,6 +294,7 @@ bool opts_ok(const pr_solve_opts* o) {
            o->beta > 0 && o->beta < 1 && o->c1 >= 0 && o->c1 < 1 && o->step0_mm > 0 && o->grad_tol >= 0 &&
            o->tumor_max_iter >= 0 && o->tumor_max_iter <= 100000 && o->tumor_tol >= 0 &&
            o->step_growth > 0 && o->step_growth <= 100 && o->step_growth_bt > 0 && o->step_growth_bt <= 100 &&
+           (o->step_model == 0 || o->step_model == 1) &&
            (o->loop_mode == PR_LOOP_GRAPH || o->loop_mode == PR_LOOP_HOST);
 }
 
@@ -570,6 +572,7 @@ void pr_default_opts(pr_solve_opts* o) {
     o->step_growth = 2.0;
     o->step_growth_bt = 1.0;
     o->warm_step = 1;
+    o->step_model = 1;
 }
 
 int pr_create(pr_ctx** out, int device, void* stream, size_t hbm_budget_bytes) {

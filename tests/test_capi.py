@@ -78,7 +78,7 @@ def test_defaults_and_version(lib):
 
     o = capi.pr_default_opts()
     assert (o.max_iters, o.c1, o.beta, o.max_backtracks, o.step0_mm) == (10, 1e-4, 0.5, 8, 1.0)
-    assert (o.step_growth, o.step_growth_bt, o.warm_step) == (2.0, 1.0, 1)
+    assert (o.step_growth, o.step_growth_bt, o.warm_step, o.step_model, o.predict) == (2.0, 1.0, 1, 1, 0)
     assert "sm_103a" in capi.pr_version()
 
 
