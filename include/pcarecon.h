@@ -117,10 +117,11 @@ typedef struct {
                               linear prediction from the last two solves' final w
                               (Section 5's predicted coefficients); default 0 */
     int step_model;        /* 1: each trial measures the curvature of J along -g; a rejected
-                              trial backtracks to the quadratic model's minimiser (within
-                              [0.1, beta] x mu) and the next first trial is that minimiser
-                              (at most step_growth x mu); 0: backtrack by beta, growth
-                              factors only; default 1 */
+                              trial backtracks to the quadratic model's minimiser and the next
+                              first trial is that minimiser (at most step_growth x mu), both
+                              rounded down to a power-of-two multiple of mu (backtracking
+                              within [1/16, beta] x mu); 0: backtrack by beta, growth factors
+                              only; default 1 */
 } pr_solve_opts;
 
 typedef struct {

@@ -24,10 +24,12 @@ Readings of the paper where it is silent (the CUDA path uses the same):
     backtracking mu <- beta mu with beta = 0.5, at most 8 backtracks. The
     first trial step is mu = step0_mm / |g| (moves w by step0_mm). Each trial
     at mu measures the curvature of J along -g, curv = 2 (J(mu) - J + mu |g|^2)
-    / mu^2. With step_model 1 (default) a rejected trial backtracks to the
-    minimiser |g|^2 / curv of that quadratic model, kept within [0.1 mu,
-    beta mu], and after an accepted step the next first trial is
-    min(step_growth x mu, |g|^2 / curv) (step_growth = 2); with step_model 0
+    / mu^2, and the quadratic model's minimiser |g|^2 / curv. With step_model 1
+    (default) steps are rounded down to powers of two of mu (so a step's
+    size cannot depend on the last bits of a cost): a rejected trial
+    backtracks to mu x pow2_floor(clamp(minimiser / mu, 1/16, beta)), and
+    after an accepted step the next first trial is mu x pow2_floor(min(
+    step_growth, minimiser / mu)) (step_growth = 2); with step_model 0
     backtracking is mu <- beta mu and the next first trial is step_growth x mu
     if mu was accepted at its first trial, else step_growth_bt x mu. A solve
     warm-started from the previous frame starts with that frame's next trial
@@ -44,6 +46,7 @@ from __future__ import annotations
 
 import ctypes
 import dataclasses
+import math
 import os
 import subprocess
 
@@ -254,6 +257,12 @@ def gradient(model, geom, angle, w, a, b, y):
     return g, float(np.sum(r * r)), p
 
 
+def pow2_floor(x: float) -> float:
+    """The largest power of two not above x (x > 0)."""
+    m, e = math.frexp(x)  # x = m 2^e, 0.5 <= m < 1
+    return math.ldexp(1.0, e - 1)
+
+
 @dataclasses.dataclass
 class SolveOptions:
     max_iters: int = 10
@@ -321,8 +330,9 @@ def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None,
                 accepted = trial
                 break
             backtracks += 1
-            if o.step_model == 1 and curv > 0:  # minimiser of the quadratic model, safeguarded
-                mu = min(o.beta * mu, max(0.1 * mu, gn * gn / curv))
+            if o.step_model == 1:  # quadratic model's minimiser, as a power-of-two fraction of mu
+                ratio = min(o.beta, max(1.0 / 16.0, gn * gn / curv / mu)) if curv > 0 else o.beta
+                mu *= pow2_floor(ratio)
             else:
                 mu *= o.beta
         if accepted is None:
@@ -330,7 +340,8 @@ def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None,
             mu_next = 0.0
             break
         if o.step_model == 1:
-            mu_next = o.step_growth * mu if curv <= 0 else min(o.step_growth * mu, gn * gn / curv)
+            ratio = min(o.step_growth, gn * gn / curv / mu) if curv > 0 else o.step_growth
+            mu_next = mu * pow2_floor(max(ratio, 1.0 / 64.0))
         else:
             mu_next = (o.step_growth if bt == 0 else o.step_growth_bt) * mu
         w = accepted.w

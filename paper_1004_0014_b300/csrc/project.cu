@@ -36,6 +36,15 @@ __device__ bool fit_ab(const SolveState* st, double sp, double spy, double* a, d
     return isfinite(*a) && isfinite(*b);
 }
 
+// The largest power of two not above x (x > 0): steps stay exact power-of-two
+// multiples, so FP32 rounding of a cost can change a step only across a
+// power-of-two boundary.
+__device__ double pow2_floor(double x) {
+    int e;
+    frexp(x, &e);  // x = m 2^e, 0.5 <= m < 1
+    return ldexp(1.0, e - 1);
+}
+
 __device__ void next_trial(SolveState* st, int K) {
 #pragma unroll
     for (int k = 0; k < kMaxK; ++k)
@@ -325,7 +334,8 @@ __device__ void controller_project(SolveState* st, const double* m, int phase, c
         // step_growth x mu; without the model, grow after a first-try
         // acceptance and keep after backtracking
         if (st->prm.step_model == 1)
-            st->mu_next = model ? fmin(st->prm.step_growth * mu, gn2 / curv) : st->prm.step_growth * mu;
+            st->mu_next = mu * pow2_floor(fmax(model ? fmin(st->prm.step_growth, gn2 / curv / mu) : st->prm.step_growth,
+                                               1.0 / 64.0));
         else
             st->mu_next = (st->bt == 0 ? st->prm.step_growth : st->prm.step_growth_bt) * mu;
         st->iter += 1;
@@ -350,8 +360,12 @@ __device__ void controller_project(SolveState* st, const double* m, int phase, c
         set_loop(st, 0, h, use_graph);
         return;
     }
-    // backtrack: to the quadratic model's minimiser within [0.1 mu, beta mu], or by beta
-    st->mu = model ? fmin(st->prm.beta * mu, fmax(0.1 * mu, gn2 / curv)) : st->prm.beta * mu;
+    // backtrack: to the quadratic model's minimiser as a power-of-two fraction
+    // of mu within [1/16, beta], or by beta
+    if (st->prm.step_model == 1)
+        st->mu = mu * pow2_floor(model ? fmin(st->prm.beta, fmax(1.0 / 16.0, gn2 / curv / mu)) : st->prm.beta);
+    else
+        st->mu = st->prm.beta * mu;
     next_trial(st, K);
 }
 
