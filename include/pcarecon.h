@@ -118,10 +118,11 @@ typedef struct {
                               (Section 5's predicted coefficients); default 0 */
     int step_model;        /* 1: each trial measures the curvature of J along -g; a rejected
                               trial backtracks to the quadratic model's minimiser and the next
-                              first trial is that minimiser (at most step_growth x mu), both
-                              rounded down to a power-of-two multiple of mu (backtracking
-                              within [1/16, beta] x mu); 0: backtrack by beta, growth factors
-                              only; default 1 */
+                              first trial is that minimiser (within [1/2, step_growth] x mu),
+                              both rounded down to a power-of-two multiple of mu
+                              (backtracking within [1/16, beta] x mu); the model is used only
+                              where mu |g|^2 > 1e-6 J, elsewhere beta / step_growth apply;
+                              0: backtrack by beta, growth factors only; default 1 */
 } pr_solve_opts;
 
 typedef struct {

@@ -24,12 +24,16 @@ Readings of the paper where it is silent (the CUDA path uses the same):
     backtracking mu <- beta mu with beta = 0.5, at most 8 backtracks. The
     first trial step is mu = step0_mm / |g| (moves w by step0_mm). Each trial
     at mu measures the curvature of J along -g, curv = 2 (J(mu) - J + mu |g|^2)
-    / mu^2, and the quadratic model's minimiser |g|^2 / curv. With step_model 1
+    / mu^2, and the quadratic model's minimiser |g|^2 / curv (the model is used
+    only where mu |g|^2 > 1e-6 J, i.e. where the step can visibly change J;
+    elsewhere the plain factors apply). With step_model 1
     (default) steps are rounded down to powers of two of mu (so a step's
     size cannot depend on the last bits of a cost): a rejected trial
     backtracks to mu x pow2_floor(clamp(minimiser / mu, 1/16, beta)), and
-    after an accepted step the next first trial is mu x pow2_floor(min(
-    step_growth, minimiser / mu)) (step_growth = 2); with step_model 0
+    after an accepted step the next first trial is mu x pow2_floor(clamp(
+    minimiser / mu, 1/2, step_growth)) (step_growth = 2: an accepted step is
+    at most halved, since near convergence the curvature of a cost
+    difference is mostly rounding); with step_model 0
     backtracking is mu <- beta mu and the next first trial is step_growth x mu
     if mu was accepted at its first trial, else step_growth_bt x mu. A solve
     warm-started from the previous frame starts with that frame's next trial
@@ -55,6 +59,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+
+# The quadratic step model is trusted only where a step's predicted decrease
+# mu |g|^2 exceeds this fraction of J.
+MODEL_MIN_DECREASE = 1e-6
 
 STOP_GRAD_TOL = 1
 STOP_MAX_ITERS = 2
@@ -324,8 +332,11 @@ def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None,
         for bt in range(o.max_backtracks + 1):
             trial = evaluate(model, geom, angle, w - mu * g)
             J_t = cost(trial.p, y, a, b)
-            # curvature of J along -g from this trial: J(mu) ~ J - mu |g|^2 + (curv/2) mu^2
+            # curvature of J along -g from this trial: J(mu) ~ J - mu |g|^2 + (curv/2) mu^2;
+            # used only where the step's predicted decrease is resolvable in J
             curv = 2.0 * (J_t - J + mu * gn * gn) / (mu * mu)
+            if not (mu * gn * gn > MODEL_MIN_DECREASE * abs(J)):
+                curv = 0.0
             if J_t <= J - o.c1 * mu * gn * gn:
                 accepted = trial
                 break
@@ -341,7 +352,7 @@ def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None,
             break
         if o.step_model == 1:
             ratio = min(o.step_growth, gn * gn / curv / mu) if curv > 0 else o.step_growth
-            mu_next = mu * pow2_floor(max(ratio, 1.0 / 64.0))
+            mu_next = mu * pow2_floor(max(ratio, 0.5))
         else:
             mu_next = (o.step_growth if bt == 0 else o.step_growth_bt) * mu
         w = accepted.w

@@ -22,6 +22,7 @@ constexpr int kTileU = 32, kTileV = 8, kProjThreads = kTileU * kTileV;
 constexpr int kReduceThreads = 256;
 constexpr int kReduceBlocks = 296;  // 2 per SM on a 148-SM B300
 constexpr int kMaxSamples = 1 << 22;  // samples per ray, far above any real geometry
+constexpr double kModelMinDecrease = 1e-6;  // see controller_project
 
 // ---------------------------------------------------------------------------
 // Controller pieces (thread 0 of the last block; FP64)
@@ -324,7 +325,12 @@ __device__ void controller_project(SolveState* st, const double* m, int phase, c
     const double mu = st->mu, gn2 = st->gnorm * st->gnorm;
     // curvature of J along -g from this trial: J(mu) ~ J - mu |g|^2 + (curv/2) mu^2
     const double curv = 2.0 * (Jt - st->J + mu * gn2) / (mu * mu);
-    const bool model = st->prm.step_model == 1 && curv > 0.0 && isfinite(curv);
+    // The quadratic model is used only where this step's predicted decrease
+    // mu |g|^2 is resolvable in the cost (above kModelMinDecrease x J): a step
+    // too small to change the cost would otherwise read as high curvature and
+    // shrink the next step further and further.
+    const bool model = st->prm.step_model == 1 && curv > 0.0 && isfinite(curv) &&
+                       mu * gn2 > kModelMinDecrease * fabs(st->J);
     bool ok = isfinite(Jt) && Jt <= st->J - st->prm.c1 * mu * gn2;
     if (ok) {
         for (int k = 0; k < kMaxK; ++k)
@@ -334,8 +340,10 @@ __device__ void controller_project(SolveState* st, const double* m, int phase, c
         // step_growth x mu; without the model, grow after a first-try
         // acceptance and keep after backtracking
         if (st->prm.step_model == 1)
+            // an accepted step is at most halved: near convergence the curvature
+            // of a cost difference is mostly rounding
             st->mu_next = mu * pow2_floor(fmax(model ? fmin(st->prm.step_growth, gn2 / curv / mu) : st->prm.step_growth,
-                                               1.0 / 64.0));
+                                               0.5));
         else
             st->mu_next = (st->bt == 0 ? st->prm.step_growth : st->prm.step_growth_bt) * mu;
         st->iter += 1;
