@@ -70,6 +70,9 @@ extern "C" {
 #define PR_STOP_NONFINITE 4         /* non-finite projection or measurement; w kept */
 #define PR_STOP_SINGULAR_FIT 5      /* Y^T Y of Eq. 4 is singular (constant y); w kept */
 #define PR_STOP_GUARD 6             /* internal trial bound reached (should not happen) */
+#define PR_STOP_RESOLVED 7          /* step_model 1: a rejected trial's predicted decrease
+                                       mu |grad J|^2 was already <= 1e-6 J, so no step can
+                                       lower J by a resolvable amount; w kept */
 
 #define PR_MAX_K 7 /* most PCA modes per model */
 

@@ -43,7 +43,9 @@ Readings of the paper where it is silent (the CUDA path uses the same):
     forgotten.
   * (a, b) before the first step 1: Eq. 4 at the starting w.
   * Stop (Section 2.2: gradient "sufficiently small" or the iteration cap):
-    |g| <= grad_tol * |g_0| or max_iters accepted steps.
+    |g| <= grad_tol * |g_0|, or max_iters accepted steps, or (step_model 1) a
+    rejected trial whose predicted decrease mu |g|^2 is already at most
+    1e-6 J: no step along -g can lower J by a resolvable amount.
 """
 
 from __future__ import annotations
@@ -67,6 +69,7 @@ MODEL_MIN_DECREASE = 1e-6
 STOP_GRAD_TOL = 1
 STOP_MAX_ITERS = 2
 STOP_LINESEARCH_FAILED = 3
+STOP_RESOLVED = 7
 
 
 def build_oracle(force: bool = False) -> str:
@@ -329,6 +332,7 @@ def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None,
         # Step 1: w <- w - mu g, mu by backtracking from the initial trial.
         mu = mu_next if mu_next else o.step0_mm / gn
         accepted = None
+        resolved = False
         for bt in range(o.max_backtracks + 1):
             trial = evaluate(model, geom, angle, w - mu * g)
             J_t = cost(trial.p, y, a, b)
@@ -341,11 +345,18 @@ def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None,
                 accepted = trial
                 break
             backtracks += 1
+            if o.step_model == 1 and not (mu * gn * gn > MODEL_MIN_DECREASE * abs(J)):
+                resolved = True  # no step along -g changes J by a resolvable amount
+                break
             if o.step_model == 1:  # quadratic model's minimiser, as a power-of-two fraction of mu
                 ratio = min(o.beta, max(1.0 / 16.0, gn * gn / curv / mu)) if curv > 0 else o.beta
                 mu *= pow2_floor(ratio)
             else:
                 mu *= o.beta
+        if resolved:
+            stop = STOP_RESOLVED
+            mu_next = mu
+            break
         if accepted is None:
             stop = STOP_LINESEARCH_FAILED
             mu_next = 0.0

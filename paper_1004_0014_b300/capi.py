@@ -30,6 +30,7 @@ PR_STOP_MAX_ITERS = 2
 PR_STOP_LINESEARCH_FAILED = 3
 PR_STOP_NONFINITE = 4
 PR_STOP_SINGULAR_FIT = 5
+PR_STOP_RESOLVED = 7
 
 PR_MAX_K = 7
 PR_HOST, PR_DEVICE = 0, 1

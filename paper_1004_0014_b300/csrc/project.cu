@@ -361,6 +361,16 @@ __device__ void controller_project(SolveState* st, const double* m, int phase, c
     st->accepted = 0;
     st->bt += 1;
     st->total_bt += 1;
+    if (st->prm.step_model == 1 && !(mu * gn2 > kModelMinDecrease * fabs(st->J))) {
+        // Even this step's predicted decrease is below what the cost resolves,
+        // and a smaller one only less: the gradient is sufficiently small
+        // (Section 2.2's stop) at the cost's resolution. w keeps its last
+        // accepted value; the next frame starts from this step.
+        st->stop = 7;  // PR_STOP_RESOLVED
+        st->mu_next = mu;
+        set_loop(st, 0, h, use_graph);
+        return;
+    }
     if (st->bt > st->prm.max_bt) {
         st->stop = 3;  // PR_STOP_LINESEARCH_FAILED: w keeps its last accepted value
         st->cum_lsf += 1;
