@@ -19,7 +19,7 @@ from . import capi
 from .capi import (  # noqa: F401
     PR_BF16, PR_DEVICE, PR_F32, PR_HOST, PR_LOOP_GRAPH, PR_LOOP_HOST, PR_MAX_K,
     PR_STOP_GRAD_TOL, PR_STOP_LINESEARCH_FAILED, PR_STOP_MAX_ITERS, PR_STOP_NONFINITE,
-    PR_STOP_SINGULAR_FIT, Geometry, PcaReconError, Result, SolveOpts, VolumeDesc,
+    PR_STOP_RESOLVED, PR_STOP_SINGULAR_FIT, Geometry, PcaReconError, Result, SolveOpts, VolumeDesc,
 )
 
 
