@@ -17,6 +17,8 @@
  *   or_backproject  the gradient formula after Eq. 4: P^T, the transpose of P
  *   or_tumor        Section 2.3: tumor position through the inverted pull-back
  *                   DVF, by the fixed-point inversion of Chen et al. (ref. 13)
+ *   or_invert       Section 2.3 with ref. 13 over the whole grid: the
+ *                   push-forward DVF, the inverse of the pull-back field
  *
  * Readings where the paper is silent (each also used by the CUDA path):
  *   - grid: voxel (i,j,k) at origin + (i,j,k)*spacing, origin = -(n-1)/2*spacing;
@@ -320,4 +322,46 @@ int or_tumor(const or_vol* v, const double* mean, const double* U, int K, const 
 void or_dvf_at(const or_vol* v, const double* mean, const double* U, int K, const double* w,
                const double p[3], double out[3]) {
     dvf_at(v, mean, U, K, w, p, out);
+}
+
+/*
+ * Section 2.3 with ref. 13 over the whole grid: the push-forward DVF y that
+ * inverts the pull-back field x = mean + sum_k u_k w_k, i.e. the displacement
+ * with  u + y(u) + x(u + y(u)) = u  at every voxel centre u. Chen et al.'s
+ * fixed-point iteration updates the whole field in each sweep,
+ *     y_{m+1}(u) = -x(u + y_m(u)),   y_0 = 0,
+ * with x trilinear and clamped to the grid edge (dvf_at), and stops when the
+ * largest update of a sweep (Euclidean, mm) is below tol or after max_iter
+ * sweeps. A voxel's update reads only its own previous value, so the sweep
+ * runs in place. y: [3][nz][ny][nx] doubles (mm). Returns the sweep count.
+ */
+int or_invert(const or_vol* v, const double* mean, const double* U, int K, const double* w,
+              double tol, int max_iter, double* y) {
+    size_t n = (size_t)v->nx * v->ny * v->nz;
+    double o[3];
+    origin(v, o);
+    memset(y, 0, 3 * n * sizeof(double));
+    int sweeps = 0;
+    while (sweeps < max_iter) {
+        double largest = 0.0;
+        for (int k = 0; k < v->nz; ++k)
+            for (int j = 0; j < v->ny; ++j)
+                for (int i = 0; i < v->nx; ++i) {
+                    size_t e = vox(v, i, j, k);
+                    double u[3] = {o[0] + i * v->dx, o[1] + j * v->dy, o[2] + k * v->dz};
+                    double pt[3], x[3], d2 = 0.0;
+                    for (int c = 0; c < 3; ++c) pt[c] = u[c] + y[(size_t)c * n + e];
+                    dvf_at(v, mean, U, K, w, pt, x);
+                    for (int c = 0; c < 3; ++c) {
+                        double next = -x[c];
+                        double step = next - y[(size_t)c * n + e];
+                        d2 += step * step;
+                        y[(size_t)c * n + e] = next;
+                    }
+                    if (d2 > largest) largest = d2;
+                }
+        ++sweeps;
+        if (sqrt(largest) < tol) break;
+    }
+    return sweeps;
 }

@@ -194,6 +194,21 @@ def tumor(vol, mean, U, w, c0, tol=1e-6, max_iter=100):
     return p, int(it)
 
 
+def invert(vol, mean, U, w, tol=1e-9, max_iter=200):
+    """Section 2.3 with ref. 13 over the whole grid: the push-forward DVF y
+    [3][nz][ny][nx] (mm) with u + y(u) + x(u + y(u)) = u at every voxel centre,
+    by Chen et al.'s whole-field fixed-point sweeps y <- -x(u + y) from y = 0
+    (x trilinear, clamped to the grid edge). Returns (y, sweeps)."""
+    mean, pm = _d(mean)
+    U, pU = _d(U)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    y = np.empty((3,) + tuple(vol.shape), dtype=np.float64)
+    sweeps = _L().or_invert(ctypes.byref(_vol(vol)), pm, pU, ctypes.c_int(len(w)),
+                            w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_double(tol),
+                            ctypes.c_int(max_iter), y.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return y, int(sweeps)
+
+
 def dvf_at(vol, mean, U, w, point):
     """x = mean + U w interpolated (clamp-to-edge) at a world point (mm)."""
     mean, pm = _d(mean)

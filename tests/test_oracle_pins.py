@@ -410,3 +410,84 @@ def test_tumor_round_trip_on_pca_dvf(small_case):
     x = O.dvf_at(c["vol"], c["pca"].mean, c["pca"].U, w, p)
     assert np.max(np.abs(p + x - c["c0"])) < 1e-9
     assert steps < 200
+
+
+# ----------------------------------------------------------------------------
+# Section 2.3 with ref. 13: the push-forward (inverse) DVF on the whole grid
+# ----------------------------------------------------------------------------
+
+
+def test_inverse_field_of_translation_is_minus_the_shift():
+    vol = Volume(16, 14, 12, 2.0, 2.0, 2.5)
+    t = np.array([1.3, -2.1, 4.4])
+    mean = np.zeros((3,) + vol.shape)
+    for c in range(3):
+        mean[c] = t[c]
+    U = RNG.standard_normal((2, 3) + vol.shape)
+    y, sweeps = O.invert(vol, mean, U, np.zeros(2), tol=1e-12)
+    for c in range(3):
+        assert np.max(np.abs(y[c] + t[c])) < 1e-12
+    assert sweeps <= 3
+
+
+def test_inverse_field_of_affine_dvf_is_the_closed_form():
+    # x(p) = A p + t (trilinear reproduces it inside the grid), so u + y + A(u + y) + t = u
+    # gives y(u) = (I + A)^-1 (u - t) - u. Checked where every iterate stays inside the grid.
+    vol = Volume(20, 18, 16, 2.0, 2.5, 3.0)
+    A0 = np.array([[0.05, -0.02, 0.01], [0.03, 0.04, -0.02], [-0.01, 0.02, 0.06]])
+    A1 = np.array([[0.02, 0.01, 0.0], [-0.01, 0.03, 0.01], [0.0, -0.02, 0.01]])
+    t0, t1 = np.array([0.7, -1.2, 2.0]), np.array([0.3, 0.5, -0.4])
+    z, yy, x = _grid_points(vol)
+    pts = np.stack([x, yy, z])
+    mean = np.einsum("ab,b...->a...", A0, pts) + t0.reshape(3, 1, 1, 1)
+    U = (np.einsum("ab,b...->a...", A1, pts) + t1.reshape(3, 1, 1, 1))[None]
+    w = np.array([0.7])
+    y, _ = O.invert(vol, mean, U, w, tol=1e-13, max_iter=300)
+    A, t = A0 + w[0] * A1, t0 + w[0] * t1
+    expect = np.einsum("ab,b...->a...", np.linalg.inv(np.eye(3) + A), pts - t.reshape(3, 1, 1, 1)) - pts
+    inner = (slice(None), slice(3, vol.nz - 3), slice(3, vol.ny - 3), slice(3, vol.nx - 3))
+    assert np.max(np.abs(y - expect)[inner]) < 1e-10
+    assert np.max(np.abs(expect[inner])) > 1.0  # displacements of a few mm, not a trivial field
+
+
+def test_inverse_field_along_one_axis_matches_bisection():
+    # x = (0, 0, a sin(2 pi z / L)) sampled on the nodes: along z the interpolant is
+    # numpy's piecewise-linear interp (which also clamps to the end values), and each
+    # voxel's inverse solves the scalar equation d + X(z_u + d) = 0 with X increasing
+    # slower than d, found here by bisection.
+    vol = Volume(6, 5, 40, 2.0, 2.0, 2.5)
+    ax, ay, az = vol.axes()
+    a, L = 3.0, 40.0
+    xz = a * np.sin(2 * math.pi * az / L)
+    mean = np.zeros((3,) + vol.shape)
+    mean[2] = xz[:, None, None]
+    U = np.zeros((1, 3) + vol.shape)
+    y, _ = O.invert(vol, mean, U, np.zeros(1), tol=1e-13, max_iter=300)
+    for k, zu in enumerate(az):
+        lo, hi = -4 * a, 4 * a
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if mid + np.interp(zu + mid, az, xz) > 0:
+                hi = mid
+            else:
+                lo = mid
+        d = 0.5 * (lo + hi)
+        assert np.max(np.abs(y[2, k] - d)) < 1e-10, k
+    assert np.max(np.abs(y[0])) < 1e-13 and np.max(np.abs(y[1])) < 1e-13
+
+
+def test_inverse_field_at_nodes_equals_pointwise_tumor_and_round_trips(small_case):
+    c = small_case
+    vol, mean, U = c["vol"], c["pca"].mean, c["pca"].U
+    w = np.array([1.2, -0.3, 0.1])
+    y, sweeps = O.invert(vol, mean, U, w, tol=1e-12, max_iter=200)
+    assert sweeps < 200
+    ax, ay, az = vol.axes()
+    rng = np.random.default_rng(7)
+    for _ in range(40):
+        i, j, k = int(rng.integers(vol.nx)), int(rng.integers(vol.ny)), int(rng.integers(vol.nz))
+        u = np.array([ax[i], ay[j], az[k]])
+        p, _ = O.tumor(vol, mean, U, w, u, tol=1e-13, max_iter=200)
+        assert np.max(np.abs(y[:, k, j, i] - (p - u))) < 1e-9
+        x = O.dvf_at(vol, mean, U, w, u + y[:, k, j, i])
+        assert np.max(np.abs(y[:, k, j, i] + x)) < 1e-9
