@@ -455,6 +455,7 @@ def run_ours(args):
                         ("regrad", capi.PR_KERNEL_REGRAD), ("warp_f", capi.PR_KERNEL_WARP_F),
                         ("project_f", capi.PR_KERNEL_PROJECT_F)):
         kern[name] = ctx.time_kernel(mid, which, angles[W], iters=20)
+    kern["invert_dvf"] = ctx.time_kernel(mid, capi.PR_KERNEL_INVERT, angles[W], iters=5)
     if args.adjoint:
         kern["backproject_dot"] = ctx.time_kernel(mid, capi.PR_KERNEL_BACKPROJECT, angles[W], iters=3)
 
@@ -495,6 +496,15 @@ def run_ours(args):
                      "traffic": recorded_traffic("k_warp<3,FH,float>", "warp.cu"),
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if peaks else "fallback",
                      "algorithmic_bytes_per_launch": bytes_warp, "share_of_solve": share_warp}
+
+    # Whole-grid DVF inversion (Section 2.3 with ref. 13), outside the solve:
+    # x/dx synthesis (12 + 12K bytes read, 16 written per voxel), then the
+    # per-voxel fixed point (the 16-byte field read once, 12 bytes of y written).
+    bytes_inv = N * (12 + 12 * Km + 16 + 16 + 12)
+    inv_gbs = bytes_inv / (kern["invert_dvf"] / 1000.0) / 1e9
+    roofline_invert = {"kernels": "k_dvf_idx + k_invert", "bound": "hbm", "achieved": inv_gbs, "peak": hbm_peak,
+                       "unit": "GB/s", "frac": inv_gbs / hbm_peak, "algorithmic_bytes_per_call": bytes_inv,
+                       "ms": kern["invert_dvf"], "tol_mm": 1e-5, "max_iter": 64}
 
     # ---------------- CPU baseline (rank 0, N = 1) ----------------
     cpu = None
@@ -537,6 +547,7 @@ def run_ours(args):
             "kernel_ms": kern,
             "roofline": roofline,
             "roofline_warp": roofline_warp,
+            "roofline_invert_dvf": roofline_invert,
             "clocks": clk.summary(),
             "paper_context": {"s_per_projection": 0.24, "hardware": "Tesla C1060",
                               "workload": "NCAT 256x256x120, K=3, 200x150 projections (context only)"},

@@ -295,6 +295,22 @@ int pr_cost_grad(pr_ctx* ctx, int model_id, const float* y_dev, double angle_rad
 int pr_tumor(pr_ctx* ctx, int model_id, const double* w, double tol, int max_iter, double* xyz,
              int* steps);
 
+/* Section 2.3 with ref. 13 over the whole grid: the push-forward DVF y, the
+ * inverse of the model's pull-back field x = mean + U w (w: K doubles, host),
+ * i.e. u + y(u) + x(u + y(u)) = u at every voxel centre u, x interpolated
+ * trilinearly with clamp to the grid edge. Chen et al.'s fixed point
+ * y <- -x(u + y) from y = 0 is iterated at each voxel until its update is
+ * below tol mm (Euclidean) or after max_iter (1..100000) updates. y_dev
+ * [3][nz][ny][nx] float32 mm (device, caller-owned). max_steps (nullable)
+ * receives the largest per-voxel update count, unconverged (nullable) the
+ * number of voxels whose last update was not below tol. The model's solver
+ * volume buffer is used as scratch (not while the model has frames in a
+ * serving slot). Synchronous. Errors: PR_EINVAL (null w or y_dev, tol < 0,
+ * max_iter out of range, a grid of 2^31 voxels or more), PR_ENOMODEL,
+ * PR_ECUDA. */
+int pr_invert_dvf(pr_ctx* ctx, int model_id, const double* w, double tol, int max_iter, float* y_dev,
+                  int* max_steps, long long* unconverged);
+
 /* ---- allocation-free cost and gradient (no counterpart in the paper) ----
  *
  * For callers that cannot allocate device memory while they run: a real-time
@@ -330,7 +346,8 @@ enum {
     PR_KERNEL_REGRAD = 2,       /* residual, cost and gradient over the detector (pr_cost_grad) */
     PR_KERNEL_BACKPROJECT = 3,  /* gather transpose contracted with h (adjoint gradient) */
     PR_KERNEL_WARP_F = 4,       /* warp writing f only */
-    PR_KERNEL_PROJECT_F = 5     /* ray-march projection of f only */
+    PR_KERNEL_PROJECT_F = 5,    /* ray-march projection of f only */
+    PR_KERNEL_INVERT = 6        /* whole-grid DVF inversion (pr_invert_dvf, tol 1e-5 mm, 64 steps) */
 };
 
 /* Launch kernel `which` `iters` times back to back on the context stream

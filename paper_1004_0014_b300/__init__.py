@@ -160,6 +160,16 @@ class Context:
     def tumor(self, mid: int, w, tol: float = 1e-6, max_iter: int = 100):
         return capi.pr_tumor(self._ctx, mid, w, tol, max_iter)
 
+    def invert_dvf(self, mid: int, w, tol: float = 1e-5, max_iter: int = 64):
+        """Push-forward DVF (3, nz, ny, nx) float32 mm on the device, the largest
+        per-voxel step count and the number of voxels not converged to tol."""
+        import torch
+
+        vol = self._models[mid]["vol"]
+        y = torch.empty((3, vol.nz, vol.ny, vol.nx), dtype=torch.float32, device="cuda:%d" % self.device)
+        steps, open_ = capi.pr_invert_dvf(self._ctx, mid, w, y, tol, max_iter)
+        return y, steps, open_
+
     # --- serving -------------------------------------------------------------
     def serve_start(self, slots: int = 4):
         capi.pr_serve_start(self._ctx, slots)

@@ -41,12 +41,12 @@ EXPORTED = [
     "pr_version", "pr_last_error", "pr_default_opts", "pr_create", "pr_destroy", "pr_load_model",
     "pr_release_model", "pr_model_footprint", "pr_reconstruct", "pr_reconstruct_async",
     "pr_fetch_result", "pr_get_state", "pr_set_state", "pr_warp", "pr_project", "pr_backproject",
-    "pr_forward", "pr_vjp", "pr_cost_grad", "pr_tumor", "pr_time_kernel", "pr_model_stats",
+    "pr_forward", "pr_vjp", "pr_cost_grad", "pr_tumor", "pr_invert_dvf", "pr_time_kernel", "pr_model_stats",
     "pr_io_bytes", "pr_cost_grad_static", "pr_serve_start", "pr_submit", "pr_poll", "pr_serve_stop",
 ]
 
 PR_KERNEL_WARP_FH, PR_KERNEL_PROJECT_FH, PR_KERNEL_REGRAD = 0, 1, 2
-PR_KERNEL_BACKPROJECT, PR_KERNEL_WARP_F, PR_KERNEL_PROJECT_F = 3, 4, 5
+PR_KERNEL_BACKPROJECT, PR_KERNEL_WARP_F, PR_KERNEL_PROJECT_F, PR_KERNEL_INVERT = 3, 4, 5, 6
 
 
 class Stats(ctypes.Structure):
@@ -149,6 +149,7 @@ def load_library(path: str | None = None):
         "pr_vjp": (_I, [_P, _I, _DP, _D, _P, _DP]),
         "pr_cost_grad": (_I, [_P, _I, _P, _D, _DP, _D, _D, _I, _DP, _DP, _P]),
         "pr_tumor": (_I, [_P, _I, _DP, _D, _I, _DP, ctypes.POINTER(_I)]),
+        "pr_invert_dvf": (_I, [_P, _I, _DP, _D, _I, _P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_longlong)]),
         "pr_time_kernel": (_I, [_P, _I, _I, _D, _I, _DP]),
         "pr_model_stats": (_I, [_P, _I, ctypes.POINTER(Stats)]),
         "pr_io_bytes": (_I, [_P, _I, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
@@ -350,6 +351,16 @@ def pr_tumor(ctx, model_id: int, w, tol: float = 1e-6, max_iter: int = 100):
     _check(_lib.pr_tumor(ctx, int(model_id), pw, float(tol), int(max_iter), xyz.ctypes.data_as(_DP),
                          ctypes.byref(steps)))
     return xyz, steps.value
+
+
+def pr_invert_dvf(ctx, model_id: int, w, y_dev, tol: float = 1e-5, max_iter: int = 64):
+    """Fills y_dev [3][nz][ny][nx] (device float32, mm); returns (max steps, unconverged voxels)."""
+    w, pw = _dvec(w)
+    steps = ctypes.c_int()
+    open_ = ctypes.c_longlong()
+    _check(_lib.pr_invert_dvf(ctx, int(model_id), pw, float(tol), int(max_iter), _dev(y_dev, "y_dev"),
+                              ctypes.byref(steps), ctypes.byref(open_)))
+    return steps.value, open_.value
 
 
 def pr_time_kernel(ctx, model_id: int, which: int, angle_rad: float, iters: int) -> float:

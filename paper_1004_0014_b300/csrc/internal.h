@@ -81,6 +81,13 @@ cudaError_t launch_cost_grad(Launcher& L, const float* p, const float* q, const 
 cudaError_t launch_tumor(Launcher& L, const ModelDev& m, const double* w_dev, double tol, int max_iter,
                          const SolveParams* prm, double* xyz_out, int* steps_out);
 
+// Section 2.3 with ref. 13 on the whole grid: push-forward field y [3][N] (mm,
+// device) of x = mean + U w (w_dev: K device doubles). X: scratch of N float4.
+// stats (device, 2 uints, zeroed by the caller): [0] the largest per-voxel step
+// count, [1] voxels whose last update was not below tol (mm).
+cudaError_t launch_invert(Launcher& L, const ModelDev& m, const double* w_dev, float4* X, double tol, int max_iter,
+                          float* y, unsigned int* stats);
+
 // r = p - a y - b with (a, b) = ab_dev[0..1].
 cudaError_t launch_residual(Launcher& L, const float* p, const float* y, int R, const double* ab_dev, float* r);
 

@@ -968,10 +968,33 @@ int pr_tumor(pr_ctx* c, int id, const double* w, double tol, int max_iter, doubl
     return PR_OK;
 }
 
+int pr_invert_dvf(pr_ctx* c, int id, const double* w, double tol, int max_iter, float* y_dev, int* max_steps,
+                  long long* unconverged) {
+    GET_MODEL(c, id, m);
+    if (!w || !y_dev) return fail(PR_EINVAL, "null argument");
+    if (!(tol >= 0) || !std::isfinite(tol) || max_iter < 1 || max_iter > 100000)
+        return fail(PR_EINVAL, "invalid tol or max_iter");
+    if (m->vol.nx * (long long)m->vol.ny * m->vol.nz >= 0x7fffffffLL) return fail(PR_EINVAL, "grid too large");
+    TRY(set_w(c, m, w));
+    Launcher L;
+    L.stream = c->stream;
+    unsigned int* stats = reinterpret_cast<unsigned int*>(m->partials);
+    CK(cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned int), c->stream));
+    CK(launch_invert(L, m->md, m->wdev, reinterpret_cast<float4*>(m->fh), tol, max_iter, y_dev, stats));
+    unsigned int st[2] = {0, 0};
+    CK(cudaMemcpyAsync(st, stats, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (max_steps) *max_steps = (int)st[0];
+    if (unconverged) *unconverged = (long long)st[1];
+    return PR_OK;
+}
+
 int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double* avg_ms) {
     GET_MODEL(c, id, m);
     if (!avg_ms || iters < 1 || iters > 100000) return fail(PR_EINVAL, "invalid iters or output");
-    if (which < PR_KERNEL_WARP_FH || which > PR_KERNEL_PROJECT_F) return fail(PR_EINVAL, "unknown kernel %d", which);
+    if (which < PR_KERNEL_WARP_FH || which > PR_KERNEL_INVERT) return fail(PR_EINVAL, "unknown kernel %d", which);
+    if (which == PR_KERNEL_INVERT && m->vol.nx * (long long)m->vol.ny * m->vol.nz >= 0x7fffffffLL)
+        return fail(PR_EINVAL, "grid too large");
     TRY(set_rg(c, m->rg, m->vol, m->geom, angle));
     if (which == PR_KERNEL_BACKPROJECT) TRY(ensure_hbuf(m));
     Launcher L;
@@ -985,10 +1008,12 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
     if (which == PR_KERNEL_BACKPROJECT) CK(launch_warp(L, m->md, m->st->w, kWarpFlatFH, nullptr, nullptr, m->hbuf));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, m->order, nu, nv, m->p, m->q, nullptr, nullptr, nullptr, nullptr,
                       kPhaseNone, 0, 0, SupportRef{m->sup, m->st->w, m->K}));
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    cudaError_t err = cudaEventRecord(e0, c->stream);
+    float* ytmp = nullptr;  // output of the timed inversion (3N floats, freed below)
+    if (which == PR_KERNEL_INVERT) CK(cudaMalloc(&ytmp, (size_t)3 * m->md.vd.n * sizeof(float)));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
     for (int i = 0; i < iters && err == cudaSuccess; ++i) {
         switch (which) {
             case PR_KERNEL_WARP_FH: err = launch_warp(L, m->md, m->st->w, kWarpFH, m->fh, nullptr, nullptr); break;
@@ -1008,14 +1033,23 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
                 err = launch_project(L, m->md.vd, m->fpad, 1, 0, m->rg, m->order, nu, nv, m->r, nullptr, nullptr, nullptr,
                                      nullptr, nullptr, kPhaseNone, 0, 0, SupportRef{m->sup, m->st->w, m->K});
                 break;
+            case PR_KERNEL_INVERT:
+                err = launch_invert(L, m->md, m->st->w, reinterpret_cast<float4*>(m->fh), 1e-5, 64, ytmp,
+                                    reinterpret_cast<unsigned int*>(m->partials));
+                break;
         }
     }
     if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
     if (err == cudaSuccess) err = cudaEventSynchronize(e1);
     float ms = 0.0f;
     if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (ytmp) {
+        cudaError_t e2 = cudaStreamSynchronize(c->stream);
+        cudaFree(ytmp);
+        if (err == cudaSuccess) err = e2;
+    }
     CK(err);
     *avg_ms = (double)ms / iters;
     return PR_OK;

@@ -122,3 +122,17 @@ def test_autograd_matches_finite_differences_and_oracle(k5):
     report("autograd_32", oracle_rel_max=worst_o, fd_rel_max=worst_fd)
     assert worst_o < TOL_GRAD
     assert worst_fd < 1e-2
+
+
+@pytest.mark.parametrize("name", ["f32", "bf16"])
+def test_k5_inverse_field(k5, name):
+    """Whole-grid DVF inversion of a K = 5 model (two loads of the eigenvector
+    fields per voxel in bfloat16) against the oracle on the same stored fields."""
+    mid, om = k5["models"][name]
+    w = np.array([1.5, -0.6, 0.3, 0.15, -0.09])
+    y, steps, open_ = k5["ctx"].invert_dvf(mid, w, tol=1e-5, max_iter=64)
+    yo, sweeps = O.invert(k5["vol"], om.mean, om.U, w, tol=1e-10, max_iter=200)
+    err = float(np.max(np.abs(y.cpu().numpy().astype(np.float64) - yo)))
+    report("k5_invert_" + name, max_abs_mm=err, max_steps=steps, oracle_sweeps=sweeps, unconverged=open_)
+    assert open_ == 0
+    assert err < 1e-3
