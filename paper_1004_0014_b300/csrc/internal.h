@@ -55,11 +55,32 @@ struct SupportRef {
     int K = 0;
 };
 
+// Scratch of the split-ray solver-pass projector (one per model; see
+// k_project_split): warp-tile order, per-part sums, tile and group moments,
+// and counters that must be zero before the first launch (each launch leaves
+// them zero).
+struct SplitScratch {
+    const int* order = nullptr;   // split_tiles ints (project_warp_tile_order)
+    float* part = nullptr;        // split_part_floats floats
+    double* tile_mom = nullptr;   // split_tiles x kProjMom doubles
+    double* group_mom = nullptr;  // split_groups x kProjMom doubles
+    unsigned int* ctr = nullptr;  // split_counters uints, zeroed once
+};
+int split_tiles(int nu, int nv);
+int split_groups(int nu, int nv);
+size_t split_part_floats(int nu, int nv, int nch);
+size_t split_counters(int nu, int nv);
+// Host: 8x4 warp tiles in launch order (split_tiles ints), centre first.
+void project_warp_tile_order(int nu, int nv, int* order);
+
 // order: device permutation of the detector tiles (nullable), see project_tile_order.
+// With nch 4 or 8 and ss given, the split-ray kernel runs (its own tile order
+// and scratch from ss; `order`, `partials` and `counter` unused).
 cudaError_t launch_project(Launcher& L, const VolDev& vd, const float* vol_pad, int nch, int K,
                            const RayGeom* rg, const int* order, int nu, int nv, float* p, float* q,
                            const float* y, SolveState* st, double* partials, unsigned int* counter,
-                           int phase, cudaGraphConditionalHandle h, int use_graph, SupportRef sup = {});
+                           int phase, cudaGraphConditionalHandle h, int use_graph, SupportRef sup = {},
+                           const SplitScratch* ss = nullptr);
 
 // Support of f0 and the largest |mean_c|, |u_kc| into sup (device); f0, mean, U
 // float32 unpadded (U may be one plane at a time: plane index k*3 + c).

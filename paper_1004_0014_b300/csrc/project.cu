@@ -15,6 +15,10 @@
 
 #include "internal.h"
 
+#include <algorithm>
+#include <utility>
+#include <vector>
+
 namespace pr {
 namespace {
 
@@ -485,6 +489,242 @@ __global__ void __launch_bounds__(kProjThreads, NCH == 4 ? 4 : 1) k_project(Proj
     }
 }
 
+// ---------------------------------------------------------------------------
+// Solver-pass projector with split rays and a dynamic work queue
+// ---------------------------------------------------------------------------
+//
+// The 4/8-channel pass has 1.3 rays per resident thread at paper scale, and
+// its run time was the time of the longest 32x8 tile: the last wave left SMs
+// idle and blocks held their slots while waiting for their slowest warp. Here
+// the unit of work is one third of the sample range of an 8x4-ray warp tile.
+// Warps take items from a global counter, longest tiles first (the parts of
+// a tile one after another), so the busy time evens out at the scale of a
+// third of a ray. Each part's sums go to scratch; the warp that finishes a
+// tile's last part adds the parts in a fixed order, writes p and q and the
+// tile's moments; fixed groups of 64 tiles and then the groups are summed in
+// tile order by whichever warp completes them, and the warp that completes
+// the last group runs the controller. Every sum is taken in an order fixed
+// by tile and part index, never by timing, so results are deterministic.
+// No warp ever waits for another.
+constexpr int kParts = 3;        // sample-range parts per warp tile
+constexpr int kGroupTiles = 64;  // tiles per fixed-order moment group
+constexpr int kSplitThreads = 256;
+
+struct SplitArgs {
+    const float* vol;
+    VolDev vd;
+    const RayGeom* rg;
+    const int* order;  // warp-tile permutation, longest rays first (nullable)
+    int nu, nv, K;
+    int ntu, ntiles, ngroups;
+    float* p;
+    float* q;
+    const float* y;
+    SolveState* st;
+    float* part;        // [ntiles][kParts][NCH + 1][32]: channel sums and the f compensation
+    double* tile_mom;   // [ntiles][kProjMom]
+    double* group_mom;  // [ngroups][kProjMom]
+    unsigned int* ctr;  // [0] queue, [1] warps done, [2] groups done, [4 + g] group g, [4 + ngroups + t] tile t
+    int phase;
+    cudaGraphConditionalHandle h;
+    int use_graph;
+    SupportRef sup;
+};
+
+// The warp that completed a tile: adds its parts in part order, writes p and
+// q, and (solver phases) forms the tile's moments and carries the fixed-order
+// group and total sums. Kept out of line so that its registers do not weigh on
+// the sample loop.
+template <int NCH>
+__device__ __noinline__ void finish_tile(const SplitArgs& A, int tile, int iu, int iv, bool valid, float ds) {
+    constexpr int KM = NCH == 8 ? 7 : 3;
+    constexpr int NV = 3 + 3 * KM;
+    const int lane = threadIdx.x & 31;
+    unsigned int* tile_ctr = A.ctr + 4 + A.ngroups;
+    unsigned int prev = 0;
+    // ---- this warp completed the tile: parts in fixed order ----
+    __threadfence();
+    if (lane == 0) tile_ctr[tile] = 0;
+    const float* src = A.part + (size_t)tile * kParts * (NCH + 1) * 32 + lane;
+    float fs = 0.0f, hs[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) hs[c] = 0.0f;
+#pragma unroll
+    for (int pp = 0; pp < kParts; ++pp) {
+        const float* sp = src + (size_t)pp * (NCH + 1) * 32;
+        fs = __fadd_rn(fs, __fsub_rn(__ldcg(sp), __ldcg(sp + NCH * 32)));
+#pragma unroll
+        for (int c = 1; c < NCH; ++c) hs[c] = __fadd_rn(hs[c], __ldcg(sp + c * 32));
+    }
+    const int R = A.nu * A.nv;
+    const int r = iv * A.nu + iu;
+    const float pv = fs * ds;
+    if (valid) {
+        A.p[r] = pv;
+        if (A.q)
+            for (int k = 0; k < A.K; ++k) A.q[(long long)k * R + r] = hs[1 + (k < NCH - 1 ? k : 0)] * ds;
+    }
+    if (A.phase == kPhaseNone) return;
+
+    // tile moments (see cost_at): exact float-float products, float-float warp sums
+    float mh[NV], ml[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) mh[i] = ml[i] = 0.0f;
+    if (valid) {
+        const float yv = A.y[r];
+        ff_prod(pv, pv, mh[0], ml[0]);
+        ff_prod(pv, yv, mh[1], ml[1]);
+        mh[2] = pv;
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            if (k < A.K) {
+                const float qv = hs[1 + k] * ds;
+                ff_prod(pv, qv, mh[3 + k], ml[3 + k]);
+                ff_prod(yv, qv, mh[3 + KM + k], ml[3 + KM + k]);
+                mh[3 + 2 * KM + k] = qv;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int m = 0; m < NV; ++m) {
+            float bh = __shfl_down_sync(0xffffffffu, mh[m], o), bl = __shfl_down_sync(0xffffffffu, ml[m], o);
+            ff_add(mh[m], ml[m], bh, bl);
+        }
+    if (lane == 0) {
+#pragma unroll
+        for (int m = 0; m < NV; ++m) A.tile_mom[(size_t)tile * kProjMom + m] = (double)mh[m] + (double)ml[m];
+        __threadfence();
+    }
+    __syncwarp();
+    const int group = tile / kGroupTiles;
+    const int gsize = min(kGroupTiles, A.ntiles - group * kGroupTiles);
+    if (lane == 0) prev = atomicAdd(A.ctr + 4 + group, 1u);
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev != (unsigned int)gsize - 1) return;
+
+    // ---- this warp completed the group: its tiles in tile order ----
+    __threadfence();
+    if (lane == 0) A.ctr[4 + group] = 0;
+    double gm[NV];
+#pragma unroll
+    for (int m = 0; m < NV; ++m) gm[m] = 0.0;
+    for (int t = lane; t < gsize; t += 32)
+#pragma unroll
+        for (int m = 0; m < NV; ++m) gm[m] += __ldcg(A.tile_mom + (size_t)(group * kGroupTiles + t) * kProjMom + m);
+#pragma unroll
+    for (int m = 0; m < NV; ++m) gm[m] = warp_sum(gm[m]);
+    if (lane == 0) {
+#pragma unroll
+        for (int m = 0; m < NV; ++m) A.group_mom[(size_t)group * kProjMom + m] = gm[m];
+        __threadfence();
+        prev = atomicAdd(A.ctr + 2, 1u);
+    }
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev != (unsigned int)A.ngroups - 1) return;
+
+    // ---- this warp completed the last group: totals in group order, controller ----
+    __threadfence();
+    double tot[NV];
+#pragma unroll
+    for (int m = 0; m < NV; ++m) tot[m] = 0.0;
+    for (int gg = lane; gg < A.ngroups; gg += 32)
+#pragma unroll
+        for (int m = 0; m < NV; ++m) tot[m] += __ldcg(A.group_mom + (size_t)gg * kProjMom + m);
+#pragma unroll
+    for (int m = 0; m < NV; ++m) tot[m] = warp_sum(tot[m]);
+    if (lane == 0) {
+        A.ctr[2] = 0;
+        controller_project<KM>(A.st, tot, A.phase, A.h, A.use_graph);
+    }
+}
+
+template <int NCH>
+__global__ void __launch_bounds__(kSplitThreads, NCH == 4 ? 4 : 2) k_project_split(SplitArgs A) {
+    const RayGeom g = *A.rg;
+    const int lane = threadIdx.x & 31;
+    const unsigned int n_items = (unsigned int)A.ntiles * kParts;
+    unsigned int* tile_ctr = A.ctr + 4 + A.ngroups;
+    constexpr int KM = NCH == 8 ? 7 : 3;
+    constexpr int NV = 3 + 3 * KM;
+
+    float lo[3] = {-1.0f, -1.0f, -1.0f}, hi[3] = {g.nmax[0], g.nmax[1], g.nmax[2]};
+    bool nonzero = true;
+    if (A.sup.sup && A.sup.w) nonzero = support_box(*A.sup.sup, A.vd, A.sup.w, A.sup.K, lo, hi);
+
+    for (;;) {
+        unsigned int item = 0;
+        if (lane == 0) item = atomicAdd(A.ctr, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) break;
+        const int slot = (int)(item / kParts), part = (int)(item - (unsigned int)slot * kParts);
+        int tile = A.order ? __ldg(A.order + slot) : slot;
+        if (tile < 0 || tile >= A.ntiles) tile = slot;  // a permutation never trips this
+        const int iu = (tile % A.ntu) * 8 + (lane & 7), iv = (tile / A.ntu) * 4 + (lane >> 3);
+        const bool valid = iu < A.nu && iv < A.nv;
+
+        float b[3];
+        ray_dir_index(g, valid ? iu : 0, valid ? iv : 0, b);
+        float t0, t1;
+        int s_lo = 0x7fffffff, s_hi = -1;
+        if (valid && nonzero && ray_box(g.a, b, lo, hi, t0, t1)) {
+            s_lo = (int)fminf(fmaxf(ceilf(t0 / g.ds - 0.5f), 0.0f), (float)kMaxSamples);
+            s_hi = (int)fminf(floorf(t1 / g.ds - 0.5f), (float)kMaxSamples);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s_lo = min(s_lo, __shfl_xor_sync(0xffffffffu, s_lo, o));
+            s_hi = max(s_hi, __shfl_xor_sync(0xffffffffu, s_hi, o));
+        }
+        float acc[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) acc[c] = 0.0f;
+        float comp = 0.0f;
+        if (s_hi >= s_lo) {
+            const int L = s_hi - s_lo + 1;
+            const int s_a = s_lo + (L * part) / kParts, s_e = s_lo + (L * (part + 1)) / kParts;
+            if constexpr (NCH == 4) {
+                CellCache4 cache;
+                for (int s = s_a; s < s_e; ++s) {
+                    float q[3];
+                    sample_pos(g, b, s, q);
+                    cache.sample(A.vol, A.vd, q, acc);
+                }
+                comp = cache.comp;
+            } else {
+                for (int s = s_a; s < s_e; ++s) {
+                    float q[3];
+                    sample_pos(g, b, s, q);
+                    accumulate<NCH>(A.vol, A.vd, q, acc, comp);
+                }
+            }
+        }
+        // publish this part, then count it
+        float* dst = A.part + ((size_t)tile * kParts + part) * (NCH + 1) * 32 + lane;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) dst[c * 32] = acc[c];
+        dst[NCH * 32] = comp;
+        __threadfence();
+        __syncwarp();
+        unsigned int prev = 0;
+        if (lane == 0) prev = atomicAdd(tile_ctr + tile, 1u);
+        prev = __shfl_sync(0xffffffffu, prev, 0);
+        if (prev != kParts - 1) continue;
+
+        finish_tile<NCH>(A, tile, iu, iv, valid, g.ds);
+    }
+    // The last warp to leave resets the queue for the next launch (no warp of
+    // this launch reads it again).
+    if (lane == 0) {
+        const unsigned int total = gridDim.x * (blockDim.x >> 5);
+        if (atomicAdd(A.ctr + 1, 1u) == total - 1) {
+            A.ctr[0] = 0;
+            A.ctr[1] = 0;
+        }
+    }
+}
+
 // Cost and gradient at explicit (a, b) (ab_dev[0..1]) for the step-level entry.
 __global__ void __launch_bounds__(kReduceThreads)
 k_cost_grad(const float* __restrict__ p, const float* __restrict__ q, const float* __restrict__ y, int R, int K,
@@ -636,10 +876,62 @@ cudaError_t launch_begin(Launcher& L, const float* y, int R, SolveState* st, dou
     return L(k_begin, dim3(kReduceBlocks), dim3(kReduceThreads), 0, y, R, st, partials, counter);
 }
 
+int split_tiles(int nu, int nv) { return ((nu + 7) / 8) * ((nv + 3) / 4); }
+int split_groups(int nu, int nv) { return (split_tiles(nu, nv) + kGroupTiles - 1) / kGroupTiles; }
+size_t split_part_floats(int nu, int nv, int nch) { return (size_t)split_tiles(nu, nv) * kParts * (nch + 1) * 32; }
+size_t split_counters(int nu, int nv) { return 4 + (size_t)split_groups(nu, nv) + (size_t)split_tiles(nu, nv); }
+
+void project_warp_tile_order(int nu, int nv, int* order) {
+    // 8x4-ray warp tiles sorted by the distance of their centre from the
+    // detector centre (long central rays first); ties by tile index.
+    const int ntu = (nu + 7) / 8, ntv = (nv + 3) / 4, n = ntu * ntv;
+    const double cu = 0.5 * nu, cv = 0.5 * nv;
+    std::vector<std::pair<double, int>> keys((size_t)n);
+    for (int t = 0; t < n; ++t) {
+        double u = ((t % ntu) + 0.5) * 8 - cu, v = ((t / ntu) + 0.5) * 4 - cv;
+        keys[(size_t)t] = {u * u + v * v, t};
+    }
+    std::sort(keys.begin(), keys.end());
+    for (int t = 0; t < n; ++t) order[t] = keys[(size_t)t].second;
+}
+
+namespace {
+// Resident blocks of the split projector on this device (computed once per device).
+int split_grid(int nch) {
+    static int cached[2][64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    int& c = cached[nch == 8 ? 1 : 0][dev];
+    if (c == 0) {
+        int sms = 0, per = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (nch == 8)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_project_split<8>, kSplitThreads, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_project_split<4>, kSplitThreads, 0);
+        c = sms * (per > 0 ? per : 1);
+    }
+    return c;
+}
+}  // namespace
+
 cudaError_t launch_project(Launcher& L, const VolDev& vd, const float* vol_pad, int nch, int K,
                            const RayGeom* rg, const int* order, int nu, int nv, float* p, float* q,
                            const float* y, SolveState* st, double* partials, unsigned int* counter,
-                           int phase, cudaGraphConditionalHandle h, int use_graph, SupportRef sup) {
+                           int phase, cudaGraphConditionalHandle h, int use_graph, SupportRef sup,
+                           const SplitScratch* ss) {
+    if (nch >= 4 && ss && ss->ctr) {
+        const int ntiles = split_tiles(nu, nv), ngroups = split_groups(nu, nv);
+        SplitArgs S{vol_pad, vd, rg, ss->order, nu, nv, K, (nu + 7) / 8, ntiles, ngroups, p, q, y, st,
+                    ss->part, ss->tile_mom, ss->group_mom, ss->ctr, phase, h, use_graph, sup};
+        const int blocks = split_grid(nch);
+        if (blocks <= 0) return cudaErrorInvalidDevice;
+        const int need = (ntiles * kParts + kSplitThreads / 32 - 1) / (kSplitThreads / 32);
+        const dim3 grid((unsigned)(need < blocks ? need : blocks));
+        if (nch == 8) return L(k_project_split<8>, grid, dim3(kSplitThreads), 0, S);
+        if (nch == 4) return L(k_project_split<4>, grid, dim3(kSplitThreads), 0, S);
+        return cudaErrorInvalidValue;
+    }
     const int ntu = (nu + kTileU - 1) / kTileU, ntv = (nv + kTileV - 1) / kTileV;
     ProjArgs A{vol_pad, vd, rg, order, nu, nv, K, ntu, p, q, y, st, partials, counter, phase, h, use_graph, sup};
     dim3 grid(ntu * ntv);

@@ -74,6 +74,8 @@ struct Model {
     RayGeom* rg = nullptr;    // geometry of step-level calls
     int* steps = nullptr;
     int* order = nullptr;           // projector tile order
+    int* order_w = nullptr;         // split projector's warp-tile order
+    SplitScratch ss;                // split projector's scratch (order_w, parts, moments, counters)
     Support* sup = nullptr;         // where the warped volume can be nonzero
     SolveState* st_host = nullptr;  // pinned
     size_t bytes = 0;
@@ -229,7 +231,8 @@ void free_model(Model* m) {
     if (m->exec) cudaGraphExecDestroy(m->exec);
     if (m->graph) cudaGraphDestroy(m->graph);
     void* bufs[] = {m->f0p, m->mean, m->U, m->fh, m->fpad, m->p, m->q, m->y, m->r, m->flat, m->hbuf,
-                    m->partials, m->counter, m->st, m->wdev, m->out, m->rg, m->steps, m->order, m->sup};
+                    m->partials, m->counter, m->st, m->wdev, m->out, m->rg, m->steps, m->order, m->sup,
+                    m->order_w, m->ss.part, m->ss.tile_mom, m->ss.group_mom, m->ss.ctr};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (m->st_host) cudaFreeHost(m->st_host);
@@ -260,7 +263,10 @@ size_t model_bytes(const pr_volume_desc& v, const pr_geometry& g, int K, int sto
     size_t nch = (size_t)fh_channels(K);
     return np * ts + 3 * n * 4 + 3 * (size_t)K * n * ts + np * nch * 4 + np * 4 + R * 4 + R * K * 4 + R * 4 +
            R * 4 + n * 4 + partial_doubles(g, vd) * 8 + 64 + sizeof(SolveState) + 64 + 128 +
-           sizeof(RayGeom) + 16 + (size_t)project_blocks(g.nu, g.nv) * sizeof(int) + sizeof(Support);
+           sizeof(RayGeom) + 16 + (size_t)project_blocks(g.nu, g.nv) * sizeof(int) + sizeof(Support) +
+           (size_t)split_tiles(g.nu, g.nv) * sizeof(int) + split_part_floats(g.nu, g.nv, (int)nch) * 4 +
+           ((size_t)split_tiles(g.nu, g.nv) + split_groups(g.nu, g.nv)) * kProjMom * 8 +
+           split_counters(g.nu, g.nv) * 4;
 }
 
 int write_params(pr_ctx* c, Model* m, double angle, const pr_solve_opts* o, cudaStream_t stream) {
@@ -312,7 +318,7 @@ int build_graph(pr_ctx* c, Model* m) {
     CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
     CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
-                      m->partials, m->counter, kPhaseInit, m->hloop, 1, SupportRef{m->sup, st->wt, m->K}));
+                      m->partials, m->counter, kPhaseInit, m->hloop, 1, SupportRef{m->sup, st->wt, m->K}, &m->ss));
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = m->hloop;
@@ -324,7 +330,7 @@ int build_graph(pr_ctx* c, Model* m) {
     B.graph = cp.conditional.phGraph_out[0];
     CK(launch_warp(B, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
     CK(launch_project(B, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
-                      m->partials, m->counter, kPhaseTrial, m->hloop, 1, SupportRef{m->sup, st->wt, m->K}));
+                      m->partials, m->counter, kPhaseTrial, m->hloop, 1, SupportRef{m->sup, st->wt, m->K}, &m->ss));
     L.last = cond;
     CK(launch_tumor(L, m->md, st->w, 0.0, 0, &st->prm, st->tumor, &st->tumor_steps));
     CK(cudaGraphInstantiate(&m->exec, m->graph, 0));
@@ -340,7 +346,7 @@ int host_loop(pr_ctx* c, Model* m, int opt_max_iters, int opt_max_bt) {
     CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
     CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
-                      m->partials, m->counter, kPhaseInit, 0, 0, SupportRef{m->sup, st->wt, m->K}));
+                      m->partials, m->counter, kPhaseInit, 0, 0, SupportRef{m->sup, st->wt, m->K}, &m->ss));
     long long guard = 0, bound = (long long)(opt_max_iters + 1) * (opt_max_bt + 1) + 2;
     for (;;) {
         CK(cudaMemcpyAsync(&m->st_host->running, &st->running, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -349,7 +355,7 @@ int host_loop(pr_ctx* c, Model* m, int opt_max_iters, int opt_max_bt) {
         if (++guard > bound) return fail(PR_ETIMEOUT, "host loop exceeded its trial bound");
         CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
         CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y,
-                          st, m->partials, m->counter, kPhaseTrial, 0, 0, SupportRef{m->sup, st->wt, m->K}));
+                          st, m->partials, m->counter, kPhaseTrial, 0, 0, SupportRef{m->sup, st->wt, m->K}, &m->ss));
         }
     CK(launch_tumor(L, m->md, st->w, 0.0, 0, &st->prm, st->tumor, &st->tumor_steps));
     return PR_OK;
@@ -673,6 +679,12 @@ int pr_load_model(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
     A(&m->steps, 16);
     A(&m->order, (size_t)project_blocks(geom->nu, geom->nv) * sizeof(int));
     A(&m->sup, sizeof(Support));
+    A(&m->order_w, (size_t)split_tiles(geom->nu, geom->nv) * sizeof(int));
+    A(&m->ss.part, split_part_floats(geom->nu, geom->nv, m->nch) * 4);
+    A(&m->ss.tile_mom, (size_t)split_tiles(geom->nu, geom->nv) * kProjMom * 8);
+    A(&m->ss.group_mom, (size_t)split_groups(geom->nu, geom->nv) * kProjMom * 8);
+    A(&m->ss.ctr, split_counters(geom->nu, geom->nv) * 4);
+    m->ss.order = m->order_w;
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&m->st_host, sizeof(SolveState), cudaHostAllocDefault);
     if (e != cudaSuccess) {
         free_model(m);
@@ -691,6 +703,7 @@ int pr_load_model(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
     cudaMemcpyKind kind = location == PR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     cudaStream_t s = c->stream;
     std::vector<int> order_host((size_t)project_blocks(geom->nu, geom->nv));  // lives until the sync below
+    std::vector<int> order_w_host((size_t)split_tiles(geom->nu, geom->nv));
     do {
         if ((e = cudaMemsetAsync(m->f0p, 0, np * ts, s))) break;
         if ((e = cudaMemsetAsync(m->fh, 0, np * m->nch * 4, s))) break;
@@ -699,6 +712,11 @@ int pr_load_model(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
         if ((e = cudaMemsetAsync(m->counter, 0, 64, s))) break;
         if ((e = cudaMemsetAsync(m->st, 0, sizeof(SolveState), s))) break;
         if ((e = cudaMemcpyAsync(m->mean, mean_dvf, 3 * n * 4, kind, s))) break;
+        if ((e = cudaMemsetAsync(m->ss.ctr, 0, split_counters(geom->nu, geom->nv) * 4, s))) break;
+        project_warp_tile_order(geom->nu, geom->nv, order_w_host.data());
+        if ((e = cudaMemcpyAsync(m->order_w, order_w_host.data(), order_w_host.size() * sizeof(int),
+                                 cudaMemcpyHostToDevice, s)))
+            break;
         project_tile_order(geom->nu, geom->nv, order_host.data());
         if ((e = cudaMemcpyAsync(m->order, order_host.data(), order_host.size() * sizeof(int),
                                  cudaMemcpyHostToDevice, s)))
@@ -927,7 +945,7 @@ int pr_cost_grad(pr_ctx* c, int id, const float* y_dev, double angle, const doub
     if (mode == 0) {
         CK(launch_warp(L, m->md, m->wdev, kWarpFH, m->fh, nullptr, nullptr));
         CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, m->order, nu, nv, m->p, m->q, nullptr, nullptr, nullptr,
-                          nullptr, kPhaseNone, 0, 0, SupportRef{m->sup, m->wdev, m->K}));
+                          nullptr, kPhaseNone, 0, 0, SupportRef{m->sup, m->wdev, m->K}, &m->ss));
         CK(launch_cost_grad(L, m->p, m->q, y_dev, m->R, m->K, m->out + 8, m->partials, m->counter, m->out));
         CK(cudaMemcpyAsync(res, m->out, sizeof(double) * (1 + m->K), cudaMemcpyDeviceToHost, c->stream));
     } else {
@@ -1007,7 +1025,7 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
     CK(launch_warp(L, m->md, m->st->w, kWarpFPad, m->fpad, nullptr, nullptr));
     if (which == PR_KERNEL_BACKPROJECT) CK(launch_warp(L, m->md, m->st->w, kWarpFlatFH, nullptr, nullptr, m->hbuf));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, m->order, nu, nv, m->p, m->q, nullptr, nullptr, nullptr, nullptr,
-                      kPhaseNone, 0, 0, SupportRef{m->sup, m->st->w, m->K}));
+                      kPhaseNone, 0, 0, SupportRef{m->sup, m->st->w, m->K}, &m->ss));
     float* ytmp = nullptr;  // output of the timed inversion (3N floats, freed below)
     if (which == PR_KERNEL_INVERT) CK(cudaMalloc(&ytmp, (size_t)3 * m->md.vd.n * sizeof(float)));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1019,7 +1037,7 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
             case PR_KERNEL_WARP_FH: err = launch_warp(L, m->md, m->st->w, kWarpFH, m->fh, nullptr, nullptr); break;
             case PR_KERNEL_PROJECT_FH:
                 err = launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, m->order, nu, nv, m->p, m->q, nullptr, nullptr,
-                                     nullptr, nullptr, kPhaseNone, 0, 0, SupportRef{m->sup, m->st->w, m->K});
+                                     nullptr, nullptr, kPhaseNone, 0, 0, SupportRef{m->sup, m->st->w, m->K}, &m->ss);
                 break;
             case PR_KERNEL_REGRAD:
                 err = launch_cost_grad(L, m->p, m->q, m->p, m->R, m->K, m->out + 8, m->partials, m->counter, m->out);
