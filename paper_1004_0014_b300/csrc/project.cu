@@ -496,17 +496,17 @@ __global__ void __launch_bounds__(kProjThreads, NCH == 4 ? 4 : 1) k_project(Proj
 // The 4/8-channel pass has 1.3 rays per resident thread at paper scale, and
 // its run time was the time of the longest 32x8 tile: the last wave left SMs
 // idle and blocks held their slots while waiting for their slowest warp. Here
-// the unit of work is one third of the sample range of an 8x4-ray warp tile.
+// the unit of work is a quarter of the sample range of an 8x4-ray warp tile.
 // Warps take items from a global counter, longest tiles first (the parts of
 // a tile one after another), so the busy time evens out at the scale of a
-// third of a ray. Each part's sums go to scratch; the warp that finishes a
+// quarter of a ray. Each part's sums go to scratch; the warp that finishes a
 // tile's last part adds the parts in a fixed order, writes p and q and the
 // tile's moments; fixed groups of 64 tiles and then the groups are summed in
 // tile order by whichever warp completes them, and the warp that completes
 // the last group runs the controller. Every sum is taken in an order fixed
 // by tile and part index, never by timing, so results are deterministic.
 // No warp ever waits for another.
-constexpr int kParts = 3;        // sample-range parts per warp tile
+constexpr int kParts = 4;        // sample-range parts per warp tile
 constexpr int kGroupTiles = 64;  // tiles per fixed-order moment group
 constexpr int kSplitThreads = 256;
 
