@@ -109,6 +109,8 @@ struct ServeSlot {
     cudaStream_t stream = nullptr;
     cudaEvent_t start = nullptr, done = nullptr;
     SolveState* host_state = nullptr;  // pinned
+    float* y_pinned = nullptr;         // pinned staging of the frame's y (y_cap floats)
+    size_t y_cap = 0;
     bool busy = false;
     ServeRequest req;
     std::chrono::steady_clock::time_point t_dispatch;
@@ -489,18 +491,38 @@ void serve_loop(pr_ctx* c) {
             sl.req = std::move(*it);
             sv->pending.erase(it);
             sl.t_dispatch = std::chrono::steady_clock::now();
+            // The slot and the patient are claimed; the CUDA calls run without the
+            // lock so that submitters and pollers are never held behind them (the
+            // model cannot be released while it has a frame in flight).
+            sl.busy = true;
+            sv->in_flight.insert(sl.req.model);
+            lock.unlock();
             cudaError_t e = cudaSuccess;
             if (!m) {
                 e = cudaErrorInvalidValue;
             } else {
-                e = cudaEventRecord(sl.start, sl.stream);
-                if (!e) e = cudaMemcpyAsync(m->y, sl.req.y.data(), (size_t)m->R * 4, cudaMemcpyHostToDevice, sl.stream);
+                const size_t R = (size_t)m->R;
+                if (sl.y_cap < R) {
+                    if (sl.y_pinned) cudaFreeHost(sl.y_pinned);
+                    sl.y_pinned = nullptr;
+                    sl.y_cap = 0;
+                    e = cudaHostAlloc((void**)&sl.y_pinned, R * 4, cudaHostAllocDefault);
+                    if (!e) sl.y_cap = R;
+                }
+                if (!e) {
+                    memcpy(sl.y_pinned, sl.req.y.data(), R * 4);
+                    e = cudaEventRecord(sl.start, sl.stream);
+                }
+                if (!e) e = cudaMemcpyAsync(m->y, sl.y_pinned, R * 4, cudaMemcpyHostToDevice, sl.stream);
                 if (!e && write_params(c, m, sl.req.angle, &sl.req.opts, sl.stream) != PR_OK) e = cudaErrorUnknown;
                 if (!e) e = cudaGraphLaunch(m->exec, sl.stream);
                 if (!e) e = cudaMemcpyAsync(sl.host_state, m->st, sizeof(SolveState), cudaMemcpyDeviceToHost, sl.stream);
                 if (!e) e = cudaEventRecord(sl.done, sl.stream);
             }
+            lock.lock();
             if (e) {
+                sl.busy = false;
+                sv->in_flight.erase(sl.req.model);
                 sv->error = PR_ECUDA;
                 sv->error_msg = std::string("dispatch failed: ") + cudaGetErrorString(e);
                 pr_served out;
@@ -512,8 +534,8 @@ void serve_loop(pr_ctx* c) {
                 sv->cv_done.notify_all();
                 continue;
             }
-            sv->in_flight.insert(sl.req.model);
-            sl.busy = true;
+            sl.req.y.clear();
+            sl.req.y.shrink_to_fit();
             busy = true;
             progressed = true;
         }
@@ -549,6 +571,7 @@ void serve_free(pr_ctx* c) {
         if (sl.done) cudaEventDestroy(sl.done);
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.host_state) cudaFreeHost(sl.host_state);
+        if (sl.y_pinned) cudaFreeHost(sl.y_pinned);
     }
     delete c->serve;
     c->serve = nullptr;
