@@ -43,7 +43,7 @@ if ROOT not in sys.path:
 
 METRIC = "reconstructions/s and p50/p99 ms per projection (256²×120, K=3) vs plain FP32 path"
 UNIT = "reconstructions/s"
-WORKLOAD = "paper-scale plain method, FP32: 256x256x120 @ 2x2x2.5 mm, K=3, %s detector, 10 iterations"
+WORKLOAD = "paper-scale plain method, %s storage: 256x256x120 @ 2x2x2.5 mm, K=%d, %s detector, 10 iterations"
 # Trials and accepted steps per reconstruction of this library's solver on this
 # workload (measured on the GPU arm); used only to scale the oracle's per-step
 # sample to a whole reconstruction in the reference arm.
@@ -171,10 +171,10 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 
 
-def build_model_inputs(detector: str = "512x384"):
+def build_model_inputs(detector: str = "512x384", K: int = 3):
     from phantom import build_pca, phantom_volume, training_dvfs, tumor_centre, workload_paper
 
-    w = workload_paper(detector=detector)
+    w = workload_paper(K=K, detector=detector)
     vol = w["vol"]
     f0 = phantom_volume(vol).astype(np.float32)
     pca = build_pca(training_dvfs(vol), w["K"])
@@ -332,7 +332,7 @@ def run_reference(args):
     from oracle import oracle as O
     from phantom import Geometry, dvf_analytic
 
-    w, f0, mean, U, c0 = build_model_inputs(args.detector)
+    w, f0, mean, U, c0 = build_model_inputs(args.detector, args.K)
     vol, geom = w["vol"], w["geom"]
     O.build_oracle()
     m_f0 = f0.astype(np.float64)
@@ -361,7 +361,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sec,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic phantom (seeded)",
-        "config": {"workload": WORKLOAD % args.detector, "frames": "j = 0..; angle j deg, t = j/6 s"},
+        "config": {"workload": WORKLOAD % (args.storage, args.K, args.detector), "frames": "j = 0..; angle j deg, t = j/6 s"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "per step: the FP64 oracle's warp of frame j and its projection of the "
                                    "central %d of %d detector rows (scaled by rows); a reconstruction = "
@@ -385,10 +385,13 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dist = dist_init(world)
 
-    w, f0, mean, U, c0 = build_model_inputs(args.detector)
+    from paper_1004_0014_b300 import PR_BF16, PR_F32
+
+    w, f0, mean, U, c0 = build_model_inputs(args.detector, args.K)
     vol, geom = w["vol"], w["geom"]
     ctx = Context(local)
-    mid = ctx.load_model(vol, geom, f0, mean, U, c0)
+    bf16 = args.storage == "bf16"
+    mid = ctx.load_model(vol, geom, f0, mean, U, c0, storage=PR_BF16 if bf16 else PR_F32)
     W, K = args.warmup, args.steps
     frames = list(range(W + K))
     ys = make_targets(ctx, w, f0, frames)
@@ -483,24 +486,25 @@ def run_ours(args):
     bytes_proj = N * 4 * nch + R * 4 * (1 + Km)
     roofline = {"kernel": "k_project<%d> (f, h_1..h_%d)" % (nch, Km), "bound": "alu", "achieved": proj_tflops,
                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": proj_tflops / fp32_peak,
-                "traffic": recorded_traffic("k_project<4>", "project.cu"),
+                "traffic": recorded_traffic("k_project<4>", "project.cu") if (Km == 3 and not bf16) else None,
                 "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (FMA peak)" % sm_mhz,
                 "samples_per_launch": samples, "flops_per_sample": flops_per_sample(nch),
                 "algorithmic_flops_per_launch": flops, "share_of_solve": share_proj,
                 "algorithmic_bytes_per_launch": bytes_proj,
                 "achieved_gbs": bytes_proj / (kern["project_fh"] / 1000.0) / 1e9}
-    bytes_warp = N * (12 + 12 * Km + 4 + 4 * nch)
+    ts = 2 if bf16 else 4  # bytes per stored value of f0 and U
+    bytes_warp = N * (12 + 3 * ts * Km + ts + 4 * nch)
     warp_gbs = bytes_warp / (kern["warp_fh"] / 1000.0) / 1e9
-    roofline_warp = {"kernel": "k_warp<%d, f+h, float>" % Km, "bound": "hbm", "achieved": warp_gbs,
-                     "peak": hbm_peak, "unit": "GB/s", "frac": warp_gbs / hbm_peak,
-                     "traffic": recorded_traffic("k_warp<3,FH,float>", "warp.cu"),
+    roofline_warp = {"kernel": "k_warp<%d, f+h, %s>" % (Km, "bf16" if bf16 else "float"), "bound": "hbm",
+                     "achieved": warp_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": warp_gbs / hbm_peak,
+                     "traffic": recorded_traffic("k_warp<3,FH,float>", "warp.cu") if (Km == 3 and not bf16) else None,
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if peaks else "fallback",
                      "algorithmic_bytes_per_launch": bytes_warp, "share_of_solve": share_warp}
 
     # Whole-grid DVF inversion (Section 2.3 with ref. 13), outside the solve:
     # x/dx synthesis (12 + 12K bytes read, 16 written per voxel), then the
     # per-voxel fixed point (the 16-byte field read once, 12 bytes of y written).
-    bytes_inv = N * (12 + 12 * Km + 16 + 16 + 12)
+    bytes_inv = N * (12 + 3 * ts * Km + 16 + 16 + 12)
     inv_gbs = bytes_inv / (kern["invert_dvf"] / 1000.0) / 1e9
     roofline_invert = {"kernels": "k_dvf_idx + k_invert", "bound": "hbm", "achieved": inv_gbs, "peak": hbm_peak,
                        "unit": "GB/s", "frac": inv_gbs / hbm_peak, "algorithmic_bytes_per_call": bytes_inv,
@@ -524,14 +528,15 @@ def run_ours(args):
             "ms_per_step": max_ms / K, "p50_ms": float(q[0]), "p99_ms": float(q[1]),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic phantom (seeded), measured projections synthesised on the device",
-            "config": {"workload": WORKLOAD % args.detector, "volume": [vol.nx, vol.ny, vol.nz],
+            "config": {"workload": WORKLOAD % (args.storage, Km, args.detector), "volume": [vol.nx, vol.ny, vol.nz],
                        "spacing_mm": [vol.dx, vol.dy, vol.dz], "K": Km, "detector": [geom.nu, geom.nv],
                        "pixel_mm": geom.du, "ray_step_mm": geom.ds, "iterations": w["max_iters"],
                        "frames": "j = %d..%d: angle j deg, t = j/6 s, 1%% noise seed j, warm start from j-1"
                                  % (W, W + K - 1),
-                       "storage": "float32", "loop": "on-device (CUDA graph, conditional WHILE)",
+                       "storage": "bfloat16 f0 and U, float32 mean" if bf16 else "float32",
+                       "loop": "on-device (CUDA graph, conditional WHILE)",
                        "l2": "inputs larger than L2: %d MB of DVF fields streamed per warp pass"
-                             % ((12 + 12 * Km) * N // 2**20),
+                             % ((12 + 3 * ts * Km) * N // 2**20),
                        "parallelism": "independent patient streams, one per GPU" if world > 1 else "1 GPU"},
             "plain_fp32": {"value": plain_value, "unit": UNIT, "p50_ms": float(np.percentile(plain, 50)),
                            "p99_ms": float(np.percentile(plain, 99)),
@@ -783,6 +788,8 @@ def main():
     ap.add_argument("--adjoint", action="store_true", help="also time the gather-adjoint gradient kernel")
     ap.add_argument("--detector", default="512x384", choices=["512x384", "200x150", "1000x750"],
                     help="detector sampling of the 40x30 cm panel")
+    ap.add_argument("--K", type=int, default=3, choices=range(1, 8), help="PCA modes of the paper-scale model")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16"], help="storage of f0 and U")
     ap.add_argument("--serve", action="store_true", help="serving arm: patients streaming Poisson frames")
     ap.add_argument("--patients", type=int, default=16)
     ap.add_argument("--rate", type=float, default=15.0, help="frames per second per patient (--serve)")

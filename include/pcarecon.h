@@ -295,6 +295,17 @@ int pr_cost_grad(pr_ctx* ctx, int model_id, const float* y_dev, double angle_rad
 int pr_tumor(pr_ctx* ctx, int model_id, const double* w, double tol, int max_iter, double* xyz,
              int* steps);
 
+/* The line-search choices of the model's last solve, one byte per trial (no
+ * counterpart in the paper; for checking a solve against a reference that
+ * may break a rounding tie the other way): bit 7 the trial was accepted,
+ * bit 6 it ended the solve (a rejected trial whose predicted decrease was
+ * unresolvable, or an accepted one after which the gradient test was met),
+ * bits 0-5 e + 32 with 2^e the factor that scaled the step next (0 when
+ * step_model is 0). Copies min(trials, cap, 1024) bytes to out (host) and
+ * sets *n to the number of trials. Synchronous. Errors: PR_EINVAL,
+ * PR_ENOMODEL, PR_ECUDA. */
+int pr_trial_log(pr_ctx* ctx, int model_id, unsigned char* out, int cap, int* n);
+
 /* Section 2.3 with ref. 13 over the whole grid: the push-forward DVF y, the
  * inverse of the model's pull-back field x = mean + U w (w: K doubles, host),
  * i.e. u + y(u) + x(u + y(u)) = u at every voxel centre u, x interpolated

@@ -318,13 +318,25 @@ class SolveResult:
     tumor_steps: int
     mu: float  # first trial step of the next warm-started frame (0 = none)
     history: list  # per accepted step: dict(J_after_step1, J_after_step2, mu, w)
+    log: list = dataclasses.field(default_factory=list)    # per trial: (accepted, stop, e), see reconstruct
+    trace: list = dataclasses.field(default_factory=list)  # per trial: the FP64 quantities behind each choice
 
 
 def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None,
-                mu_next: float | None = None) -> SolveResult:
+                mu_next: float | None = None, replay: list | None = None) -> SolveResult:
     """Section 2.2: alternate step 1 (Eq. 3, gradient step with Armijo's rule at
     fixed a, b) and step 2 (Eq. 4, exact a, b at fixed w), then Section 2.3.
-    mu_next: the previous frame's next trial step (None or 0 = cold)."""
+    mu_next: the previous frame's next trial step (None or 0 = cold).
+
+    Every line-search trial makes three floating-point choices, logged as
+    (accepted, stop, e): the Armijo test; a stop (a rejected trial whose
+    predicted decrease is unresolvable, or an accepted step after which the
+    gradient test is met); and e, the power-of-two exponent of the factor that
+    scales mu next (the backtrack after a rejection, the next first trial after
+    an acceptance; 0 with step_model 0, whose factors are fixed). With
+    `replay` (such a log, e.g. the CUDA path's), trial i takes the logged
+    choices instead of its own; `trace` keeps, per trial, the FP64 quantities
+    from which its own choices follow, so a test can tell a tie from an error."""
     o = opts or SolveOptions()
     y = np.asarray(y, dtype=np.float64)
     w = np.array(w0, dtype=np.float64)
@@ -336,9 +348,11 @@ def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None,
     backtracks = 0
     stop = STOP_MAX_ITERS
     history = []
+    log, trace = [], []
+    grad_stop = False
     while True:
         gn = float(np.linalg.norm(g))
-        if gn <= o.grad_tol * g0 or gn == 0.0:
+        if grad_stop or (not log and (gn <= o.grad_tol * g0 or gn == 0.0)):
             stop = STOP_GRAD_TOL
             break
         if n >= o.max_iters:
@@ -353,21 +367,49 @@ def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None,
             J_t = cost(trial.p, y, a, b)
             # curvature of J along -g from this trial: J(mu) ~ J - mu |g|^2 + (curv/2) mu^2;
             # used only where the step's predicted decrease is resolvable in J
-            curv = 2.0 * (J_t - J + mu * gn * gn) / (mu * mu)
-            if not (mu * gn * gn > MODEL_MIN_DECREASE * abs(J)):
-                curv = 0.0
-            if J_t <= J - o.c1 * mu * gn * gn:
+            curv_raw = 2.0 * (J_t - J + mu * gn * gn) / (mu * mu)
+            model_ok = mu * gn * gn > MODEL_MIN_DECREASE * abs(J)
+            curv = curv_raw if model_ok else 0.0
+            ok = J_t <= J - o.c1 * mu * gn * gn
+            # this trial's own choices (see the docstring)
+            if ok:
+                if o.step_model == 1:
+                    ratio = min(o.step_growth, gn * gn / curv / mu) if curv > 0 else o.step_growth
+                    factor = pow2_floor(max(ratio, 0.5))
+                else:
+                    factor = o.step_growth if bt == 0 else o.step_growth_bt
+                own = (True, False, _exp2(factor) if o.step_model == 1 else 0)
+            elif o.step_model == 1 and not model_ok:
+                factor = 1.0
+                own = (False, True, 0)
+            else:
+                if o.step_model == 1:  # quadratic model's minimiser, as a power-of-two fraction of mu
+                    ratio = min(o.beta, max(1.0 / 16.0, gn * gn / curv / mu)) if curv > 0 else o.beta
+                    factor = pow2_floor(ratio)
+                else:
+                    factor = o.beta
+                own = (False, False, _exp2(factor) if o.step_model == 1 else 0)
+            trace.append(dict(J=J, J_t=J_t, mu=mu, gn2=gn * gn, curv=curv_raw, model_ok=model_ok, bt=bt,
+                              own=own, margin=J_t - (J - o.c1 * mu * gn * gn)))
+            choice = own
+            if replay is not None and len(log) < len(replay):
+                choice = tuple(replay[len(log)])
+                if choice[0] != own[0] or choice[2] != own[2]:
+                    if o.step_model == 1:
+                        factor = 2.0 ** choice[2]
+                    elif choice[0]:
+                        factor = o.step_growth if bt == 0 else o.step_growth_bt
+                    else:
+                        factor = o.beta
+            log.append(choice)
+            if choice[0]:
                 accepted = trial
                 break
             backtracks += 1
-            if o.step_model == 1 and not (mu * gn * gn > MODEL_MIN_DECREASE * abs(J)):
+            if choice[1]:
                 resolved = True  # no step along -g changes J by a resolvable amount
                 break
-            if o.step_model == 1:  # quadratic model's minimiser, as a power-of-two fraction of mu
-                ratio = min(o.beta, max(1.0 / 16.0, gn * gn / curv / mu)) if curv > 0 else o.beta
-                mu *= pow2_floor(ratio)
-            else:
-                mu *= o.beta
+            mu *= factor
         if resolved:
             stop = STOP_RESOLVED
             mu_next = mu
@@ -376,17 +418,30 @@ def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None,
             stop = STOP_LINESEARCH_FAILED
             mu_next = 0.0
             break
-        if o.step_model == 1:
-            ratio = min(o.step_growth, gn * gn / curv / mu) if curv > 0 else o.step_growth
-            mu_next = mu * pow2_floor(max(ratio, 0.5))
-        else:
-            mu_next = (o.step_growth if bt == 0 else o.step_growth_bt) * mu
+        mu_next = mu * factor
         w = accepted.w
         # Step 2: (a, b) by Eq. 4 at the new w.
         a, b = fit_ab(accepted.p, y)
         g, J, _ = gradient(model, geom, angle, w, a, b, y)
         history.append(dict(J_step1=J_t, J_step2=J, mu=mu, w=w.copy()))
         n += 1
+        # the gradient test after this step is the accepted trial's stop choice
+        gn_new = float(np.linalg.norm(g))
+        own_stop = gn_new <= o.grad_tol * g0 or gn_new == 0.0
+        trace[-1]["gn_after"] = gn_new
+        trace[-1]["g0"] = g0
+        trace[-1]["own_grad_stop"] = own_stop
+        if replay is not None and len(log) <= len(replay):
+            grad_stop = bool(log[-1][1])
+        else:
+            grad_stop = own_stop
+            log[-1] = (True, own_stop, log[-1][2])
     p_t, steps = tumor(model.vol, model.mean, model.U, w, model.c0, o.tumor_tol, o.tumor_max_iter)
     return SolveResult(w=w, a=a, b=b, J=J, grad=g, iters=n, backtracks=backtracks, stop_reason=stop,
-                       tumor=p_t, tumor_steps=steps, mu=mu_next or 0.0, history=history)
+                       tumor=p_t, tumor_steps=steps, mu=mu_next or 0.0, history=history, log=log, trace=trace)
+
+
+def _exp2(factor: float) -> int:
+    """Exponent e of a power of two factor = 2^e."""
+    m, e = math.frexp(factor)
+    return e - 1

@@ -160,6 +160,10 @@ class Context:
     def tumor(self, mid: int, w, tol: float = 1e-6, max_iter: int = 100):
         return capi.pr_tumor(self._ctx, mid, w, tol, max_iter)
 
+    def trial_log(self, mid: int):
+        """The last solve's line-search choices: (accepted, stop, e) per trial."""
+        return capi.pr_trial_log(self._ctx, mid)
+
     def invert_dvf(self, mid: int, w, tol: float = 1e-5, max_iter: int = 64):
         """Push-forward DVF (3, nz, ny, nx) float32 mm on the device, the largest
         per-voxel step count and the number of voxels not converged to tol."""

@@ -41,7 +41,8 @@ EXPORTED = [
     "pr_version", "pr_last_error", "pr_default_opts", "pr_create", "pr_destroy", "pr_load_model",
     "pr_release_model", "pr_model_footprint", "pr_reconstruct", "pr_reconstruct_async",
     "pr_fetch_result", "pr_get_state", "pr_set_state", "pr_warp", "pr_project", "pr_backproject",
-    "pr_forward", "pr_vjp", "pr_cost_grad", "pr_tumor", "pr_invert_dvf", "pr_time_kernel", "pr_model_stats",
+    "pr_forward", "pr_vjp", "pr_cost_grad", "pr_tumor", "pr_invert_dvf", "pr_trial_log", "pr_time_kernel",
+    "pr_model_stats",
     "pr_io_bytes", "pr_cost_grad_static", "pr_serve_start", "pr_submit", "pr_poll", "pr_serve_stop",
 ]
 
@@ -150,6 +151,7 @@ def load_library(path: str | None = None):
         "pr_cost_grad": (_I, [_P, _I, _P, _D, _DP, _D, _D, _I, _DP, _DP, _P]),
         "pr_tumor": (_I, [_P, _I, _DP, _D, _I, _DP, ctypes.POINTER(_I)]),
         "pr_invert_dvf": (_I, [_P, _I, _DP, _D, _I, _P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_longlong)]),
+        "pr_trial_log": (_I, [_P, _I, _P, _I, ctypes.POINTER(_I)]),
         "pr_time_kernel": (_I, [_P, _I, _I, _D, _I, _DP]),
         "pr_model_stats": (_I, [_P, _I, ctypes.POINTER(Stats)]),
         "pr_io_bytes": (_I, [_P, _I, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
@@ -361,6 +363,14 @@ def pr_invert_dvf(ctx, model_id: int, w, y_dev, tol: float = 1e-5, max_iter: int
     _check(_lib.pr_invert_dvf(ctx, int(model_id), pw, float(tol), int(max_iter), _dev(y_dev, "y_dev"),
                               ctypes.byref(steps), ctypes.byref(open_)))
     return steps.value, open_.value
+
+
+def pr_trial_log(ctx, model_id: int):
+    """The last solve's trial choices as a list of (accepted, stop, e)."""
+    buf = (ctypes.c_ubyte * 1024)()
+    n = ctypes.c_int()
+    _check(_lib.pr_trial_log(ctx, int(model_id), ctypes.cast(buf, _P), 1024, ctypes.byref(n)))
+    return [(bool(b & 0x80), bool(b & 0x40), (b & 0x3F) - 32) for b in buf[:min(n.value, 1024)]]
 
 
 def pr_time_kernel(ctx, model_id: int, which: int, angle_rad: float, iters: int) -> float:

@@ -103,7 +103,8 @@ struct SolveParams {
     int warm_step;   // 1: a warm start also takes the state's next step
     int predict;     // 1: a warm start extrapolates w linearly from the last two solves
     int step_model;  // 1: curvature-informed first trial and quadratic backtracking
-    int pad2_;
+    int tlog_cap;    // bytes of tlog
+    unsigned char* tlog;  // per-trial choices of this solve (nullable), see log_trial
 };
 
 // On-device state of one solve (FP64 scalars; Section 2.2's alternation).

@@ -25,8 +25,11 @@ enum WarpMode : int {
     kWarpFlatFH = 3,  // f [N] (nullable) and h [K][N] (nullable), unpadded
 };
 
-// Channels per voxel of the interleaved solver volume: f, h_1..h_K, rounded up to 4 or 8.
-inline int fh_channels(int K) { return K <= 3 ? 4 : 8; }
+// Channels per voxel of the solver volume: f, h_1..h_K, rounded up to 4, 6 or 8.
+// 4 and 8: interleaved float4 per voxel (one or two). 6 (K = 4, 5): a float4
+// array of (f, h_1, h_2, h_3) over the padded grid, then a float2 array of
+// (h_4, h_5), so that every corner is one 16-byte and one 8-byte aligned load.
+inline int fh_channels(int K) { return K <= 3 ? 4 : (K <= 5 ? 6 : 8); }
 
 // G1: x = mean + U w (Eq. 1), f(v) = F0(v + x(v)), h_k(v) (Section 2.2).
 // w_dev: K doubles in device memory.

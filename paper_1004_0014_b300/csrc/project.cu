@@ -180,6 +180,49 @@ struct CellCache4 {
     float comp = 0.0f;  // running compensation of acc[0]
 };
 
+// The same for the 6-channel volume (K = 4, 5): a float4 and a float2 per
+// corner, 48 registers of corners.
+struct CellCache6 {
+    int base = -1;
+    float c[8][6];  // corners: index = dx + 2 dy + 4 dz
+
+    __device__ __forceinline__ void sample(const float* __restrict__ vol, const VolDev& vd, const float q[3],
+                                           float (&acc)[6]) {
+        float tx, ty, tz;
+        int ix = cell(q[0], vd.nx, tx), iy = cell(q[1], vd.ny, ty), iz = cell(q[2], vd.nz, tz);
+        int b = ((iz + 1) * vd.nyp + (iy + 1)) * vd.nxp + (ix + 1);
+        if (b != base) {
+            base = b;
+            const int plane = vd.nxp * vd.nyp;
+            const int off[4] = {0, vd.nxp, plane, plane + vd.nxp};
+            const float4* v4 = reinterpret_cast<const float4*>(vol);
+            const float2* v2 = reinterpret_cast<const float2*>(vol + 4 * vd.np);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float4 a0 = __ldg(v4 + b + off[k]), a1 = __ldg(v4 + b + off[k] + 1);
+                float2 e0 = __ldg(v2 + b + off[k]), e1 = __ldg(v2 + b + off[k] + 1);
+                c[2 * k][0] = a0.x, c[2 * k][1] = a0.y, c[2 * k][2] = a0.z, c[2 * k][3] = a0.w;
+                c[2 * k][4] = e0.x, c[2 * k][5] = e0.y;
+                c[2 * k + 1][0] = a1.x, c[2 * k + 1][1] = a1.y, c[2 * k + 1][2] = a1.z, c[2 * k + 1][3] = a1.w;
+                c[2 * k + 1][4] = e1.x, c[2 * k + 1][5] = e1.y;
+            }
+        }
+        float wy0 = 1.0f - ty, wz0 = 1.0f - tz;
+        const float wyz[4] = {wy0 * wz0, ty * wz0, wy0 * tz, ty * tz};
+        float s0 = 0.0f;  // this sample's f value, added to the ray sum with compensation
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float w0 = wyz[k] * (1.0f - tx), w1 = wyz[k] * tx;
+            s0 = __fmaf_rn(w1, c[2 * k + 1][0], __fmaf_rn(w0, c[2 * k][0], s0));
+#pragma unroll
+            for (int ch = 1; ch < 6; ++ch)
+                acc[ch] = __fmaf_rn(w1, c[2 * k + 1][ch], __fmaf_rn(w0, c[2 * k][ch], acc[ch]));
+        }
+        kahan_add(acc[0], comp, s0);
+    }
+    float comp = 0.0f;  // running compensation of acc[0]
+};
+
 template <int NCH>
 __device__ __forceinline__ void accumulate(const float* __restrict__ vol, const VolDev& vd, const float q[3],
                                            float (&acc)[NCH], float& comp) {
@@ -256,6 +299,18 @@ __device__ double cost_at(const SolveState* st, const double* m, double a, doubl
 // Cost and gradient at the state's (a, b) from the moments, then the stopping
 // rule (Section 2.2) and, if the solve goes on, the first trial of the next
 // step. Thread 0 of the last block.
+// The floating-point choices of line-search trial st->trials (1-based), one
+// byte: bit 7 accepted, bit 6 stop (a rejected trial: the predicted decrease
+// was unresolvable; an accepted one: the gradient test was met after it),
+// bits 0-5 e + 32, where 2^e is the factor that scales mu next (0 when the
+// factors are fixed, step_model 0). Kept so that a checker can follow the
+// same path in FP64 and tell a rounding tie from a wrong branch.
+__device__ void log_trial(SolveState* st, bool ok, bool stop, int e) {
+    const int i = st->trials - 1;
+    if (st->prm.tlog && i >= 0 && i < st->prm.tlog_cap)
+        st->prm.tlog[i] = (unsigned char)((ok ? 0x80 : 0) | (stop ? 0x40 : 0) | ((e + 32) & 0x3f));
+}
+
 template <int KM>
 __device__ void finish_point(SolveState* st, const double* m, int K, cudaGraphConditionalHandle h,
                              int use_graph) {
@@ -281,6 +336,8 @@ __device__ void finish_point(SolveState* st, const double* m, int K, cudaGraphCo
     }
     if (gn <= st->prm.grad_tol * st->gnorm0 || gn == 0.0) {
         st->stop = 1;  // PR_STOP_GRAD_TOL
+        const int i = st->trials - 1;  // the accepted trial before this point, if any
+        if (st->accepted && st->prm.tlog && i >= 0 && i < st->prm.tlog_cap) st->prm.tlog[i] |= 0x40;
         set_loop(st, 0, h, use_graph);
         return;
     }
@@ -343,13 +400,17 @@ __device__ void controller_project(SolveState* st, const double* m, int phase, c
         // next first trial: the quadratic model's minimiser, at most
         // step_growth x mu; without the model, grow after a first-try
         // acceptance and keep after backtracking
-        if (st->prm.step_model == 1)
+        if (st->prm.step_model == 1) {
             // an accepted step is at most halved: near convergence the curvature
             // of a cost difference is mostly rounding
-            st->mu_next = mu * pow2_floor(fmax(model ? fmin(st->prm.step_growth, gn2 / curv / mu) : st->prm.step_growth,
-                                               0.5));
-        else
+            const double f = pow2_floor(fmax(model ? fmin(st->prm.step_growth, gn2 / curv / mu) : st->prm.step_growth,
+                                             0.5));
+            st->mu_next = mu * f;
+            log_trial(st, true, false, ilogb(f));
+        } else {
             st->mu_next = (st->bt == 0 ? st->prm.step_growth : st->prm.step_growth_bt) * mu;
+            log_trial(st, true, false, 0);
+        }
         st->iter += 1;
         st->cum_iters += 1;
         st->accepted = 1;
@@ -370,11 +431,17 @@ __device__ void controller_project(SolveState* st, const double* m, int phase, c
         // and a smaller one only less: the gradient is sufficiently small
         // (Section 2.2's stop) at the cost's resolution. w keeps its last
         // accepted value; the next frame starts from this step.
+        log_trial(st, false, true, 0);
         st->stop = 7;  // PR_STOP_RESOLVED
         st->mu_next = mu;
         set_loop(st, 0, h, use_graph);
         return;
     }
+    // backtrack: to the quadratic model's minimiser as a power-of-two fraction
+    // of mu within [1/16, beta], or by beta
+    double f = st->prm.beta;
+    if (st->prm.step_model == 1) f = pow2_floor(model ? fmin(st->prm.beta, fmax(1.0 / 16.0, gn2 / curv / mu)) : st->prm.beta);
+    log_trial(st, false, false, st->prm.step_model == 1 ? ilogb(f) : 0);
     if (st->bt > st->prm.max_bt) {
         st->stop = 3;  // PR_STOP_LINESEARCH_FAILED: w keeps its last accepted value
         st->cum_lsf += 1;
@@ -382,12 +449,7 @@ __device__ void controller_project(SolveState* st, const double* m, int phase, c
         set_loop(st, 0, h, use_graph);
         return;
     }
-    // backtrack: to the quadratic model's minimiser as a power-of-two fraction
-    // of mu within [1/16, beta], or by beta
-    if (st->prm.step_model == 1)
-        st->mu = mu * pow2_floor(model ? fmin(st->prm.beta, fmax(1.0 / 16.0, gn2 / curv / mu)) : st->prm.beta);
-    else
-        st->mu = st->prm.beta * mu;
+    st->mu = mu * f;
     next_trial(st, K);
 }
 
@@ -537,7 +599,7 @@ struct SplitArgs {
 // the sample loop.
 template <int NCH>
 __device__ __noinline__ void finish_tile(const SplitArgs& A, int tile, int iu, int iv, bool valid, float ds) {
-    constexpr int KM = NCH == 8 ? 7 : 3;
+    constexpr int KM = NCH == 8 ? 7 : (NCH == 6 ? 5 : 3);
     constexpr int NV = 3 + 3 * KM;
     const int lane = threadIdx.x & 31;
     unsigned int* tile_ctr = A.ctr + 4 + A.ngroups;
@@ -646,8 +708,6 @@ __global__ void __launch_bounds__(kSplitThreads, NCH == 4 ? 4 : 2) k_project_spl
     const int lane = threadIdx.x & 31;
     const unsigned int n_items = (unsigned int)A.ntiles * kParts;
     unsigned int* tile_ctr = A.ctr + 4 + A.ngroups;
-    constexpr int KM = NCH == 8 ? 7 : 3;
-    constexpr int NV = 3 + 3 * KM;
 
     float lo[3] = {-1.0f, -1.0f, -1.0f}, hi[3] = {g.nmax[0], g.nmax[1], g.nmax[2]};
     bool nonzero = true;
@@ -686,6 +746,14 @@ __global__ void __launch_bounds__(kSplitThreads, NCH == 4 ? 4 : 2) k_project_spl
             const int s_a = s_lo + (L * part) / kParts, s_e = s_lo + (L * (part + 1)) / kParts;
             if constexpr (NCH == 4) {
                 CellCache4 cache;
+                for (int s = s_a; s < s_e; ++s) {
+                    float q[3];
+                    sample_pos(g, b, s, q);
+                    cache.sample(A.vol, A.vd, q, acc);
+                }
+                comp = cache.comp;
+            } else if constexpr (NCH == 6) {
+                CellCache6 cache;
                 for (int s = s_a; s < s_e; ++s) {
                     float q[3];
                     sample_pos(g, b, s, q);
@@ -898,15 +966,17 @@ void project_warp_tile_order(int nu, int nv, int* order) {
 namespace {
 // Resident blocks of the split projector on this device (computed once per device).
 int split_grid(int nch) {
-    static int cached[2][64] = {};
+    static int cached[3][64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-    int& c = cached[nch == 8 ? 1 : 0][dev];
+    int& c = cached[nch == 8 ? 2 : (nch == 6 ? 1 : 0)][dev];
     if (c == 0) {
         int sms = 0, per = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (nch == 8)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_project_split<8>, kSplitThreads, 0);
+        else if (nch == 6)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_project_split<6>, kSplitThreads, 0);
         else
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_project_split<4>, kSplitThreads, 0);
         c = sms * (per > 0 ? per : 1);
@@ -929,6 +999,7 @@ cudaError_t launch_project(Launcher& L, const VolDev& vd, const float* vol_pad, 
         const int need = (ntiles * kParts + kSplitThreads / 32 - 1) / (kSplitThreads / 32);
         const dim3 grid((unsigned)(need < blocks ? need : blocks));
         if (nch == 8) return L(k_project_split<8>, grid, dim3(kSplitThreads), 0, S);
+        if (nch == 6) return L(k_project_split<6>, grid, dim3(kSplitThreads), 0, S);
         if (nch == 4) return L(k_project_split<4>, grid, dim3(kSplitThreads), 0, S);
         return cudaErrorInvalidValue;
     }

@@ -75,6 +75,7 @@ struct Model {
     int* steps = nullptr;
     int* order = nullptr;           // projector tile order
     int* order_w = nullptr;         // split projector's warp-tile order
+    unsigned char* tlog = nullptr;  // per-trial choices of the last solve (kTrialLog bytes)
     SplitScratch ss;                // split projector's scratch (order_w, parts, moments, counters)
     Support* sup = nullptr;         // where the warped volume can be nonzero
     SolveState* st_host = nullptr;  // pinned
@@ -234,7 +235,7 @@ void free_model(Model* m) {
     if (m->graph) cudaGraphDestroy(m->graph);
     void* bufs[] = {m->f0p, m->mean, m->U, m->fh, m->fpad, m->p, m->q, m->y, m->r, m->flat, m->hbuf,
                     m->partials, m->counter, m->st, m->wdev, m->out, m->rg, m->steps, m->order, m->sup,
-                    m->order_w, m->ss.part, m->ss.tile_mom, m->ss.group_mom, m->ss.ctr};
+                    m->order_w, m->ss.part, m->ss.tile_mom, m->ss.group_mom, m->ss.ctr, m->tlog};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (m->st_host) cudaFreeHost(m->st_host);
@@ -258,6 +259,8 @@ size_t partial_doubles(const pr_geometry& g, const VolDev& vd) {
 // Device bytes pr_load_model allocates for a model (the admission check uses
 // this before allocating; the gradient-adjoint scratch of K x N floats is
 // allocated on first use and added to the footprint then).
+constexpr int kTrialLog = 1024;  // bytes of the per-solve trial log
+
 size_t model_bytes(const pr_volume_desc& v, const pr_geometry& g, int K, int storage) {
     VolDev vd = make_vd(v);
     size_t n = (size_t)vd.n, np = (size_t)vd.np, R = (size_t)g.nu * g.nv;
@@ -268,7 +271,7 @@ size_t model_bytes(const pr_volume_desc& v, const pr_geometry& g, int K, int sto
            sizeof(RayGeom) + 16 + (size_t)project_blocks(g.nu, g.nv) * sizeof(int) + sizeof(Support) +
            (size_t)split_tiles(g.nu, g.nv) * sizeof(int) + split_part_floats(g.nu, g.nv, (int)nch) * 4 +
            ((size_t)split_tiles(g.nu, g.nv) + split_groups(g.nu, g.nv)) * kProjMom * 8 +
-           split_counters(g.nu, g.nv) * 4;
+           split_counters(g.nu, g.nv) * 4 + kTrialLog;
 }
 
 int write_params(pr_ctx* c, Model* m, double angle, const pr_solve_opts* o, cudaStream_t stream) {
@@ -291,6 +294,8 @@ int write_params(pr_ctx* c, Model* m, double angle, const pr_solve_opts* o, cuda
     prm.tumor_max_iter = o->tumor_max_iter;
     prm.K = m->K;
     prm.cold_start = o->cold_start ? 1 : 0;
+    prm.tlog = m->tlog;
+    prm.tlog_cap = kTrialLog;
     // Pageable source: the copy is staged before cudaMemcpyAsync returns, so
     // back-to-back asynchronous solves cannot see a later solve's parameters.
     CK(cudaMemcpyAsync(&m->st->prm, &prm, sizeof prm, cudaMemcpyHostToDevice, stream));
@@ -708,6 +713,7 @@ int pr_load_model(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
     A(&m->ss.group_mom, (size_t)split_groups(geom->nu, geom->nv) * kProjMom * 8);
     A(&m->ss.ctr, split_counters(geom->nu, geom->nv) * 4);
     m->ss.order = m->order_w;
+    A(&m->tlog, kTrialLog);
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&m->st_host, sizeof(SolveState), cudaHostAllocDefault);
     if (e != cudaSuccess) {
         free_model(m);
@@ -815,6 +821,18 @@ int pr_reconstruct_async(pr_ctx* c, int id, const float* y_dev, double angle, co
     if (opts && opts->loop_mode == PR_LOOP_HOST) return fail(PR_EINVAL, "host loop is synchronous; use pr_reconstruct");
     CK(cudaMemcpyAsync(m->y, y_dev, (size_t)m->R * 4, cudaMemcpyDeviceToDevice, c->stream));
     return enqueue_solve(c, m, angle, opts);
+}
+
+int pr_trial_log(pr_ctx* c, int id, unsigned char* out, int cap, int* n) {
+    GET_MODEL(c, id, m);
+    if (!out || !n || cap < 0) return fail(PR_EINVAL, "null argument or negative cap");
+    int trials = 0;
+    CK(cudaMemcpyAsync(&trials, &m->st->trials, sizeof trials, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const int k = std::min(std::min(trials, cap), kTrialLog);
+    if (k > 0) CK(cudaMemcpy(out, m->tlog, (size_t)k, cudaMemcpyDeviceToHost));
+    *n = trials;
+    return PR_OK;
 }
 
 int pr_fetch_result(pr_ctx* c, int id, pr_result* out) {

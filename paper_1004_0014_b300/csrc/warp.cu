@@ -34,7 +34,7 @@ __device__ __forceinline__ float lerp(float a, float b, float t) { return __fmaf
 template <int K, int MODE, typename TS>
 __global__ void __launch_bounds__(kWarpThreads) k_warp(WarpArgs<TS> A) {
     constexpr bool kH = (MODE == kWarpFH || MODE == kWarpFlatFH);
-    constexpr int kNch = K <= 3 ? 4 : 8;
+    constexpr int kNch = K <= 3 ? 4 : (K <= 5 ? 6 : 8);
     const VolDev& vd = A.vd;
     long long v0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * 4;
     if (v0 >= vd.n) return;
@@ -128,10 +128,15 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp(WarpArgs<TS> A) {
                 o[0] = val;
 #pragma unroll
                 for (int c = 1; c < kNch; ++c) o[c] = (c - 1 < K) ? h[c - 1 < K ? c - 1 : 0] : 0.0f;
-                float4* dst = reinterpret_cast<float4*>(A.out_pad + pidx * kNch);
+                if (kNch == 6) {
+                    reinterpret_cast<float4*>(A.out_pad)[pidx] = make_float4(o[0], o[1], o[2], o[3]);
+                    reinterpret_cast<float2*>(A.out_pad + 4 * vd.np)[pidx] = make_float2(o[4], o[5 < kNch ? 5 : 0]);
+                } else {
+                    float4* dst = reinterpret_cast<float4*>(A.out_pad + pidx * kNch);
 #pragma unroll
-                for (int c4 = 0; c4 < kNch / 4; ++c4)
-                    dst[c4] = make_float4(o[4 * c4], o[4 * c4 + 1], o[4 * c4 + 2], o[4 * c4 + 3]);
+                    for (int c4 = 0; c4 < kNch / 4; ++c4)
+                        dst[c4] = make_float4(o[4 * c4], o[4 * c4 + 1], o[4 * c4 + 2], o[4 * c4 + 3]);
+                }
             } else if (MODE == kWarpFPad) {
                 A.out_pad[pidx] = val;
             } else {

@@ -6,7 +6,7 @@ quantisation error against the float32 inputs is reported, not asserted."""
 import numpy as np
 import pytest
 
-from gpu_util import TOL_GRAD, TOL_PROJ, TOL_TUMOR_MM, TOL_W, noisy, rel, report
+from gpu_util import TOL_GRAD, TOL_PROJ, TOL_TUMOR_MM, TOL_W, checked_oracle_solve, noisy, rel, report
 from oracle import oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -69,11 +69,14 @@ def test_k5_solve(k5, name):
 
     mid, om = k5["models"][name]
     res = k5["ctx"].reconstruct(mid, k5["y"], k5["th"], default_opts(max_iters=12, cold_start=1))
-    ores = O.reconstruct(om, k5["geom"], k5["th"], k5["y"].astype(np.float64), np.zeros(5),
-                         O.SolveOptions(max_iters=12))
+    so = O.SolveOptions(max_iters=12)
+    ores, ties = checked_oracle_solve(
+        k5["ctx"].trial_log(mid),
+        lambda rp: O.reconstruct(om, k5["geom"], k5["th"], k5["y"].astype(np.float64), np.zeros(5), so, replay=rp),
+        so)
     et = float(np.max(np.abs(res["tumor"] - ores.tumor)))
     report("k5_solve_" + name, w_rel=rel(res["w"], ores.w), J_rel=abs(res["J"] - ores.J) / ores.J, tumor_mm=et,
-           backtracks=res["backtracks"], oracle_backtracks=ores.backtracks)
+           backtracks=res["backtracks"], oracle_backtracks=ores.backtracks, ties=ties)
     assert res["iters"] == ores.iters
     assert abs(res["J"] - ores.J) / ores.J < TOL_PROJ
     assert rel(res["w"], ores.w) < TOL_W
@@ -136,3 +139,36 @@ def test_k5_inverse_field(k5, name):
     report("k5_invert_" + name, max_abs_mm=err, max_steps=steps, oracle_sweeps=sweeps, unconverged=open_)
     assert open_ == 0
     assert err < 1e-3
+
+
+def test_k4_cost_gradient_and_solve(k5):
+    """K = 4 (the 6-channel solver volume with one unused channel): cost and
+    both gradient forms at a point, and a short solve, against the oracle."""
+    from paper_1004_0014_b300 import default_opts
+
+    pca, ctx, vol, geom, th = k5["pca"], k5["ctx"], k5["vol"], k5["geom"], k5["th"]
+    f0 = k5["models"]["f32"][1].f0.astype(np.float32)
+    mean, U = pca.mean.astype(np.float32), pca.U[:4].astype(np.float32)
+    mid = ctx.load_model(vol, geom, f0, mean, U, k5["models"]["f32"][1].c0)
+    om = O.Model(vol, f0.astype(np.float64), mean.astype(np.float64), U.astype(np.float64),
+                 k5["models"]["f32"][1].c0)
+    try:
+        w = np.array([0.5, -0.2, 0.1, 0.05])
+        go, Jo, _ = O.gradient(om, geom, th, w, 1.01, -0.002, k5["y"].astype(np.float64))
+        for mode in (0, 1):
+            J, g = ctx.cost_grad(mid, k5["yd"], th, w, 1.01, -0.002, mode)
+            report("k4_cost_grad", mode=mode, J_rel=abs(J - Jo) / Jo, g_rel=rel(g, go))
+            assert abs(J - Jo) / Jo < TOL_PROJ
+            assert rel(g, go) < TOL_GRAD
+        res = ctx.reconstruct(mid, k5["y"], th, default_opts(max_iters=8, cold_start=1))
+        so = O.SolveOptions(max_iters=8)
+        ores, ties = checked_oracle_solve(
+            ctx.trial_log(mid),
+            lambda rp: O.reconstruct(om, geom, th, k5["y"].astype(np.float64), np.zeros(4), so, replay=rp), so)
+        report("k4_solve", w_rel=rel(res["w"], ores.w), J_rel=abs(res["J"] - ores.J) / ores.J,
+               backtracks=res["backtracks"], oracle_backtracks=ores.backtracks, ties=ties)
+        assert res["iters"] == ores.iters
+        assert abs(res["J"] - ores.J) / ores.J < TOL_PROJ
+        assert rel(res["w"], ores.w) < TOL_W
+    finally:
+        ctx.release_model(mid)

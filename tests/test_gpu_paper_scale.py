@@ -8,7 +8,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_util import TOL_GRAD, TOL_PROJ, TOL_TUMOR_MM, TOL_W, rel, report
+from gpu_util import TOL_GRAD, TOL_PROJ, TOL_TUMOR_MM, TOL_W, checked_oracle_solve, rel, report
 from oracle import oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -58,11 +58,15 @@ def test_paper_scale_solve(paper):
     p = paper
     it = 5
     res = p["ctx"].reconstruct(p["mid"], p["y"], p["th"], default_opts(max_iters=it, cold_start=1))
-    ores = O.reconstruct(p["om"], p["geom"], p["th"], p["y"].astype(np.float64), np.zeros(3),
-                         O.SolveOptions(max_iters=it))
+    so = O.SolveOptions(max_iters=it)
+    ores, ties = checked_oracle_solve(
+        p["ctx"].trial_log(p["mid"]),
+        lambda rp: O.reconstruct(p["om"], p["geom"], p["th"], p["y"].astype(np.float64), np.zeros(3), so,
+                                 replay=rp), so)
     et = float(np.max(np.abs(res["tumor"] - ores.tumor)))
     report("paper_solve", iters=res["iters"], J_rel=abs(res["J"] - ores.J) / ores.J, w_rel=rel(res["w"], ores.w),
-           tumor_mm=et, trials=res["trials"], oracle_backtracks=ores.backtracks, backtracks=res["backtracks"])
+           tumor_mm=et, trials=res["trials"], oracle_backtracks=ores.backtracks, backtracks=res["backtracks"],
+           ties=ties)
     assert res["iters"] == ores.iters == it
     assert res["backtracks"] == ores.backtracks
     assert abs(res["J"] - ores.J) / ores.J < TOL_PROJ

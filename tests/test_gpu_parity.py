@@ -6,8 +6,8 @@ import math
 import numpy as np
 import pytest
 
-from gpu_util import (RAGGED_GEOM, RAGGED_VOL, TOL_GRAD, TOL_PROJ, TOL_TUMOR_MM, TOL_W, noisy,
-                      random_volume, rel, report)
+from gpu_util import (RAGGED_GEOM, RAGGED_VOL, TOL_GRAD, TOL_PROJ, TOL_TUMOR_MM, TOL_W, checked_oracle_solve,
+                      noisy, random_volume, rel, report)
 from oracle import oracle as O
 from phantom import Geometry, Volume
 
@@ -215,13 +215,16 @@ def test_reconstruct_matches_oracle(ctx, small):
     om, geom, th = small["om"], small["geom"], small["angle"]
     it = small["max_iters"]
     res = ctx.reconstruct(small["mid"], small["y"], th, _opts(max_iters=it, cold_start=1, w0=[0, 0, 0]))
-    ores = O.reconstruct(om, geom, th, _up(small["y"]), np.zeros(3), O.SolveOptions(max_iters=it))
+    so = O.SolveOptions(max_iters=it)
+    ores, ties = checked_oracle_solve(
+        ctx.trial_log(small["mid"]),
+        lambda rp: O.reconstruct(om, geom, th, _up(small["y"]), np.zeros(3), so, replay=rp), so)
     eJ = abs(res["J"] - ores.J) / ores.J
     ew = rel(res["w"], ores.w)
     et = float(np.max(np.abs(res["tumor"] - ores.tumor)))
     report("reconstruct64", iters=res["iters"], J_rel=eJ, w_rel=ew, tumor_mm=et,
            a_rel=abs(res["a"] - ores.a) / abs(ores.a), trials=res["trials"], backtracks=res["backtracks"],
-           oracle_backtracks=ores.backtracks)
+           oracle_backtracks=ores.backtracks, ties=ties)
     assert res["iters"] == ores.iters == it
     assert res["stop_reason"] == ores.stop_reason
     assert eJ < TOL_PROJ
@@ -256,8 +259,11 @@ def test_warm_start_carries_w(ctx, small):
     res2 = ctx.reconstruct(small["mid"], small["y"], small["angle"], _opts(max_iters=3))
     # a warm-started solve starts from the state and leaves its answer there
     assert np.array_equal(ctx.get_state(small["mid"]), res2["w"])
-    ores = O.reconstruct(small["om"], small["geom"], small["angle"], _up(small["y"]), w_set,
-                         O.SolveOptions(max_iters=3))
+    so = O.SolveOptions(max_iters=3)
+    ores, _ = checked_oracle_solve(
+        ctx.trial_log(small["mid"]),
+        lambda rp: O.reconstruct(small["om"], small["geom"], small["angle"], _up(small["y"]), w_set, so,
+                                 replay=rp), so)
     assert rel(res2["w"], ores.w) < TOL_W
 
 
@@ -323,12 +329,17 @@ def test_warm_started_frames_match_oracle(ctx, small):
     for i, th in enumerate(angles):
         ft = O.warp(vol, om.f0, dvf_analytic(vol, 1.0 + i / 6.0, 1.5))
         ys.append(_f32(noisy(O.project(vol, geom, th, ft), 10 + i)))
+    so = O.SolveOptions(max_iters=6)
     a = ctx.reconstruct(small["mid"], ys[0], angles[0], _opts(max_iters=6, cold_start=1, w0=[0, 0, 0]))
+    log_a = ctx.trial_log(small["mid"])
     b = ctx.reconstruct(small["mid"], ys[1], angles[1], _opts(max_iters=6))
-    oa = O.reconstruct(om, geom, angles[0], _up(ys[0]), np.zeros(3), O.SolveOptions(max_iters=6))
-    ob = O.reconstruct(om, geom, angles[1], _up(ys[1]), oa.w, O.SolveOptions(max_iters=6), mu_next=oa.mu)
+    log_b = ctx.trial_log(small["mid"])
+    oa, ties_a = checked_oracle_solve(
+        log_a, lambda rp: O.reconstruct(om, geom, angles[0], _up(ys[0]), np.zeros(3), so, replay=rp), so)
+    ob, ties_b = checked_oracle_solve(
+        log_b, lambda rp: O.reconstruct(om, geom, angles[1], _up(ys[1]), oa.w, so, mu_next=oa.mu, replay=rp), so)
     report("warm_frames64", w_rel=rel(b["w"], ob.w), mu_rel=abs(b["mu"] - ob.mu) / ob.mu,
-           backtracks=b["backtracks"], oracle_backtracks=ob.backtracks)
+           backtracks=b["backtracks"], oracle_backtracks=ob.backtracks, ties=ties_a + ties_b)
     # the step is step0 / |grad J| times powers of beta and step_growth, so it
     # carries the gradient's tolerance
     assert abs(a["mu"] - oa.mu) / oa.mu < TOL_GRAD
@@ -348,19 +359,22 @@ def test_predicted_start_matches_oracle_chain(ctx, small):
         th = 0.2 + 0.02 * j
         ft = O.warp(vol, om.f0, dvf_analytic(vol, 0.6 + j / 6.0, 1.5))
         frames.append((th, _f32(noisy(O.project(vol, geom, th, ft), 40 + j))))
-    gpu = []
+    gpu, logs = [], []
     for j, (th, y) in enumerate(frames):
         kw = dict(max_iters=5, predict=1)
         if j == 0:
             kw.update(cold_start=1, w0=[0, 0, 0])
         gpu.append(ctx.reconstruct(small["mid"], y, th, _opts(**kw)))
+        logs.append(ctx.trial_log(small["mid"]))
     ws, mu = [], None
+    so = O.SolveOptions(max_iters=5)
     for j, (th, y) in enumerate(frames):
         w0 = np.zeros(3) if j == 0 else (ws[-1] if j == 1 else 2 * ws[-1] - ws[-2])
-        r = O.reconstruct(om, geom, th, _up(y), w0, O.SolveOptions(max_iters=5), mu_next=mu)
+        r, ties = checked_oracle_solve(
+            logs[j], lambda rp: O.reconstruct(om, geom, th, _up(y), w0, so, mu_next=mu, replay=rp), so)
         ws.append(r.w)
         mu = r.mu
         report("predict_chain64", frame=j, w_rel=rel(gpu[j]["w"], r.w), backtracks=gpu[j]["backtracks"],
-               oracle_backtracks=r.backtracks)
+               oracle_backtracks=r.backtracks, ties=ties)
         assert gpu[j]["backtracks"] == r.backtracks
         assert rel(gpu[j]["w"], r.w) < TOL_W
