@@ -193,6 +193,20 @@ int pr_model_footprint(pr_ctx* ctx, int model_id, size_t* bytes);
 int pr_reconstruct(pr_ctx* ctx, int model_id, const float* y, int y_location, double angle_rad,
                    const pr_solve_opts* opts, pr_result* out, float* volume_out);
 
+/* Several solves (Sections 2.2 and 2.3 each) in one CUDA graph launch, with
+ * no host round trip between them: solve i reconstructs y[i] (host,
+ * [nv][nu] float32 in the geometry of model model_ids[i]) at angles[i], as
+ * pr_reconstruct would. Solves of one model run in the order given, each
+ * warm-starting from the one before; solves of different models are
+ * independent and run concurrently on the GPU. opts (nullable = defaults)
+ * apply to every solve; the host loop mode is not allowed. out[i] receives
+ * solve i's result. The instantiated graph is kept for the next call with the
+ * same sequence of model ids (only the staged frames and parameters change);
+ * a model release discards it. 1 <= n <= 4096. Synchronous; not while
+ * serving. Errors: PR_EINVAL, PR_ENOMODEL, PR_ENOMEM, PR_ECUDA. */
+int pr_reconstruct_batch(pr_ctx* ctx, int n, const int* model_ids, const float* const* y,
+                         const double* angles, const pr_solve_opts* opts, pr_result* out);
+
 /* As pr_reconstruct with a device-resident y, but only enqueues the solve on
  * the context stream and returns. y_dev is read by the enqueued work, so it
  * must stay valid and unchanged until pr_fetch_result returns. Fetch the

@@ -94,6 +94,11 @@ class Context:
             res["volume"] = vo
         return res
 
+    def reconstruct_batch(self, mids, ys, angles, opts: SolveOpts | None = None):
+        """Solves frame i of model mids[i] for every i in one graph launch
+        (host ys); results as dicts, in order."""
+        return [r.as_dict() for r in capi.pr_reconstruct_batch(self._ctx, mids, ys, angles, opts)]
+
     def reconstruct_async(self, mid: int, y_dev, angle_rad: float, opts: SolveOpts | None = None):
         capi.pr_reconstruct_async(self._ctx, mid, y_dev, angle_rad, opts)
 

@@ -39,7 +39,7 @@ PR_LOOP_GRAPH, PR_LOOP_HOST = 0, 1
 
 EXPORTED = [
     "pr_version", "pr_last_error", "pr_default_opts", "pr_create", "pr_destroy", "pr_load_model",
-    "pr_release_model", "pr_model_footprint", "pr_reconstruct", "pr_reconstruct_async",
+    "pr_release_model", "pr_model_footprint", "pr_reconstruct", "pr_reconstruct_batch", "pr_reconstruct_async",
     "pr_fetch_result", "pr_get_state", "pr_set_state", "pr_warp", "pr_project", "pr_backproject",
     "pr_forward", "pr_vjp", "pr_cost_grad", "pr_tumor", "pr_invert_dvf", "pr_trial_log", "pr_time_kernel",
     "pr_model_stats",
@@ -140,6 +140,8 @@ def load_library(path: str | None = None):
         "pr_model_footprint": (_I, [_P, _I, ctypes.POINTER(ctypes.c_size_t)]),
         "pr_reconstruct": (_I, [_P, _I, _P, _I, _D, ctypes.POINTER(SolveOpts), ctypes.POINTER(Result), _P]),
         "pr_reconstruct_async": (_I, [_P, _I, _P, _D, ctypes.POINTER(SolveOpts)]),
+        "pr_reconstruct_batch": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_P), _DP, ctypes.POINTER(SolveOpts),
+                                      ctypes.POINTER(Result)]),
         "pr_fetch_result": (_I, [_P, _I, ctypes.POINTER(Result)]),
         "pr_get_state": (_I, [_P, _I, _DP]),
         "pr_set_state": (_I, [_P, _I, _DP]),
@@ -282,6 +284,21 @@ def pr_reconstruct(ctx, model_id: int, y, angle_rad: float, opts: SolveOpts | No
     _check(_lib.pr_reconstruct(ctx, int(model_id), py, ly, float(angle_rad),
                                ctypes.byref(opts) if opts is not None else None, ctypes.byref(res), vo))
     return res
+
+
+def pr_reconstruct_batch(ctx, model_ids, ys, angles, opts: SolveOpts | None = None):
+    """Solves n frames (host arrays) in one graph launch; returns n Results."""
+    n = len(model_ids)
+    if not (len(ys) == len(angles) == n):
+        raise ValueError("model_ids, ys and angles must have the same length")
+    arrs = [_f32(y) for y in ys]
+    ids = (_I * n)(*[int(i) for i in model_ids])
+    ptrs = (_P * n)(*[a.ctypes.data for a in arrs])
+    ang = np.ascontiguousarray(angles, dtype=np.float64)
+    out = (Result * n)()
+    _check(_lib.pr_reconstruct_batch(ctx, n, ids, ptrs, ang.ctypes.data_as(_DP),
+                                     ctypes.byref(opts) if opts is not None else None, out))
+    return list(out)
 
 
 def pr_reconstruct_async(ctx, model_id: int, y_dev, angle_rad: float, opts: SolveOpts | None = None):

@@ -9,6 +9,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -117,6 +118,8 @@ struct ServeSlot {
     std::chrono::steady_clock::time_point t_dispatch;
 };
 
+struct Batch;  // pr_reconstruct_batch's graph and staging (defined with it)
+
 struct Serve {
     std::thread worker;
     std::condition_variable cv_work, cv_done;
@@ -144,6 +147,7 @@ struct pr_ctx {
     float* pad = nullptr;  // scratch for pr_project
     size_t pad_cap = 0;
     RayGeom* rg = nullptr;
+    Batch* batch = nullptr;  // graph and staging of pr_reconstruct_batch
 };
 
 namespace {
@@ -274,7 +278,7 @@ size_t model_bytes(const pr_volume_desc& v, const pr_geometry& g, int K, int sto
            split_counters(g.nu, g.nv) * 4 + kTrialLog;
 }
 
-int write_params(pr_ctx* c, Model* m, double angle, const pr_solve_opts* o, cudaStream_t stream) {
+SolveParams make_params(const Model* m, double angle, const pr_solve_opts* o) {
     SolveParams prm;
     memset(&prm, 0, sizeof prm);
     prm.rg = make_rg(m->vol, m->geom, angle);
@@ -296,6 +300,11 @@ int write_params(pr_ctx* c, Model* m, double angle, const pr_solve_opts* o, cuda
     prm.cold_start = o->cold_start ? 1 : 0;
     prm.tlog = m->tlog;
     prm.tlog_cap = kTrialLog;
+    return prm;
+}
+
+int write_params(pr_ctx* c, Model* m, double angle, const pr_solve_opts* o, cudaStream_t stream) {
+    SolveParams prm = make_params(m, angle, o);
     // Pageable source: the copy is staged before cudaMemcpyAsync returns, so
     // back-to-back asynchronous solves cannot see a later solve's parameters.
     CK(cudaMemcpyAsync(&m->st->prm, &prm, sizeof prm, cudaMemcpyHostToDevice, stream));
@@ -449,6 +458,100 @@ double ms_between(std::chrono::steady_clock::time_point a, std::chrono::steady_c
 
 // Worker: retire finished slots, then fill free slots with the oldest request
 // whose model has nothing in flight. Runs until stopped and idle.
+// ---------------------------------------------------------------------------
+// Batched solves in one graph (pr_reconstruct_batch)
+// ---------------------------------------------------------------------------
+// One CUDA graph holds every solve of a batch. A solve is a chain of nodes:
+// copy its y and parameters from the batch's staging arrays into the model,
+// the solve's kernels with a conditional WHILE of its own, the tumor, and a
+// copy of the final state into the batch's result array. Solves of one model
+// are chained in batch order (each warm-starts from the one before); solves
+// of different models are independent branches that the GPU runs
+// concurrently. The instantiated graph is kept while the batch's model
+// sequence repeats; only the staged data change between launches.
+struct Batch {
+    std::vector<int> key;  // model ids in batch order
+    std::vector<size_t> y_off;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    float* y = nullptr;  // staged frames (device)
+    size_t y_cap = 0;
+    SolveParams* prm = nullptr;  // staged parameters (device)
+    SolveState* res = nullptr;   // final states (device)
+    SolveState* res_host = nullptr;  // pinned
+    int cap = 0;
+};
+
+void batch_drop_graph(Batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->key.clear();
+}
+
+void batch_free(pr_ctx* c) {
+    Batch* b = c->batch;
+    if (!b) return;
+    batch_drop_graph(b);
+    if (b->y) cudaFree(b->y);
+    if (b->prm) cudaFree(b->prm);
+    if (b->res) cudaFree(b->res);
+    if (b->res_host) cudaFreeHost(b->res_host);
+    delete b;
+    c->batch = nullptr;
+}
+
+int add_solve_nodes(cudaGraph_t g, Model* m, const cudaGraphNode_t* dep, const float* y_src, const SolveParams* prm_src,
+                    SolveState* res_dst, cudaGraphNode_t* last) {
+    SolveState* st = m->st;
+    cudaGraphNode_t ny, np, nr;
+    CK(cudaGraphAddMemcpyNode1D(&ny, g, dep, dep ? 1 : 0, m->y, y_src, (size_t)m->R * 4, cudaMemcpyDeviceToDevice));
+    CK(cudaGraphAddMemcpyNode1D(&np, g, &ny, 1, &st->prm, prm_src, sizeof(SolveParams), cudaMemcpyDeviceToDevice));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    Launcher L;
+    L.graph = g;
+    L.last = np;
+    L.has_last = true;
+    CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
+    CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
+    CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
+                      m->partials, m->counter, kPhaseInit, h, 1, SupportRef{m->sup, st->wt, m->K}, &m->ss));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cond;
+    CK(cudaGraphAddNode(&cond, g, &L.last, nullptr, 1, &cp));
+    Launcher B;
+    B.graph = cp.conditional.phGraph_out[0];
+    CK(launch_warp(B, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
+    CK(launch_project(B, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
+                      m->partials, m->counter, kPhaseTrial, h, 1, SupportRef{m->sup, st->wt, m->K}, &m->ss));
+    L.last = cond;
+    CK(launch_tumor(L, m->md, st->w, 0.0, 0, &st->prm, st->tumor, &st->tumor_steps));
+    CK(cudaGraphAddMemcpyNode1D(&nr, g, &L.last, 1, res_dst, st, sizeof(SolveState), cudaMemcpyDeviceToDevice));
+    *last = nr;
+    return PR_OK;
+}
+
+int build_batch_graph(Batch* b, const std::vector<Model*>& ms) {
+    batch_drop_graph(b);
+    CK(cudaGraphCreate(&b->graph, 0));
+    std::map<const Model*, cudaGraphNode_t> tail;
+    for (size_t i = 0; i < ms.size(); ++i) {
+        auto it = tail.find(ms[i]);
+        cudaGraphNode_t last;
+        TRY(add_solve_nodes(b->graph, ms[i], it == tail.end() ? nullptr : &it->second, b->y + b->y_off[i], b->prm + i,
+                            b->res + i, &last));
+        tail[ms[i]] = last;
+    }
+    CK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    return PR_OK;
+}
+
 void serve_loop(pr_ctx* c) {
     cudaSetDevice(c->device);
     Serve* sv = c->serve;
@@ -644,6 +747,7 @@ void pr_destroy(pr_ctx* c) {
     cudaSetDevice(c->device);
     serve_free(c);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    batch_free(c);
     for (auto& kv : c->models) free_model(kv.second);
     c->models.clear();
     if (c->pad) cudaFree(c->pad);
@@ -804,6 +908,8 @@ int pr_release_model(pr_ctx* c, int id) {
         c->used -= m->bytes;
         c->models.erase(id);
     }
+    if (c->batch && std::find(c->batch->key.begin(), c->batch->key.end(), id) != c->batch->key.end())
+        batch_drop_graph(c->batch);  // its nodes point into this model's buffers
     free_model(m);
     return PR_OK;
 }
@@ -859,6 +965,78 @@ int pr_reconstruct(pr_ctx* c, int id, const float* y, int y_location, double ang
         CK(cudaMemcpyAsync(volume_out, m->flat, (size_t)m->md.vd.n * 4, cudaMemcpyDeviceToHost, c->stream));
     }
     return pr_fetch_result(c, id, out);
+}
+
+int pr_reconstruct_batch(pr_ctx* c, int n, const int* model_ids, const float* const* y, const double* angles,
+                         const pr_solve_opts* opts, pr_result* out) {
+    if (!c || !model_ids || !y || !angles || !out) return fail(PR_EINVAL, "null argument");
+    if (n < 1 || n > 4096) return fail(PR_EINVAL, "batch size %d outside 1..4096", n);
+    if (c->serve && !c->serve->stop) return fail(PR_EINVAL, "stop serving before a batch");
+    pr_solve_opts o;
+    if (opts)
+        o = *opts;
+    else
+        pr_default_opts(&o);
+    if (!opts_ok(&o) || o.loop_mode != PR_LOOP_GRAPH) return fail(PR_EINVAL, "invalid solve options for a batch");
+    std::vector<Model*> ms((size_t)n);
+    std::vector<size_t> off((size_t)n);
+    size_t total = 0;
+    {
+        std::lock_guard<std::mutex> lock(c->mu);
+        for (int i = 0; i < n; ++i) {
+            Model* m = find(c, model_ids[i]);
+            if (!m) return fail(PR_ENOMODEL, "no model %d", model_ids[i]);
+            if (!y[i]) return fail(PR_EINVAL, "null y[%d]", i);
+            if (!isfinite(angles[i])) return fail(PR_EINVAL, "angle %d is not finite", i);
+            ms[(size_t)i] = m;
+            off[(size_t)i] = total;
+            total += ((size_t)m->R + 3) / 4 * 4;  // 16-byte aligned slices
+        }
+    }
+    CK(cudaSetDevice(c->device));
+    if (!c->batch) c->batch = new Batch;
+    Batch* b = c->batch;
+    if (b->y_cap < total || b->cap < n) {  // grow the staging; graphs bake its addresses
+        batch_drop_graph(b);
+        if (b->y) cudaFree(b->y);
+        if (b->prm) cudaFree(b->prm);
+        if (b->res) cudaFree(b->res);
+        if (b->res_host) cudaFreeHost(b->res_host);
+        b->y = nullptr, b->prm = nullptr, b->res = nullptr, b->res_host = nullptr, b->y_cap = 0, b->cap = 0;
+        cudaError_t e = cudaMalloc(&b->y, total * 4);
+        if (!e) e = cudaMalloc(&b->prm, (size_t)n * sizeof(SolveParams));
+        if (!e) e = cudaMalloc(&b->res, (size_t)n * sizeof(SolveState));
+        if (!e) e = cudaHostAlloc((void**)&b->res_host, (size_t)n * sizeof(SolveState), cudaHostAllocDefault);
+        if (e) {
+            batch_free(c);
+            cudaGetLastError();
+            return fail(PR_ENOMEM, "batch staging: %s", cudaGetErrorString(e));
+        }
+        b->y_cap = total;
+        b->cap = n;
+    }
+    std::vector<int> key(model_ids, model_ids + n);
+    if (!b->exec || key != b->key || off != b->y_off) {
+        b->y_off = off;
+        int rc = build_batch_graph(b, ms);
+        if (rc) {
+            batch_drop_graph(b);
+            return rc;
+        }
+        b->key = key;
+    }
+    std::vector<SolveParams> prm((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        Model* m = ms[(size_t)i];
+        prm[(size_t)i] = make_params(m, angles[i], &o);
+        CK(cudaMemcpyAsync(b->y + off[(size_t)i], y[i], (size_t)m->R * 4, cudaMemcpyHostToDevice, c->stream));
+    }
+    CK(cudaMemcpyAsync(b->prm, prm.data(), (size_t)n * sizeof(SolveParams), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaGraphLaunch(b->exec, c->stream));
+    CK(cudaMemcpyAsync(b->res_host, b->res, (size_t)n * sizeof(SolveState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < n; ++i) fill_result(ms[(size_t)i], b->res_host[i], &out[i]);
+    return PR_OK;
 }
 
 int pr_get_state(pr_ctx* c, int id, double* w) {
