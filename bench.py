@@ -459,8 +459,18 @@ def run_ours(args):
                         ("project_f", capi.PR_KERNEL_PROJECT_F)):
         kern[name] = ctx.time_kernel(mid, which, angles[W], iters=20)
     kern["invert_dvf"] = ctx.time_kernel(mid, capi.PR_KERNEL_INVERT, angles[W], iters=5)
+    fixed = None
     if args.adjoint:
         kern["backproject_dot"] = ctx.time_kernel(mid, capi.PR_KERNEL_BACKPROJECT, angles[W], iters=3)
+        # fixed gantry angle: the transpose's footprint weights stored once
+        t0 = time.perf_counter()
+        nb = ctx.fix_angle(mid, angles[W])
+        t_build = time.perf_counter() - t0
+        kern["backproject_dot_fixed_angle"] = ctx.time_kernel(mid, capi.PR_KERNEL_BACKPROJECT, angles[W], iters=5)
+        ctx.fix_angle(mid, float("nan"))
+        fixed = {"table_bytes": nb, "build_s": t_build,
+                 "adjoint_ms": kern["backproject_dot_fixed_angle"], "adjoint_ms_on_the_fly": kern["backproject_dot"],
+                 "table_gbs": (nb + 4 * vol.n * w["K"]) / (kern["backproject_dot_fixed_angle"] / 1000.0) / 1e9}
 
     # Dominant kernel: the 4-channel projector, bound by instruction issue and
     # FP32 arithmetic (ncu: DRAM ~1%, L1 ~70%, issue ~65%), so its roofline is
@@ -553,6 +563,7 @@ def run_ours(args):
             "roofline": roofline,
             "roofline_warp": roofline_warp,
             "roofline_invert_dvf": roofline_invert,
+            "fixed_angle_adjoint": fixed,
             "clocks": clk.summary(),
             "paper_context": {"s_per_projection": 0.24, "hardware": "Tesla C1060",
                               "workload": "NCAT 256x256x120, K=3, 200x150 projections (context only)"},

@@ -320,6 +320,19 @@ int pr_tumor(pr_ctx* ctx, int model_id, const double* w, double tol, int max_ite
  * PR_ENOMODEL, PR_ECUDA. */
 int pr_trial_log(pr_ctx* ctx, int model_id, unsigned char* out, int cap, int* n);
 
+/* Section 5's fixed-angle geometry (fluoroscopy: the gantry does not move,
+ * so P is the same matrix for every frame). Builds the model's table of the
+ * transpose at angle_rad: for each voxel its detector footprint and the weight
+ * of every footprint pixel (the sum of the trilinear hat over the pixel's ray
+ * samples), about (footprint pixels) x N floats. pr_vjp and pr_cost_grad mode
+ * 1 at exactly this angle then gather the stored weights instead of
+ * recomputing them, with bitwise-identical results; other angles compute as
+ * before. A NaN angle drops the table. The table counts against the HBM
+ * budget (PR_EADMIT if it does not fit); *table_bytes (nullable) receives its
+ * size. Synchronous. Errors: PR_EINVAL (infinite angle, detector wider than
+ * 32767), PR_ENOMODEL, PR_EADMIT, PR_ENOMEM, PR_ECUDA. */
+int pr_fix_angle(pr_ctx* ctx, int model_id, double angle_rad, size_t* table_bytes);
+
 /* Section 2.3 with ref. 13 over the whole grid: the push-forward DVF y, the
  * inverse of the model's pull-back field x = mean + U w (w: K doubles, host),
  * i.e. u + y(u) + x(u + y(u)) = u at every voxel centre u, x interpolated
@@ -369,7 +382,8 @@ enum {
     PR_KERNEL_WARP_FH = 0,      /* fused DVF synthesis + warp writing f and h (solver pass) */
     PR_KERNEL_PROJECT_FH = 1,   /* ray-march projection of (f, h_1..h_K) (solver pass) */
     PR_KERNEL_REGRAD = 2,       /* residual, cost and gradient over the detector (pr_cost_grad) */
-    PR_KERNEL_BACKPROJECT = 3,  /* gather transpose contracted with h (adjoint gradient) */
+    PR_KERNEL_BACKPROJECT = 3,  /* gather transpose contracted with h (adjoint gradient; the
+                                   fixed-angle table when pr_fix_angle built one at this angle) */
     PR_KERNEL_WARP_F = 4,       /* warp writing f only */
     PR_KERNEL_PROJECT_F = 5,    /* ray-march projection of f only */
     PR_KERNEL_INVERT = 6        /* whole-grid DVF inversion (pr_invert_dvf, tol 1e-5 mm, 64 steps) */

@@ -13,6 +13,15 @@
 // h_k(v) on the fly (the gradient formula after Eq. 4: dJ/dw_k = 2 sum_v
 // g(v) h_k(v), or the vector-Jacobian product without the 2) and g is never
 // stored; block partials are reduced in FP64 in a fixed order.
+//
+// Fixed gantry angle (Section 5: fluoroscopy keeps P the same for every
+// frame): the weight of each footprint pixel, sum over its samples of the
+// hat product, depends on the geometry alone. A table of these weights
+// (footprint rectangle per voxel, weights slot-major: slot s of voxel v at
+// s * N + v, so a warp reads consecutive voxels) is built once per angle;
+// with it the transpose is a gather of stored weights against r, in the same
+// pixel order and with the same multiply-adds as the on-the-fly form, so the
+// two give bitwise-equal results.
 #include "internal.h"
 
 namespace pr {
@@ -33,48 +42,68 @@ __device__ __forceinline__ void footprint(const RayGeom& g, float px, float py, 
     vmax = fmaxf(vmax, v);
 }
 
+// Footprint rectangle [u0, u1] x [w0, w1] of voxel (i, j, k): the detector
+// pixels whose rays can cross the voxel's support box (v - spacing, v + spacing).
+__device__ __forceinline__ void voxel_footprint(const RayGeom& g, int i, int j, int k, int& u0, int& u1, int& w0,
+                                                int& w1) {
+    float cx = g.origin[0] + i * g.sp[0], cy = g.origin[1] + j * g.sp[1], cz = g.origin[2] + k * g.sp[2];
+    float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        footprint(g, cx + ((c & 1) ? g.sp[0] : -g.sp[0]), cy + ((c & 2) ? g.sp[1] : -g.sp[1]),
+                  cz + ((c & 4) ? g.sp[2] : -g.sp[2]), umin, umax, vmin, vmax);
+    umin = fmaxf(umin, -1.0f);
+    vmin = fmaxf(vmin, -1.0f);
+    umax = fminf(umax, (float)g.nu);
+    vmax = fminf(vmax, (float)g.nv);
+    u0 = max(0, (int)ceilf(umin)), u1 = min(g.nu - 1, (int)floorf(umax));
+    w0 = max(0, (int)ceilf(vmin)), w1 = min(g.nv - 1, (int)floorf(vmax));
+}
+
+// Weight of pixel (iu, iv) for voxel (i, j, k): the sum over the ray's samples
+// inside the voxel's support of the trilinear hat product (0 if it misses).
+__device__ __forceinline__ float pixel_weight(const RayGeom& g, int i, int j, int k, int iu, int iv) {
+    const float lo[3] = {(float)(i - 1), (float)(j - 1), (float)(k - 1)};
+    const float hi[3] = {(float)(i + 1), (float)(j + 1), (float)(k + 1)};
+    const float fi = (float)i, fj = (float)j, fk = (float)k;
+    float b[3], t0, t1;
+    ray_dir_index(g, iu, iv, b);
+    if (!ray_box(g.a, b, lo, hi, t0, t1)) return 0.0f;
+    int s0 = (int)fminf(fmaxf(ceilf(t0 / g.ds - 0.5f), 0.0f), 1.0e7f);
+    int s1 = (int)fminf(floorf(t1 / g.ds - 0.5f), 1.0e7f);
+    float wsum = 0.0f;
+    for (int s = s0; s <= s1; ++s) {
+        float q[3];
+        sample_pos(g, b, s, q);
+        float wx = 1.0f - fabsf(q[0] - fi), wy = 1.0f - fabsf(q[1] - fj), wz = 1.0f - fabsf(q[2] - fk);
+        if (wx > 0.0f && wy > 0.0f && wz > 0.0f) wsum = __fmaf_rn(wx * wy, wz, wsum);
+    }
+    return wsum;
+}
+
 template <int K>
 __global__ void __launch_bounds__(kBpThreads)
 k_backproject(const RayGeom* __restrict__ rgp, VolDev vd, const float* __restrict__ r, float* __restrict__ g_out,
-              const float* __restrict__ h, double* partials, unsigned int* counter, double* out) {
+              const float* __restrict__ h, double* partials, unsigned int* counter, double* out, BpTable tab) {
     const RayGeom g = *rgp;
     long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     float acc = 0.0f;
     if (v < vd.n) {
         long long jk = v / vd.nx;
         int i = (int)(v - jk * vd.nx), j = (int)(jk % vd.ny), k = (int)(jk / vd.ny);
-        // Support box of voxel v in world coordinates and its detector footprint.
-        float cx = g.origin[0] + i * g.sp[0], cy = g.origin[1] + j * g.sp[1], cz = g.origin[2] + k * g.sp[2];
-        float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-            footprint(g, cx + ((c & 1) ? g.sp[0] : -g.sp[0]), cy + ((c & 2) ? g.sp[1] : -g.sp[1]),
-                      cz + ((c & 4) ? g.sp[2] : -g.sp[2]), umin, umax, vmin, vmax);
-        umin = fmaxf(umin, -1.0f);
-        vmin = fmaxf(vmin, -1.0f);
-        umax = fminf(umax, (float)g.nu);
-        vmax = fminf(vmax, (float)g.nv);
-        int u0 = max(0, (int)ceilf(umin)), u1 = min(g.nu - 1, (int)floorf(umax));
-        int w0 = max(0, (int)ceilf(vmin)), w1 = min(g.nv - 1, (int)floorf(vmax));
-        const float lo[3] = {(float)(i - 1), (float)(j - 1), (float)(k - 1)};
-        const float hi[3] = {(float)(i + 1), (float)(j + 1), (float)(k + 1)};
-        const float fi = (float)i, fj = (float)j, fk = (float)k;
-        for (int iv = w0; iv <= w1; ++iv) {
-            for (int iu = u0; iu <= u1; ++iu) {
-                float b[3], t0, t1;
-                ray_dir_index(g, iu, iv, b);
-                if (!ray_box(g.a, b, lo, hi, t0, t1)) continue;
-                int s0 = (int)fminf(fmaxf(ceilf(t0 / g.ds - 0.5f), 0.0f), 1.0e7f);
-                int s1 = (int)fminf(floorf(t1 / g.ds - 0.5f), 1.0e7f);
-                float wsum = 0.0f;
-                for (int s = s0; s <= s1; ++s) {
-                    float q[3];
-                    sample_pos(g, b, s, q);
-                    float wx = 1.0f - fabsf(q[0] - fi), wy = 1.0f - fabsf(q[1] - fj), wz = 1.0f - fabsf(q[2] - fk);
-                    if (wx > 0.0f && wy > 0.0f && wz > 0.0f) wsum = __fmaf_rn(wx * wy, wz, wsum);
-                }
-                acc = __fmaf_rn(wsum, __ldg(r + (long long)iv * g.nu + iu), acc);
-            }
+        if (tab.w) {  // fixed angle: stored weights, same pixel order and multiply-adds
+            const short4 fp = __ldg(tab.rect + v);
+            int slot = 0;
+            for (int iv = fp.y; iv < fp.y + fp.w; ++iv)
+                for (int iu = fp.x; iu < fp.x + fp.z; ++iu, ++slot)
+                    acc = __fmaf_rn(__ldg(tab.w + (long long)slot * vd.n + v), __ldg(r + (long long)iv * g.nu + iu),
+                                    acc);
+        } else {
+            int u0, u1, w0, w1;
+            voxel_footprint(g, i, j, k, u0, u1, w0, w1);
+            for (int iv = w0; iv <= w1; ++iv)
+                for (int iu = u0; iu <= u1; ++iu)
+                    acc = __fmaf_rn(pixel_weight(g, i, j, k, iu, iv), __ldg(r + (long long)iv * g.nu + iu), acc);
         }
         acc *= g.ds;
         if (g_out) g_out[v] = acc;
@@ -97,24 +126,69 @@ k_backproject(const RayGeom* __restrict__ rgp, VolDev vd, const float* __restric
     }
 }
 
+// Fixed-angle table, pass 1: each voxel's footprint rectangle, and the largest
+// footprint (slots) over the grid.
+__global__ void __launch_bounds__(kBpThreads) k_bp_rect(const RayGeom* __restrict__ rgp, VolDev vd, short4* rect,
+                                                         unsigned int* max_slots) {
+    const RayGeom g = *rgp;
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    unsigned int sz = 0;
+    if (v < vd.n) {
+        long long jk = v / vd.nx;
+        int i = (int)(v - jk * vd.nx), j = (int)(jk % vd.ny), k = (int)(jk / vd.ny);
+        int u0, u1, w0, w1;
+        voxel_footprint(g, i, j, k, u0, u1, w0, w1);
+        const int nu = max(0, u1 - u0 + 1), nv = max(0, w1 - w0 + 1);
+        rect[v] = make_short4((short)u0, (short)w0, (short)nu, (short)nv);
+        sz = (unsigned int)(nu * nv);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sz = max(sz, __shfl_xor_sync(0xffffffffu, sz, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(max_slots, sz);
+}
+
+// Pass 2: the weights, slot-major.
+__global__ void __launch_bounds__(kBpThreads) k_bp_fill(const RayGeom* __restrict__ rgp, VolDev vd,
+                                                         const short4* __restrict__ rect, float* w) {
+    const RayGeom g = *rgp;
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= vd.n) return;
+    long long jk = v / vd.nx;
+    int i = (int)(v - jk * vd.nx), j = (int)(jk % vd.ny), k = (int)(jk / vd.ny);
+    const short4 fp = rect[v];
+    int slot = 0;
+    for (int iv = fp.y; iv < fp.y + fp.w; ++iv)
+        for (int iu = fp.x; iu < fp.x + fp.z; ++iu, ++slot) w[(long long)slot * vd.n + v] = pixel_weight(g, i, j, k, iu, iv);
+}
+
 }  // namespace
+
+cudaError_t launch_bp_rect(Launcher& L, const VolDev& vd, const RayGeom* rg, short4* rect, unsigned int* max_slots) {
+    return L(k_bp_rect, dim3((unsigned)((vd.n + kBpThreads - 1) / kBpThreads)), dim3(kBpThreads), 0, rg, vd, rect,
+             max_slots);
+}
+
+cudaError_t launch_bp_fill(Launcher& L, const VolDev& vd, const RayGeom* rg, const short4* rect, float* w) {
+    return L(k_bp_fill, dim3((unsigned)((vd.n + kBpThreads - 1) / kBpThreads)), dim3(kBpThreads), 0, rg, vd, rect, w);
+}
 
 int backproject_blocks(const VolDev& vd) { return (int)((vd.n + kBpThreads - 1) / kBpThreads); }
 
 cudaError_t launch_backproject(Launcher& L, const VolDev& vd, const RayGeom* rg, const float* r, float* g_flat,
-                               const float* h, int K, double* partials, unsigned int* counter, double* out) {
+                               const float* h, int K, double* partials, unsigned int* counter, double* out,
+                               BpTable tab) {
     dim3 grid((unsigned)backproject_blocks(vd));
     dim3 block(kBpThreads);
     if (!h) K = 0;
     switch (K) {
-        case 0: return L(k_backproject<0>, grid, block, 0, rg, vd, r, g_flat, h, partials, counter, out);
-        case 1: return L(k_backproject<1>, grid, block, 0, rg, vd, r, g_flat, h, partials, counter, out);
-        case 2: return L(k_backproject<2>, grid, block, 0, rg, vd, r, g_flat, h, partials, counter, out);
-        case 3: return L(k_backproject<3>, grid, block, 0, rg, vd, r, g_flat, h, partials, counter, out);
-        case 4: return L(k_backproject<4>, grid, block, 0, rg, vd, r, g_flat, h, partials, counter, out);
-        case 5: return L(k_backproject<5>, grid, block, 0, rg, vd, r, g_flat, h, partials, counter, out);
-        case 6: return L(k_backproject<6>, grid, block, 0, rg, vd, r, g_flat, h, partials, counter, out);
-        case 7: return L(k_backproject<7>, grid, block, 0, rg, vd, r, g_flat, h, partials, counter, out);
+        case 0: return L(k_backproject<0>, grid, block, 0, rg, vd, r, g_flat, h, partials, counter, out, tab);
+        case 1: return L(k_backproject<1>, grid, block, 0, rg, vd, r, g_flat, h, partials, counter, out, tab);
+        case 2: return L(k_backproject<2>, grid, block, 0, rg, vd, r, g_flat, h, partials, counter, out, tab);
+        case 3: return L(k_backproject<3>, grid, block, 0, rg, vd, r, g_flat, h, partials, counter, out, tab);
+        case 4: return L(k_backproject<4>, grid, block, 0, rg, vd, r, g_flat, h, partials, counter, out, tab);
+        case 5: return L(k_backproject<5>, grid, block, 0, rg, vd, r, g_flat, h, partials, counter, out, tab);
+        case 6: return L(k_backproject<6>, grid, block, 0, rg, vd, r, g_flat, h, partials, counter, out, tab);
+        case 7: return L(k_backproject<7>, grid, block, 0, rg, vd, r, g_flat, h, partials, counter, out, tab);
     }
     return cudaErrorInvalidValue;
 }

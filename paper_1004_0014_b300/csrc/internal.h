@@ -115,12 +115,26 @@ cudaError_t launch_invert(Launcher& L, const ModelDev& m, const double* w_dev, f
 // r = p - a y - b with (a, b) = ab_dev[0..1].
 cudaError_t launch_residual(Launcher& L, const float* p, const float* y, int R, const double* ab_dev, float* r);
 
+// Fixed-angle table of the transpose (see backproject.cu): per voxel its
+// footprint rectangle (u0, w0, width, height), and the pixel weights slot-major
+// (slot s of voxel v at w[s * N + v]). Null w: weights computed on the fly.
+struct BpTable {
+    const short4* rect = nullptr;
+    const float* w = nullptr;
+};
+
 // P^T by voxel-driven gather. With h (K planes, unpadded) given, the per-voxel
 // values are never stored: out[k] = sum_v (P^T r)(v) h_k(v) (and g_flat may be
-// null); otherwise g_flat [N] receives P^T r.
+// null); otherwise g_flat [N] receives P^T r. With tab.w, the weights come from
+// a table built for rg's angle (bitwise the same result).
 cudaError_t launch_backproject(Launcher& L, const VolDev& vd, const RayGeom* rg, const float* r,
                                float* g_flat, const float* h, int K, double* partials,
-                               unsigned int* counter, double* out);
+                               unsigned int* counter, double* out, BpTable tab = {});
+
+// Fixed-angle table: rect [N] and the largest footprint into *max_slots (device,
+// zeroed by the caller), then the weights (max_slots x N floats).
+cudaError_t launch_bp_rect(Launcher& L, const VolDev& vd, const RayGeom* rg, short4* rect, unsigned int* max_slots);
+cudaError_t launch_bp_fill(Launcher& L, const VolDev& vd, const RayGeom* rg, const short4* rect, float* w);
 
 // Record msg as the calling thread's pr_last_error() text; returns code.
 int set_last_error(int code, const char* msg);

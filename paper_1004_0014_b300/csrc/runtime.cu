@@ -77,6 +77,12 @@ struct Model {
     int* order = nullptr;           // projector tile order
     int* order_w = nullptr;         // split projector's warp-tile order
     unsigned char* tlog = nullptr;  // per-trial choices of the last solve (kTrialLog bytes)
+    // fixed-angle transpose table (pr_fix_angle); bt_bytes counted in `bytes`
+    bool fixed = false;
+    double fixed_angle = 0.0;
+    short4* bt_rect = nullptr;
+    float* bt_w = nullptr;
+    size_t bt_bytes = 0;
     SplitScratch ss;                // split projector's scratch (order_w, parts, moments, counters)
     Support* sup = nullptr;         // where the warped volume can be nonzero
     SolveState* st_host = nullptr;  // pinned
@@ -239,7 +245,8 @@ void free_model(Model* m) {
     if (m->graph) cudaGraphDestroy(m->graph);
     void* bufs[] = {m->f0p, m->mean, m->U, m->fh, m->fpad, m->p, m->q, m->y, m->r, m->flat, m->hbuf,
                     m->partials, m->counter, m->st, m->wdev, m->out, m->rg, m->steps, m->order, m->sup,
-                    m->order_w, m->ss.part, m->ss.tile_mom, m->ss.group_mom, m->ss.ctr, m->tlog};
+                    m->order_w, m->ss.part, m->ss.tile_mom, m->ss.group_mom, m->ss.ctr, m->tlog,
+                    m->bt_rect, m->bt_w};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (m->st_host) cudaFreeHost(m->st_host);
@@ -415,6 +422,28 @@ int enqueue_solve(pr_ctx* c, Model* m, double angle, const pr_solve_opts* opts) 
     }
     CK(cudaGraphLaunch(m->exec, c->stream));
     return PR_OK;
+}
+
+// The fixed-angle transpose table of m if it was built for exactly this angle.
+BpTable bp_table(const Model* m, double angle) {
+    BpTable t;
+    if (m->fixed && m->bt_w && angle == m->fixed_angle) {
+        t.rect = m->bt_rect;
+        t.w = m->bt_w;
+    }
+    return t;
+}
+
+void drop_bp_table(pr_ctx* c, Model* m) {
+    if (m->bt_rect) cudaFree(m->bt_rect);
+    if (m->bt_w) cudaFree(m->bt_w);
+    m->bt_rect = nullptr;
+    m->bt_w = nullptr;
+    m->fixed = false;
+    std::lock_guard<std::mutex> lock(c->mu);
+    m->bytes -= m->bt_bytes;
+    c->used -= m->bt_bytes;
+    m->bt_bytes = 0;
 }
 
 int ensure_hbuf(Model* m) {
@@ -1130,6 +1159,65 @@ int pr_forward(pr_ctx* c, int id, const double* w, double angle, float* p_dev) {
     return PR_OK;
 }
 
+int pr_fix_angle(pr_ctx* c, int id, double angle, size_t* table_bytes) {
+    GET_MODEL(c, id, m);
+    CK(cudaStreamSynchronize(c->stream));
+    drop_bp_table(c, m);
+    if (table_bytes) *table_bytes = 0;
+    if (isnan(angle)) return PR_OK;  // NaN: back to weights computed per call
+    if (!isfinite(angle)) return fail(PR_EINVAL, "angle is not finite");
+    if (m->geom.nu > 32767 || m->geom.nv > 32767) return fail(PR_EINVAL, "detector too wide for the table");
+    const VolDev& vd = m->md.vd;
+    TRY(set_rg(c, m->rg, m->vol, m->geom, angle));
+    Launcher L;
+    L.stream = c->stream;
+    short4* rect = nullptr;
+    CK(cudaMalloc(&rect, (size_t)vd.n * sizeof(short4)));
+    unsigned int* slots_dev = reinterpret_cast<unsigned int*>(m->partials);
+    unsigned int slots = 0;
+    cudaError_t e = cudaMemsetAsync(slots_dev, 0, sizeof(unsigned int), c->stream);
+    if (!e) e = launch_bp_rect(L, vd, m->rg, rect, slots_dev);
+    if (!e) e = cudaMemcpyAsync(&slots, slots_dev, sizeof slots, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) {
+        cudaFree(rect);
+        return fail(PR_ECUDA, "fixed-angle footprints: %s", cudaGetErrorString(e));
+    }
+    const size_t need = (size_t)vd.n * sizeof(short4) + (size_t)slots * vd.n * sizeof(float);
+    {
+        std::lock_guard<std::mutex> lock(c->mu);
+        if (c->used + need > c->budget) {
+            cudaFree(rect);
+            return fail(PR_EADMIT, "fixed-angle table of %zu bytes exceeds the HBM budget", need);
+        }
+    }
+    float* w = nullptr;
+    if (slots > 0 && cudaMalloc(&w, (size_t)slots * vd.n * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(rect);
+        return fail(PR_ENOMEM, "fixed-angle table of %zu bytes: allocation failed", need);
+    }
+    if (slots > 0) e = launch_bp_fill(L, vd, m->rg, rect, w);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) {
+        cudaFree(rect);
+        if (w) cudaFree(w);
+        return fail(PR_ECUDA, "fixed-angle weights: %s", cudaGetErrorString(e));
+    }
+    m->bt_rect = rect;
+    m->bt_w = w;
+    m->fixed = w != nullptr;
+    m->fixed_angle = angle;
+    {
+        std::lock_guard<std::mutex> lock(c->mu);
+        m->bt_bytes = need;
+        m->bytes += need;
+        c->used += need;
+    }
+    if (table_bytes) *table_bytes = need;
+    return PR_OK;
+}
+
 int pr_vjp(pr_ctx* c, int id, const double* w, double angle, const float* grad_p_dev, double* grad_w) {
     GET_MODEL(c, id, m);
     if (!w || !grad_p_dev || !grad_w) return fail(PR_EINVAL, "null argument");
@@ -1139,7 +1227,8 @@ int pr_vjp(pr_ctx* c, int id, const double* w, double angle, const float* grad_p
     Launcher L;
     L.stream = c->stream;
     CK(launch_warp(L, m->md, m->wdev, kWarpFlatFH, nullptr, nullptr, m->hbuf));
-    CK(launch_backproject(L, m->md.vd, m->rg, grad_p_dev, nullptr, m->hbuf, m->K, m->partials, m->counter, m->out));
+    CK(launch_backproject(L, m->md.vd, m->rg, grad_p_dev, nullptr, m->hbuf, m->K, m->partials, m->counter, m->out,
+                          bp_table(m, angle)));
     double buf[8];
     CK(cudaMemcpyAsync(buf, m->out, sizeof(double) * m->K, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -1177,7 +1266,7 @@ int pr_cost_grad(pr_ctx* c, int id, const float* y_dev, double angle, const doub
         CK(launch_residual(L, m->p, y_dev, m->R, m->out + 8, m->r));
         CK(cudaMemcpyAsync(res, m->out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         CK(launch_backproject(L, m->md.vd, m->rg, m->r, nullptr, m->hbuf, m->K, m->partials, m->counter,
-                              m->out + 1));
+                              m->out + 1, bp_table(m, angle)));
         CK(cudaMemcpyAsync(res + 1, m->out + 1, sizeof(double) * m->K, cudaMemcpyDeviceToHost, c->stream));
     }
     if (p_dev) CK(cudaMemcpyAsync(p_dev, m->p, (size_t)m->R * 4, cudaMemcpyDeviceToDevice, c->stream));
@@ -1263,7 +1352,7 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
                 break;
             case PR_KERNEL_BACKPROJECT:
                 err = launch_backproject(L, m->md.vd, m->rg, m->p, nullptr, m->hbuf, m->K, m->partials, m->counter,
-                                         m->out);
+                                         m->out, bp_table(m, angle));
                 break;
             case PR_KERNEL_WARP_F: err = launch_warp(L, m->md, m->st->w, kWarpFPad, m->fpad, nullptr, nullptr); break;
             case PR_KERNEL_PROJECT_F:
