@@ -494,9 +494,9 @@ def run_ours(args):
     share_warp = (1 + trials_per_solve) * kern["warp_fh"] / per_solve_ms
     proj_tflops = flops / (kern["project_fh"] / 1000.0) / 1e12
     bytes_proj = N * 4 * nch + R * 4 * (1 + Km)
-    roofline = {"kernel": "k_project<%d> (f, h_1..h_%d)" % (nch, Km), "bound": "alu", "achieved": proj_tflops,
+    roofline = {"kernel": "k_project_split<%d> (f, h_1..h_%d)" % (nch, Km), "bound": "alu", "achieved": proj_tflops,
                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": proj_tflops / fp32_peak,
-                "traffic": recorded_traffic("k_project<4>", "project.cu") if (Km == 3 and not bf16) else None,
+                "traffic": recorded_traffic("k_project_split<4>", "project.cu") if (Km == 3 and not bf16) else None,
                 "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (FMA peak)" % sm_mhz,
                 "samples_per_launch": samples, "flops_per_sample": flops_per_sample(nch),
                 "algorithmic_flops_per_launch": flops, "share_of_solve": share_proj,
