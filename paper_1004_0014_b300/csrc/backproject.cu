@@ -88,7 +88,19 @@ k_backproject(const RayGeom* __restrict__ rgp, VolDev vd, const float* __restric
     const RayGeom g = *rgp;
     long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     float acc = 0.0f;
-    if (v < vd.n) {
+    // Contracted with h and not stored: a voxel whose h_k are all zero (air,
+    // away from the warped image's edges) adds nothing, so its footprint is
+    // not visited.
+    bool needed = v < vd.n;
+    if constexpr (K > 0) {
+        if (needed && !g_out) {
+            bool any = false;
+#pragma unroll
+            for (int m = 0; m < K; ++m) any = any || __ldg(h + m * vd.n + v) != 0.0f;
+            needed = any;
+        }
+    }
+    if (needed) {
         long long jk = v / vd.nx;
         int i = (int)(v - jk * vd.nx), j = (int)(jk % vd.ny), k = (int)(jk / vd.ny);
         if (tab.w) {  // fixed angle: stored weights, same pixel order and multiply-adds
@@ -106,8 +118,8 @@ k_backproject(const RayGeom* __restrict__ rgp, VolDev vd, const float* __restric
                     acc = __fmaf_rn(pixel_weight(g, i, j, k, iu, iv), __ldg(r + (long long)iv * g.nu + iu), acc);
         }
         acc *= g.ds;
-        if (g_out) g_out[v] = acc;
     }
+    if (g_out && v < vd.n) g_out[v] = acc;
     if constexpr (K > 0) {
         double d[K];
 #pragma unroll

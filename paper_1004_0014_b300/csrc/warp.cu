@@ -31,43 +31,15 @@ struct WarpArgs {
 
 __device__ __forceinline__ float lerp(float a, float b, float t) { return __fmaf_rn(t, b - a, a); }
 
+// DVF synthesis, pull-back warp and (kH) h_k for the four consecutive voxels
+// v0..v0+3 whose mean (mx) and eigenvector (u) values are already in registers.
 template <int K, int MODE, typename TS>
-__global__ void __launch_bounds__(kWarpThreads) k_warp(WarpArgs<TS> A) {
+__device__ __forceinline__ void warp4(const WarpArgs<TS>& A, long long v0, const float (&w)[K],
+                                      const float (&mx)[3][4], const float (&u)[K][3][4]) {
     constexpr bool kH = (MODE == kWarpFH || MODE == kWarpFlatFH);
     constexpr int kNch = K <= 3 ? 4 : (K <= 5 ? 6 : 8);
     const VolDev& vd = A.vd;
-    long long v0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * 4;
-    if (v0 >= vd.n) return;
     const long long n = vd.n;
-
-    float w[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) w[k] = (float)A.w[k];
-
-    // Fields of the four voxels: mean (3) and eigenvectors (3K).
-    float mx[3][4];
-    float u[K][3][4];
-    const bool full = A.vec_ok && (v0 + 3 < n);
-    if (full) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) ld4(A.mean + c * n + v0, mx[c]);
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) ld4(A.U + (3LL * k + c) * n + v0, u[k][c]);
-    } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            long long v = v0 + e < n ? v0 + e : n - 1;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) mx[c][e] = __ldg(A.mean + c * n + v);
-#pragma unroll
-            for (int k = 0; k < K; ++k)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) u[k][c][e] = ld_val(A.U + (3LL * k + c) * n + v);
-        }
-    }
-
     long long jk = v0 / vd.nx;
     int i = (int)(v0 - jk * vd.nx);
     int j = (int)(jk % vd.ny);
@@ -155,6 +127,44 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp(WarpArgs<TS> A) {
             }
         }
     }
+}
+
+template <int K, int MODE, typename TS>
+__global__ void __launch_bounds__(kWarpThreads) k_warp(WarpArgs<TS> A) {
+    const VolDev& vd = A.vd;
+    long long v0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * 4;
+    if (v0 >= vd.n) return;
+    const long long n = vd.n;
+
+    float w[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) w[k] = (float)A.w[k];
+
+    // Fields of the four voxels: mean (3) and eigenvectors (3K).
+    float mx[3][4];
+    float u[K][3][4];
+    const bool full = A.vec_ok && (v0 + 3 < n);
+    if (full) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ld4(A.mean + c * n + v0, mx[c]);
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ld4(A.U + (3LL * k + c) * n + v0, u[k][c]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            long long v = v0 + e < n ? v0 + e : n - 1;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) mx[c][e] = __ldg(A.mean + c * n + v);
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) u[k][c][e] = ld_val(A.U + (3LL * k + c) * n + v);
+        }
+    }
+
+    warp4<K, MODE, TS>(A, v0, w, mx, u);
 }
 
 template <int K, typename TS>
