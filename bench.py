@@ -232,45 +232,6 @@ def flops_per_sample(nch: int) -> int:
     return 2 * 8 * nch + 19 + 6
 
 
-def projector_samples(vol, geom, angle, f0, mean, U, w):
-    """Samples the projector takes at gantry angle `angle` and coefficients w:
-    per ray, the source-anchored samples inside the support box of the warped
-    volume (the nonzero box of f0 dilated by two cells and by the largest
-    displacement w allows), the same clipping as the kernel, in float64."""
-    nzk, nzj, nzi = np.nonzero(f0)
-    if nzk.size == 0:
-        return 0
-    sp = vol.spacing
-    n = np.array([vol.nx, vol.ny, vol.nz], float)
-    lo = np.array([nzi.min(), nzj.min(), nzk.min()], float)
-    hi = np.array([nzi.max(), nzj.max(), nzk.max()], float)
-    d = np.abs(mean).reshape(3, -1).max(axis=1)
-    for k in range(U.shape[0]):
-        d = d + abs(w[k]) * np.abs(U[k]).reshape(3, -1).max(axis=1)
-    d = d / sp * 1.01 + 0.01
-    lo = np.maximum(-1.0, lo - 2.0 - d)
-    hi = np.minimum(n, hi + 2.0 + d)
-    st, ct = math.sin(angle), math.cos(angle)
-    S = np.array([geom.sad * st, -geom.sad * ct, 0.0])
-    eh, uh, vh = np.array([-st, ct, 0.0]), np.array([ct, st, 0.0]), np.array([0.0, 0.0, 1.0])
-    iv, iu = np.meshgrid(np.arange(geom.nv), np.arange(geom.nu), indexing="ij")
-    su = (iu - 0.5 * (geom.nu - 1)) * geom.du
-    sv = (iv - 0.5 * (geom.nv - 1)) * geom.dv
-    dirs = geom.sdd * eh[None, None, :] + su[..., None] * uh + sv[..., None] * vh
-    dirs /= np.linalg.norm(dirs, axis=-1, keepdims=True)
-    a = (S - vol.origin) / sp
-    b = dirs / sp
-    with np.errstate(divide="ignore", invalid="ignore"):
-        ta = (lo - a) / b
-        tb = (hi - a) / b
-    t0 = np.maximum(0.0, np.nanmax(np.minimum(ta, tb), axis=-1))
-    t1 = np.nanmin(np.maximum(ta, tb), axis=-1)
-    s_lo = np.maximum(0, np.ceil(t0 / geom.ds - 0.5))
-    s_hi = np.floor(t1 / geom.ds - 0.5)
-    cnt = np.where(t1 > t0, np.maximum(0, s_hi - s_lo + 1), 0)
-    return int(cnt.sum())
-
-
 def recorded_traffic(kernel: str, source: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, only
     if the kernel's source file is unchanged since the capture (else None)."""
@@ -486,7 +447,9 @@ def run_ours(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
     sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
     fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    samples = projector_samples(vol, geom, angles[W], f0, mean, U, w_start)
+    # samples the projector evaluates at the timed frame: support box and brick
+    # trace, counted by the library with the kernel's own clipping
+    samples = ctx.count_samples(mid, angles[W], w_start)
     flops = samples * flops_per_sample(nch)
     per_solve_ms = elapsed_ms / K
     trials_per_solve = trials / K

@@ -320,6 +320,13 @@ int pr_tumor(pr_ctx* ctx, int model_id, const double* w, double tol, int max_ite
  * PR_ENOMODEL, PR_ECUDA. */
 int pr_trial_log(pr_ctx* ctx, int model_id, unsigned char* out, int cap, int* n);
 
+/* Measurement (no counterpart in the paper): the number of ray samples the
+ * solver-pass projector evaluates for the model at angle_rad and coefficients
+ * w (K doubles, host), summed over rays: each ray's samples inside the warped
+ * volume's support box, less those at either end that the brick levels show
+ * to be exactly zero. Synchronous. Errors: PR_EINVAL, PR_ENOMODEL, PR_ECUDA. */
+int pr_count_samples(pr_ctx* ctx, int model_id, double angle_rad, const double* w, long long* count);
+
 /* Section 5's fixed-angle geometry (fluoroscopy: the gantry does not move,
  * so P is the same matrix for every frame). Builds the model's table of the
  * transpose at angle_rad: for each voxel its detector footprint and the weight

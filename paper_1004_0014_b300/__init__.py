@@ -165,6 +165,10 @@ class Context:
     def tumor(self, mid: int, w, tol: float = 1e-6, max_iter: int = 100):
         return capi.pr_tumor(self._ctx, mid, w, tol, max_iter)
 
+    def count_samples(self, mid: int, angle_rad: float, w) -> int:
+        """Ray samples the solver-pass projector evaluates at this angle and w."""
+        return capi.pr_count_samples(self._ctx, mid, angle_rad, w)
+
     def fix_angle(self, mid: int, angle_rad: float) -> int:
         """Fixed-angle transpose table for the model at this angle (NaN drops it)."""
         return capi.pr_fix_angle(self._ctx, mid, angle_rad)

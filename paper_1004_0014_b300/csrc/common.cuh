@@ -69,11 +69,14 @@ struct Support {
 
 // Sample box (index space) of a ray march over the warped volume at
 // coefficients w; returns false when the volume is zero everywhere.
+// margin (nullable) receives the largest per-axis reach 2 + d_c (voxels): a
+// sample whose cell is farther than that from every nonzero f0 voxel is 0.
 __device__ __forceinline__ bool support_box(const Support& s, const VolDev& vd, const double* w, int K,
-                                            float lo[3], float hi[3]) {
+                                            float lo[3], float hi[3], float* margin = nullptr) {
     const float inv[3] = {vd.inv_dx, vd.inv_dy, vd.inv_dz};
     const float n[3] = {(float)vd.nx, (float)vd.ny, (float)vd.nz};
     bool any = true;
+    float reach = 0.0f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         float d = __uint_as_float(s.mean_max[c]);
@@ -81,8 +84,10 @@ __device__ __forceinline__ bool support_box(const Support& s, const VolDev& vd, 
         d = d * inv[c] * 1.01f + 0.01f;  // margin for float rounding of x and of the bounds
         lo[c] = fmaxf(-1.0f, (float)s.lo[c] - 2.0f - d);
         hi[c] = fminf(n[c], (float)s.hi[c] + 2.0f + d);
+        reach = fmaxf(reach, 2.0f + d);
         any = any && (s.lo[c] <= s.hi[c]) && (lo[c] < hi[c]);
     }
+    if (margin) *margin = reach;
     return any;
 }
 

@@ -52,11 +52,27 @@ cudaError_t launch_begin(Launcher& L, const float* y, int R, SolveState* st, dou
 // partials and counter drive the fused reduction and the controller.
 // Optional clipping of the ray march to the support of a model's warped
 // volume: sup (device) and the coefficients w (device, K doubles) it was warped at.
+// lev (nullable): per 4^3-voxel brick of the grid (bn[0] x bn[1] x bn[2], x
+// fastest) the Chebyshev distance in bricks to the nearest brick holding a
+// nonzero f0 voxel (0: the brick holds one; capped at 255), so that rays skip
+// the samples at either end that lie too far from the body to be nonzero.
 struct SupportRef {
     const Support* sup = nullptr;
     const double* w = nullptr;
     int K = 0;
+    const unsigned char* lev = nullptr;
+    int bn[3] = {0, 0, 0};
 };
+
+// Brick occupancy of an unpadded f0 (device, float32): occ[brick] = 1 where the
+// brick holds a nonzero voxel (occ zeroed by the caller; bricks of 4^3 voxels).
+cudaError_t launch_brick_occ(Launcher& L, const VolDev& vd, const float* f0, unsigned char* occ);
+
+// Exact per-ray sample count of the solver-pass projector (after the support box
+// and the brick-level trace) at coefficients w (device doubles) into *count
+// (device, zeroed by the caller).
+cudaError_t launch_count_samples(Launcher& L, const VolDev& vd, const RayGeom* rg, int nu, int nv, SupportRef sup,
+                                 unsigned long long* count);
 
 // Scratch of the split-ray solver-pass projector (one per model; see
 // k_project_split): warp-tile order, per-part sums, tile and group moments,

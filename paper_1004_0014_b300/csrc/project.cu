@@ -138,6 +138,42 @@ __device__ __forceinline__ int cell(float q, int n, float& t) {
     return i;
 }
 
+// Brick-level trace of a ray's sample range. Level k of the brick holding a
+// point means every nonzero f0 voxel is at least 4 (k - 1) voxels away from it
+// (Chebyshev), and the warped f and every h_k at a sample can be nonzero only
+// within `margin` (support_box) of a nonzero f0 voxel. So from each end of
+// [s_lo, s_hi] the samples with 4 (k - 1) > margin are skipped, advancing by as
+// many samples as the slack allows (a sample moves at most ds max|b_c| voxels).
+// Only exact zeros are skipped; at most kTraceSteps look-ups per end.
+constexpr int kTraceSteps = 32;
+
+__device__ __forceinline__ float brick_slack(const RayGeom& g, const float b[3], int s, const SupportRef& sr) {
+    float q[3];
+    sample_pos(g, b, s, q);
+    const int bx = min(max((int)floorf(q[0] * 0.25f), 0), sr.bn[0] - 1);
+    const int by = min(max((int)floorf(q[1] * 0.25f), 0), sr.bn[1] - 1);
+    const int bz = min(max((int)floorf(q[2] * 0.25f), 0), sr.bn[2] - 1);
+    const int k = __ldg(sr.lev + (bz * sr.bn[1] + by) * sr.bn[0] + bx);
+    return 4.0f * (float)(k - 1);
+}
+
+__device__ __forceinline__ void trace_range(const RayGeom& g, const float b[3], const SupportRef& sr, float margin,
+                                            int& s_lo, int& s_hi) {
+    if (!sr.lev || s_lo > s_hi) return;
+    const float step = g.ds * fmaxf(fabsf(b[0]), fmaxf(fabsf(b[1]), fabsf(b[2])));
+    if (!(step > 1.0e-6f)) return;
+    for (int it = 0; it < kTraceSteps && s_lo <= s_hi; ++it) {
+        const float slack = brick_slack(g, b, s_lo, sr) - margin;
+        if (!(slack > 0.0f)) break;
+        s_lo += max(1, (int)fminf(slack / step, 1.0e6f));
+    }
+    for (int it = 0; it < kTraceSteps && s_lo <= s_hi; ++it) {
+        const float slack = brick_slack(g, b, s_hi, sr) - margin;
+        if (!(slack > 0.0f)) break;
+        s_hi -= max(1, (int)fminf(slack / step, 1.0e6f));
+    }
+}
+
 // Sample accumulation that keeps the eight corners of the last trilinear cell
 // in registers: consecutive samples 1 mm apart often fall in the same 2-2.5 mm
 // cell, and then a lane that stays in its cell does not touch L1 for that
@@ -470,7 +506,8 @@ __global__ void __launch_bounds__(kProjThreads, NCH == 4 ? 4 : 1) k_project(Proj
     ray_dir_index(g, valid ? iu : 0, valid ? iv : 0, b);
     float lo[3] = {-1.0f, -1.0f, -1.0f}, hi[3] = {g.nmax[0], g.nmax[1], g.nmax[2]};
     bool nonzero = true;
-    if (A.sup.sup && A.sup.w) nonzero = support_box(*A.sup.sup, A.vd, A.sup.w, A.sup.K, lo, hi);
+    float margin = 0.0f;
+    if (A.sup.sup && A.sup.w) nonzero = support_box(*A.sup.sup, A.vd, A.sup.w, A.sup.K, lo, hi, &margin);
     float t0, t1;
     int s_lo = 0x7fffffff, s_hi = -1;
     if (valid && nonzero && ray_box(g.a, b, lo, hi, t0, t1)) {
@@ -478,6 +515,8 @@ __global__ void __launch_bounds__(kProjThreads, NCH == 4 ? 4 : 1) k_project(Proj
         // conversion and the loop counter far from overflow.
         s_lo = (int)fminf(fmaxf(ceilf(t0 / g.ds - 0.5f), 0.0f), (float)kMaxSamples);
         s_hi = (int)fminf(floorf(t1 / g.ds - 0.5f), (float)kMaxSamples);
+        if (A.sup.w) trace_range(g, b, A.sup, margin, s_lo, s_hi);
+        if (s_lo > s_hi) s_lo = 0x7fffffff, s_hi = -1;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -711,7 +750,8 @@ __global__ void __launch_bounds__(kSplitThreads, NCH == 4 ? 4 : 2) k_project_spl
 
     float lo[3] = {-1.0f, -1.0f, -1.0f}, hi[3] = {g.nmax[0], g.nmax[1], g.nmax[2]};
     bool nonzero = true;
-    if (A.sup.sup && A.sup.w) nonzero = support_box(*A.sup.sup, A.vd, A.sup.w, A.sup.K, lo, hi);
+    float margin = 0.0f;
+    if (A.sup.sup && A.sup.w) nonzero = support_box(*A.sup.sup, A.vd, A.sup.w, A.sup.K, lo, hi, &margin);
 
     for (;;) {
         unsigned int item = 0;
@@ -731,6 +771,8 @@ __global__ void __launch_bounds__(kSplitThreads, NCH == 4 ? 4 : 2) k_project_spl
         if (valid && nonzero && ray_box(g.a, b, lo, hi, t0, t1)) {
             s_lo = (int)fminf(fmaxf(ceilf(t0 / g.ds - 0.5f), 0.0f), (float)kMaxSamples);
             s_hi = (int)fminf(floorf(t1 / g.ds - 0.5f), (float)kMaxSamples);
+            if (A.sup.w) trace_range(g, b, A.sup, margin, s_lo, s_hi);
+            if (s_lo > s_hi) s_lo = 0x7fffffff, s_hi = -1;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -1046,6 +1088,43 @@ __global__ void k_support_init(Support* s) {
     }
 }
 
+__global__ void __launch_bounds__(256) k_brick_occ(VolDev vd, const float* __restrict__ f0, unsigned char* occ, int bnx,
+                                                    int bny) {
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < vd.n; v += (long long)gridDim.x * blockDim.x) {
+        if (f0[v] != 0.0f) {
+            long long jk = v / vd.nx;
+            const int i = (int)(v - jk * vd.nx), j = (int)(jk % vd.ny), k = (int)(jk / vd.ny);
+            occ[((k >> 2) * bny + (j >> 2)) * bnx + (i >> 2)] = 1;
+        }
+    }
+}
+
+// One thread per ray: the projector's own clipping (support box, then the
+// brick trace), summed as 64-bit counts.
+__global__ void __launch_bounds__(256) k_count_samples(VolDev vd, const RayGeom* __restrict__ rgp, int nu, int nv,
+                                                       SupportRef sr, unsigned long long* count) {
+    const RayGeom g = *rgp;
+    float lo[3] = {-1.0f, -1.0f, -1.0f}, hi[3] = {g.nmax[0], g.nmax[1], g.nmax[2]};
+    float margin = 0.0f;
+    bool nonzero = true;
+    if (sr.sup && sr.w) nonzero = support_box(*sr.sup, vd, sr.w, sr.K, lo, hi, &margin);
+    unsigned long long c = 0;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < nu * nv && nonzero) {
+        float b[3], t0, t1;
+        ray_dir_index(g, r % nu, r / nu, b);
+        if (ray_box(g.a, b, lo, hi, t0, t1)) {
+            int s_lo = (int)fminf(fmaxf(ceilf(t0 / g.ds - 0.5f), 0.0f), (float)kMaxSamples);
+            int s_hi = (int)fminf(floorf(t1 / g.ds - 0.5f), (float)kMaxSamples);
+            if (sr.w) trace_range(g, b, sr, margin, s_lo, s_hi);
+            if (s_hi >= s_lo) c = (unsigned long long)(s_hi - s_lo + 1);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
 __global__ void __launch_bounds__(256) k_support_box(VolDev vd, const float* __restrict__ f0, Support* s) {
     int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, hi[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < vd.n;
@@ -1080,6 +1159,16 @@ __global__ void __launch_bounds__(256) k_maxabs(const float* __restrict__ x, lon
 }
 
 }  // namespace
+
+cudaError_t launch_brick_occ(Launcher& L, const VolDev& vd, const float* f0, unsigned char* occ) {
+    const int bnx = (vd.nx + 3) / 4, bny = (vd.ny + 3) / 4;
+    return L(k_brick_occ, dim3(148 * 8), dim3(256), 0, vd, f0, occ, bnx, bny);
+}
+
+cudaError_t launch_count_samples(Launcher& L, const VolDev& vd, const RayGeom* rg, int nu, int nv, SupportRef sup,
+                                 unsigned long long* count) {
+    return L(k_count_samples, dim3((unsigned)((nu * nv + 255) / 256)), dim3(256), 0, vd, rg, nu, nv, sup, count);
+}
 
 cudaError_t launch_support_init(Launcher& L, Support* sup) { return L(k_support_init, dim3(1), dim3(32), 0, sup); }
 

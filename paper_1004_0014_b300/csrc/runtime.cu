@@ -85,6 +85,8 @@ struct Model {
     size_t bt_bytes = 0;
     SplitScratch ss;                // split projector's scratch (order_w, parts, moments, counters)
     Support* sup = nullptr;         // where the warped volume can be nonzero
+    unsigned char* lev = nullptr;   // brick levels of f0 (see SupportRef)
+    int bn[3] = {0, 0, 0};
     SolveState* st_host = nullptr;  // pinned
     size_t bytes = 0;
     // graph
@@ -228,6 +230,60 @@ RayGeom make_rg(const pr_volume_desc& v, const pr_geometry& g, double th) {
     return r;
 }
 
+// Brick levels of f0 (already in m->flat, unpadded): occupancy on the device,
+// then a multi-source breadth-first search over the 26 neighbours on the host
+// (level = Chebyshev distance in bricks to an occupied brick, capped at 255).
+cudaError_t make_brick_levels(Launcher& L, Model* m, cudaStream_t s) {
+    const size_t nb = (size_t)m->bn[0] * m->bn[1] * m->bn[2];
+    cudaError_t e = cudaMemsetAsync(m->lev, 0, nb, s);
+    if (!e) e = launch_brick_occ(L, m->md.vd, m->flat, m->lev);
+    std::vector<unsigned char> lev(nb);
+    if (!e) e = cudaMemcpyAsync(lev.data(), m->lev, nb, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return e;
+    std::vector<int> q;
+    q.reserve(nb);
+    for (size_t b = 0; b < nb; ++b) {
+        if (lev[b]) {
+            lev[b] = 0;
+            q.push_back((int)b);
+        } else {
+            lev[b] = 255;
+        }
+    }
+    const int bx = m->bn[0], by = m->bn[1], bz = m->bn[2];
+    for (size_t h = 0; h < q.size(); ++h) {
+        const int b = q[h], x = b % bx, y = (b / bx) % by, z = b / (bx * by);
+        const int next = lev[(size_t)b] + 1;
+        if (next >= 255) continue;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int X = x + dx, Y = y + dy, Z = z + dz;
+                    if (X < 0 || Y < 0 || Z < 0 || X >= bx || Y >= by || Z >= bz) continue;
+                    const size_t nbi = ((size_t)Z * by + Y) * bx + X;
+                    if (lev[nbi] > next) {
+                        lev[nbi] = (unsigned char)next;
+                        q.push_back((int)nbi);
+                    }
+                }
+    }
+    e = cudaMemcpyAsync(m->lev, lev.data(), nb, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaStreamSynchronize(s);  // lev (host) lives until the copy is done
+    return e;
+}
+
+// The projector's support description of model m at coefficients w (device).
+SupportRef sref(const Model* m, const double* w) {
+    SupportRef r;
+    r.sup = m->sup;
+    r.w = w;
+    r.K = m->K;
+    r.lev = m->lev;
+    for (int c = 0; c < 3; ++c) r.bn[c] = m->bn[c];
+    return r;
+}
+
 Model* find(pr_ctx* c, int id) {
     auto it = c->models.find(id);
     return it == c->models.end() ? nullptr : it->second;
@@ -246,7 +302,7 @@ void free_model(Model* m) {
     void* bufs[] = {m->f0p, m->mean, m->U, m->fh, m->fpad, m->p, m->q, m->y, m->r, m->flat, m->hbuf,
                     m->partials, m->counter, m->st, m->wdev, m->out, m->rg, m->steps, m->order, m->sup,
                     m->order_w, m->ss.part, m->ss.tile_mom, m->ss.group_mom, m->ss.ctr, m->tlog,
-                    m->bt_rect, m->bt_w};
+                    m->bt_rect, m->bt_w, m->lev};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (m->st_host) cudaFreeHost(m->st_host);
@@ -282,7 +338,8 @@ size_t model_bytes(const pr_volume_desc& v, const pr_geometry& g, int K, int sto
            sizeof(RayGeom) + 16 + (size_t)project_blocks(g.nu, g.nv) * sizeof(int) + sizeof(Support) +
            (size_t)split_tiles(g.nu, g.nv) * sizeof(int) + split_part_floats(g.nu, g.nv, (int)nch) * 4 +
            ((size_t)split_tiles(g.nu, g.nv) + split_groups(g.nu, g.nv)) * kProjMom * 8 +
-           split_counters(g.nu, g.nv) * 4 + kTrialLog;
+           split_counters(g.nu, g.nv) * 4 + kTrialLog +
+           (size_t)((v.nx + 3) / 4) * ((v.ny + 3) / 4) * ((v.nz + 3) / 4);
 }
 
 SolveParams make_params(const Model* m, double angle, const pr_solve_opts* o) {
@@ -341,7 +398,7 @@ int build_graph(pr_ctx* c, Model* m) {
     CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
     CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
-                      m->partials, m->counter, kPhaseInit, m->hloop, 1, SupportRef{m->sup, st->wt, m->K}, &m->ss));
+                      m->partials, m->counter, kPhaseInit, m->hloop, 1, sref(m, st->wt), &m->ss));
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = m->hloop;
@@ -353,7 +410,7 @@ int build_graph(pr_ctx* c, Model* m) {
     B.graph = cp.conditional.phGraph_out[0];
     CK(launch_warp(B, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
     CK(launch_project(B, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
-                      m->partials, m->counter, kPhaseTrial, m->hloop, 1, SupportRef{m->sup, st->wt, m->K}, &m->ss));
+                      m->partials, m->counter, kPhaseTrial, m->hloop, 1, sref(m, st->wt), &m->ss));
     L.last = cond;
     CK(launch_tumor(L, m->md, st->w, 0.0, 0, &st->prm, st->tumor, &st->tumor_steps));
     CK(cudaGraphInstantiate(&m->exec, m->graph, 0));
@@ -369,7 +426,7 @@ int host_loop(pr_ctx* c, Model* m, int opt_max_iters, int opt_max_bt) {
     CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
     CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
-                      m->partials, m->counter, kPhaseInit, 0, 0, SupportRef{m->sup, st->wt, m->K}, &m->ss));
+                      m->partials, m->counter, kPhaseInit, 0, 0, sref(m, st->wt), &m->ss));
     long long guard = 0, bound = (long long)(opt_max_iters + 1) * (opt_max_bt + 1) + 2;
     for (;;) {
         CK(cudaMemcpyAsync(&m->st_host->running, &st->running, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -378,7 +435,7 @@ int host_loop(pr_ctx* c, Model* m, int opt_max_iters, int opt_max_bt) {
         if (++guard > bound) return fail(PR_ETIMEOUT, "host loop exceeded its trial bound");
         CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
         CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y,
-                          st, m->partials, m->counter, kPhaseTrial, 0, 0, SupportRef{m->sup, st->wt, m->K}, &m->ss));
+                          st, m->partials, m->counter, kPhaseTrial, 0, 0, sref(m, st->wt), &m->ss));
         }
     CK(launch_tumor(L, m->md, st->w, 0.0, 0, &st->prm, st->tumor, &st->tumor_steps));
     return PR_OK;
@@ -546,7 +603,7 @@ int add_solve_nodes(cudaGraph_t g, Model* m, const cudaGraphNode_t* dep, const f
     CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
     CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
-                      m->partials, m->counter, kPhaseInit, h, 1, SupportRef{m->sup, st->wt, m->K}, &m->ss));
+                      m->partials, m->counter, kPhaseInit, h, 1, sref(m, st->wt), &m->ss));
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
@@ -558,7 +615,7 @@ int add_solve_nodes(cudaGraph_t g, Model* m, const cudaGraphNode_t* dep, const f
     B.graph = cp.conditional.phGraph_out[0];
     CK(launch_warp(B, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
     CK(launch_project(B, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
-                      m->partials, m->counter, kPhaseTrial, h, 1, SupportRef{m->sup, st->wt, m->K}, &m->ss));
+                      m->partials, m->counter, kPhaseTrial, h, 1, sref(m, st->wt), &m->ss));
     L.last = cond;
     CK(launch_tumor(L, m->md, st->w, 0.0, 0, &st->prm, st->tumor, &st->tumor_steps));
     CK(cudaGraphAddMemcpyNode1D(&nr, g, &L.last, 1, res_dst, st, sizeof(SolveState), cudaMemcpyDeviceToDevice));
@@ -847,6 +904,8 @@ int pr_load_model(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
     A(&m->ss.ctr, split_counters(geom->nu, geom->nv) * 4);
     m->ss.order = m->order_w;
     A(&m->tlog, kTrialLog);
+    m->bn[0] = (vol->nx + 3) / 4, m->bn[1] = (vol->ny + 3) / 4, m->bn[2] = (vol->nz + 3) / 4;
+    A(&m->lev, (size_t)m->bn[0] * m->bn[1] * m->bn[2]);
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&m->st_host, sizeof(SolveState), cudaHostAllocDefault);
     if (e != cudaSuccess) {
         free_model(m);
@@ -889,6 +948,7 @@ int pr_load_model(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
         L.stream = s;
         if ((e = launch_support_init(L, m->sup))) break;
         if ((e = launch_support_box(L, vd, m->flat, m->sup))) break;
+        if ((e = make_brick_levels(L, m, s))) break;
         for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = launch_maxabs(L, m->mean + (size_t)c * n, (long long)n, &m->sup->mean_max[c]);
         if (e) break;
         if ((e = launch_pad(L, vd, m->flat, m->fpad))) break;
@@ -1154,8 +1214,25 @@ int pr_forward(pr_ctx* c, int id, const double* w, double angle, float* p_dev) {
     L.stream = c->stream;
     CK(launch_warp(L, m->md, m->wdev, kWarpFPad, m->fpad, nullptr, nullptr));
     CK(launch_project(L, m->md.vd, m->fpad, 1, 0, m->rg, m->order, m->geom.nu, m->geom.nv, p_dev, nullptr, nullptr, nullptr,
-                      nullptr, nullptr, kPhaseNone, 0, 0, SupportRef{m->sup, m->wdev, m->K}));
+                      nullptr, nullptr, kPhaseNone, 0, 0, sref(m, m->wdev)));
     CK(cudaStreamSynchronize(c->stream));
+    return PR_OK;
+}
+
+int pr_count_samples(pr_ctx* c, int id, double angle, const double* w, long long* count) {
+    GET_MODEL(c, id, m);
+    if (!w || !count) return fail(PR_EINVAL, "null argument");
+    TRY(set_w(c, m, w));
+    TRY(set_rg(c, m->rg, m->vol, m->geom, angle));
+    Launcher L;
+    L.stream = c->stream;
+    unsigned long long* dev = reinterpret_cast<unsigned long long*>(m->partials);
+    unsigned long long host = 0;
+    CK(cudaMemsetAsync(dev, 0, sizeof host, c->stream));
+    CK(launch_count_samples(L, m->md.vd, m->rg, m->geom.nu, m->geom.nv, sref(m, m->wdev), dev));
+    CK(cudaMemcpyAsync(&host, dev, sizeof host, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *count = (long long)host;
     return PR_OK;
 }
 
@@ -1253,7 +1330,7 @@ int pr_cost_grad(pr_ctx* c, int id, const float* y_dev, double angle, const doub
     if (mode == 0) {
         CK(launch_warp(L, m->md, m->wdev, kWarpFH, m->fh, nullptr, nullptr));
         CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, m->order, nu, nv, m->p, m->q, nullptr, nullptr, nullptr,
-                          nullptr, kPhaseNone, 0, 0, SupportRef{m->sup, m->wdev, m->K}, &m->ss));
+                          nullptr, kPhaseNone, 0, 0, sref(m, m->wdev), &m->ss));
         CK(launch_cost_grad(L, m->p, m->q, y_dev, m->R, m->K, m->out + 8, m->partials, m->counter, m->out));
         CK(cudaMemcpyAsync(res, m->out, sizeof(double) * (1 + m->K), cudaMemcpyDeviceToHost, c->stream));
     } else {
@@ -1261,7 +1338,7 @@ int pr_cost_grad(pr_ctx* c, int id, const float* y_dev, double angle, const doub
         CK(launch_warp(L, m->md, m->wdev, kWarpFPad, m->fpad, nullptr, nullptr));
         CK(launch_warp(L, m->md, m->wdev, kWarpFlatFH, nullptr, nullptr, m->hbuf));
         CK(launch_project(L, m->md.vd, m->fpad, 1, 0, m->rg, m->order, nu, nv, m->p, nullptr, nullptr, nullptr, nullptr,
-                          nullptr, kPhaseNone, 0, 0, SupportRef{m->sup, m->wdev, m->K}));
+                          nullptr, kPhaseNone, 0, 0, sref(m, m->wdev)));
         CK(launch_cost_grad(L, m->p, nullptr, y_dev, m->R, 0, m->out + 8, m->partials, m->counter, m->out));
         CK(launch_residual(L, m->p, y_dev, m->R, m->out + 8, m->r));
         CK(cudaMemcpyAsync(res, m->out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -1333,7 +1410,7 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
     CK(launch_warp(L, m->md, m->st->w, kWarpFPad, m->fpad, nullptr, nullptr));
     if (which == PR_KERNEL_BACKPROJECT) CK(launch_warp(L, m->md, m->st->w, kWarpFlatFH, nullptr, nullptr, m->hbuf));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, m->order, nu, nv, m->p, m->q, nullptr, nullptr, nullptr, nullptr,
-                      kPhaseNone, 0, 0, SupportRef{m->sup, m->st->w, m->K}, &m->ss));
+                      kPhaseNone, 0, 0, sref(m, m->st->w), &m->ss));
     float* ytmp = nullptr;  // output of the timed inversion (3N floats, freed below)
     if (which == PR_KERNEL_INVERT) CK(cudaMalloc(&ytmp, (size_t)3 * m->md.vd.n * sizeof(float)));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1345,7 +1422,7 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
             case PR_KERNEL_WARP_FH: err = launch_warp(L, m->md, m->st->w, kWarpFH, m->fh, nullptr, nullptr); break;
             case PR_KERNEL_PROJECT_FH:
                 err = launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, m->order, nu, nv, m->p, m->q, nullptr, nullptr,
-                                     nullptr, nullptr, kPhaseNone, 0, 0, SupportRef{m->sup, m->st->w, m->K}, &m->ss);
+                                     nullptr, nullptr, kPhaseNone, 0, 0, sref(m, m->st->w), &m->ss);
                 break;
             case PR_KERNEL_REGRAD:
                 err = launch_cost_grad(L, m->p, m->q, m->p, m->R, m->K, m->out + 8, m->partials, m->counter, m->out);
@@ -1357,7 +1434,7 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
             case PR_KERNEL_WARP_F: err = launch_warp(L, m->md, m->st->w, kWarpFPad, m->fpad, nullptr, nullptr); break;
             case PR_KERNEL_PROJECT_F:
                 err = launch_project(L, m->md.vd, m->fpad, 1, 0, m->rg, m->order, nu, nv, m->r, nullptr, nullptr, nullptr,
-                                     nullptr, nullptr, kPhaseNone, 0, 0, SupportRef{m->sup, m->st->w, m->K});
+                                     nullptr, nullptr, kPhaseNone, 0, 0, sref(m, m->st->w));
                 break;
             case PR_KERNEL_INVERT:
                 err = launch_invert(L, m->md, m->st->w, reinterpret_cast<float4*>(m->fh), 1e-5, 64, ytmp,
