@@ -503,9 +503,26 @@ void drop_bp_table(pr_ctx* c, Model* m) {
     m->bt_bytes = 0;
 }
 
-int ensure_hbuf(Model* m) {
+// The adjoint's h scratch (K x N floats), allocated on first use and charged
+// to the model and the context like the rest of the model.
+int ensure_hbuf(pr_ctx* c, Model* m) {
     if (m->hbuf) return PR_OK;
-    CK(dalloc(&m->hbuf, (size_t)m->K * m->md.vd.n * 4, &m->bytes));
+    const size_t bytes = (size_t)m->K * m->md.vd.n * 4;
+    {
+        std::lock_guard<std::mutex> lock(c->mu);
+        if (c->used + bytes > c->budget)
+            return fail(PR_EADMIT, "adjoint scratch of %zu bytes exceeds the HBM budget", bytes);
+        c->used += bytes;
+    }
+    if (cudaMalloc(&m->hbuf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        m->hbuf = nullptr;
+        std::lock_guard<std::mutex> lock(c->mu);
+        c->used -= bytes;
+        return fail(PR_ENOMEM, "adjoint scratch of %zu bytes: allocation failed", bytes);
+    }
+    std::lock_guard<std::mutex> lock(c->mu);
+    m->bytes += bytes;
     return PR_OK;
 }
 
@@ -1298,7 +1315,7 @@ int pr_fix_angle(pr_ctx* c, int id, double angle, size_t* table_bytes) {
 int pr_vjp(pr_ctx* c, int id, const double* w, double angle, const float* grad_p_dev, double* grad_w) {
     GET_MODEL(c, id, m);
     if (!w || !grad_p_dev || !grad_w) return fail(PR_EINVAL, "null argument");
-    TRY(ensure_hbuf(m));
+    TRY(ensure_hbuf(c, m));
     TRY(set_w(c, m, w));
     TRY(set_rg(c, m->rg, m->vol, m->geom, angle));
     Launcher L;
@@ -1334,7 +1351,7 @@ int pr_cost_grad(pr_ctx* c, int id, const float* y_dev, double angle, const doub
         CK(launch_cost_grad(L, m->p, m->q, y_dev, m->R, m->K, m->out + 8, m->partials, m->counter, m->out));
         CK(cudaMemcpyAsync(res, m->out, sizeof(double) * (1 + m->K), cudaMemcpyDeviceToHost, c->stream));
     } else {
-        TRY(ensure_hbuf(m));
+        TRY(ensure_hbuf(c, m));
         CK(launch_warp(L, m->md, m->wdev, kWarpFPad, m->fpad, nullptr, nullptr));
         CK(launch_warp(L, m->md, m->wdev, kWarpFlatFH, nullptr, nullptr, m->hbuf));
         CK(launch_project(L, m->md.vd, m->fpad, 1, 0, m->rg, m->order, nu, nv, m->p, nullptr, nullptr, nullptr, nullptr,
@@ -1399,7 +1416,7 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
     if (which == PR_KERNEL_INVERT && m->vol.nx * (long long)m->vol.ny * m->vol.nz >= 0x7fffffffLL)
         return fail(PR_EINVAL, "grid too large");
     TRY(set_rg(c, m->rg, m->vol, m->geom, angle));
-    if (which == PR_KERNEL_BACKPROJECT) TRY(ensure_hbuf(m));
+    if (which == PR_KERNEL_BACKPROJECT) TRY(ensure_hbuf(c, m));
     Launcher L;
     L.stream = c->stream;
     const int nu = m->geom.nu, nv = m->geom.nv;

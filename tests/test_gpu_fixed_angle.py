@@ -76,3 +76,36 @@ def test_fixed_angle_table_is_admitted_by_budget(setup):
         assert e.value.code == -1
     finally:
         small.close()
+
+
+def test_adjoint_scratch_is_charged_to_the_budget(setup):
+    """The adjoint's h scratch is allocated on first use: it must fit the
+    context's HBM budget, and releasing the model returns exactly what was
+    charged (a later model of the same size is admitted again)."""
+    from paper_1004_0014_b300 import Context, PcaReconError
+
+    s = setup
+    f0, mean, U = (np.ascontiguousarray(a, dtype=np.float32) for a in (s["f0"], s["pca"].mean, s["pca"].U))
+    probe = Context(0)
+    need = probe.footprint(probe.load_model(s["vol"], s["geom"], f0, mean, U, s["c0"]))
+    probe.close()
+    c = Context(0, hbm_budget_bytes=need + 1024)  # the model fits, its adjoint scratch does not
+    try:
+        mid = c.load_model(s["vol"], s["geom"], f0, mean, U, s["c0"])
+        with pytest.raises(PcaReconError) as e:
+            c.vjp(mid, np.zeros(3), s["th"], s["gp"])
+        assert e.value.code == -3
+        assert c.footprint(mid) == need
+        c.release_model(mid)
+        mid = c.load_model(s["vol"], s["geom"], f0, mean, U, s["c0"])
+        assert c.footprint(mid) == need
+    finally:
+        c.close()
+    roomy = Context(0, hbm_budget_bytes=2 * need + 8 * s["vol"].nx * s["vol"].ny * s["vol"].nz * 4)
+    try:
+        for _ in range(3):  # load, use the adjoint, release: the budget must not drift
+            mid = roomy.load_model(s["vol"], s["geom"], f0, mean, U, s["c0"])
+            roomy.vjp(mid, np.zeros(3), s["th"], s["gp"])
+            roomy.release_model(mid)
+    finally:
+        roomy.close()
