@@ -393,7 +393,9 @@ enum {
                                    fixed-angle table when pr_fix_angle built one at this angle) */
     PR_KERNEL_WARP_F = 4,       /* warp writing f only */
     PR_KERNEL_PROJECT_F = 5,    /* ray-march projection of f only */
-    PR_KERNEL_INVERT = 6        /* whole-grid DVF inversion (pr_invert_dvf, tol 1e-5 mm, 64 steps) */
+    PR_KERNEL_INVERT = 6,       /* whole-grid DVF inversion (pr_invert_dvf, tol 1e-5 mm, 64 steps) */
+    PR_KERNEL_PROJECT_FH_TRIAL = 7 /* the solver pass as a line-search trial runs it: projection with
+                                      the moments and the controller (on a copy of the solve state) */
 };
 
 /* Launch kernel `which` `iters` times back to back on the context stream

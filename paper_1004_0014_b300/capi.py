@@ -49,6 +49,7 @@ EXPORTED = [
 
 PR_KERNEL_WARP_FH, PR_KERNEL_PROJECT_FH, PR_KERNEL_REGRAD = 0, 1, 2
 PR_KERNEL_BACKPROJECT, PR_KERNEL_WARP_F, PR_KERNEL_PROJECT_F, PR_KERNEL_INVERT = 3, 4, 5, 6
+PR_KERNEL_PROJECT_FH_TRIAL = 7
 
 
 class Stats(ctypes.Structure):

@@ -1412,7 +1412,7 @@ int pr_invert_dvf(pr_ctx* c, int id, const double* w, double tol, int max_iter, 
 int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double* avg_ms) {
     GET_MODEL(c, id, m);
     if (!avg_ms || iters < 1 || iters > 100000) return fail(PR_EINVAL, "invalid iters or output");
-    if (which < PR_KERNEL_WARP_FH || which > PR_KERNEL_INVERT) return fail(PR_EINVAL, "unknown kernel %d", which);
+    if (which < PR_KERNEL_WARP_FH || which > PR_KERNEL_PROJECT_FH_TRIAL) return fail(PR_EINVAL, "unknown kernel %d", which);
     if (which == PR_KERNEL_INVERT && m->vol.nx * (long long)m->vol.ny * m->vol.nz >= 0x7fffffffLL)
         return fail(PR_EINVAL, "grid too large");
     TRY(set_rg(c, m->rg, m->vol, m->geom, angle));
@@ -1430,6 +1430,11 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
                       kPhaseNone, 0, 0, sref(m, m->st->w), &m->ss));
     float* ytmp = nullptr;  // output of the timed inversion (3N floats, freed below)
     if (which == PR_KERNEL_INVERT) CK(cudaMalloc(&ytmp, (size_t)3 * m->md.vd.n * sizeof(float)));
+    SolveState* sst = nullptr;  // copy of the solve state the timed trial passes update (freed below)
+    if (which == PR_KERNEL_PROJECT_FH_TRIAL) {
+        CK(cudaMalloc(&sst, sizeof(SolveState)));
+        CK(cudaMemcpyAsync(sst, m->st, sizeof(SolveState), cudaMemcpyDeviceToDevice, c->stream));
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t err = cudaEventCreate(&e0);
     if (err == cudaSuccess) err = cudaEventCreate(&e1);
@@ -1457,6 +1462,10 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
                 err = launch_invert(L, m->md, m->st->w, reinterpret_cast<float4*>(m->fh), 1e-5, 64, ytmp,
                                     reinterpret_cast<unsigned int*>(m->partials));
                 break;
+            case PR_KERNEL_PROJECT_FH_TRIAL:
+                err = launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, m->order, nu, nv, m->p, m->q, m->y, sst,
+                                     m->partials, m->counter, kPhaseTrial, 0, 0, sref(m, m->st->w), &m->ss);
+                break;
         }
     }
     if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
@@ -1465,9 +1474,10 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
     if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    if (ytmp) {
+    if (ytmp || sst) {
         cudaError_t e2 = cudaStreamSynchronize(c->stream);
-        cudaFree(ytmp);
+        if (ytmp) cudaFree(ytmp);
+        if (sst) cudaFree(sst);
         if (err == cudaSuccess) err = e2;
     }
     CK(err);
