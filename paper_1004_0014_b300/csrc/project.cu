@@ -2,15 +2,18 @@
 // fused residual/moment epilogue, and the on-device controller of Section
 // 2.2's alternation: Eq. 4 for (a, b), Armijo's rule for the step of Eq. 3,
 // and the stopping rule. Also the y-moment / initialisation kernel, the
-// residual-gradient kernel, and the Section 2.3 tumor fixed point.
+// cost-gradient kernel of the step-level call, and the Section 2.3 tumor
+// fixed point.
 //
 // Projector layout: one thread per ray; a warp owns an 8 x 4 patch of
-// detector pixels and a block of 256 threads a 32 x 8 tile, so the 32 samples
-// a warp takes at one step lie within about one voxel of each other and the
-// eight trilinear taps of the warp hit a handful of cache lines. All lanes of
-// a warp march the union of their sample ranges; a point outside the
-// interpolant's support is clamped onto the zero border of the padded volume
-// and adds exactly zero, so the loop has no divergent exits.
+// detector pixels, so the 32 samples a warp takes at one step lie within about
+// one voxel of each other and the eight trilinear taps of the warp hit a
+// handful of cache lines. All lanes of a warp march the union of their sample
+// ranges; a point outside the interpolant's support is clamped onto the zero
+// border of the padded volume and adds exactly zero, so the loop has no
+// divergent exits. The solver pass (k_project_split) splits each warp's range
+// into parts taken from a work queue; the single-channel pass (k_project) gives
+// a block of 256 threads a 32 x 8 tile.
 #include <math.h>
 
 #include "internal.h"
@@ -29,7 +32,7 @@ constexpr int kMaxSamples = 1 << 22;  // samples per ray, far above any real geo
 constexpr double kModelMinDecrease = 1e-6;  // see controller_project
 
 // ---------------------------------------------------------------------------
-// Controller pieces (thread 0 of the last block; FP64)
+// Controller pieces (one thread of the warp that completes a pass; FP64)
 // ---------------------------------------------------------------------------
 
 // Eq. 4: (a, b) = (Y^T Y)^-1 Y^T p with Y = [y, 1].
@@ -334,7 +337,7 @@ __device__ double cost_at(const SolveState* st, const double* m, double a, doubl
 
 // Cost and gradient at the state's (a, b) from the moments, then the stopping
 // rule (Section 2.2) and, if the solve goes on, the first trial of the next
-// step. Thread 0 of the last block.
+// step. One thread of the warp that completes the pass.
 // The floating-point choices of line-search trial st->trials (1-based), one
 // byte: bit 7 accepted, bit 6 stop (a rejected trial: the predicted decrease
 // was unresolvable; an accepted one: the gradient test was met after it),
@@ -553,7 +556,7 @@ __global__ void __launch_bounds__(kProjThreads, NCH == 4 ? 4 : 1) k_project(Proj
     if (A.phase == kPhaseNone) return;
 
     // Epilogue: this pass's moments (FP64; see cost_at), block sums, and the
-    // controller in the last block to finish.
+    // controller in the last block to finish (single-channel pass).
     // Products of two floats are exact as float-float pairs, and the sums run
     // in float-float within a warp and in FP64 across warps and blocks.
     constexpr int KM = NCH == 8 ? 7 : 3;

@@ -1,9 +1,10 @@
 // C-ABI runtime of pcarecon: contexts, resident patient models with HBM
 // admission, the per-model CUDA graph that runs Section 2.2's whole
-// alternation on the device (a conditional WHILE node whose body is
-// warp -> project -> residual-gradient, with the Armijo and stopping
-// decisions taken in FP64 by the kernels themselves), the host-driven loop
-// used as the plain baseline, and the step-level entry points.
+// alternation on the device (a conditional WHILE node whose body is warp ->
+// project, with the moments, the Armijo and stopping decisions taken in FP64
+// by the projector's last finishing warp), batched solves in one graph, the
+// serving worker, the host-driven loop used as the plain baseline, fixed-angle
+// transpose tables, and the step-level entry points.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -385,10 +386,10 @@ bool opts_ok(const pr_solve_opts* o) {
 }
 
 // Section 2.2's loop as a CUDA graph: prologue (y moments; f and h at w0;
-// projection, whose last block fits Eq. 4 and forms the cost and gradient), a
-// WHILE node whose body is one line-search trial (warp, then projection with
-// the Armijo test, Eq. 4, cost, gradient and stopping rule in its last
-// block), and the Section 2.3 tumor kernel.
+// projection, whose last finishing warp fits Eq. 4 and forms the cost and
+// gradient), a WHILE node whose body is one line-search trial (warp, then
+// projection with the Armijo test, Eq. 4, cost, gradient and stopping rule in
+// the warp that completes it), and the Section 2.3 tumor kernel.
 int build_graph(pr_ctx* c, Model* m) {
     CK(cudaGraphCreate(&m->graph, 0));
     CK(cudaGraphConditionalHandleCreate(&m->hloop, m->graph, 1, cudaGraphCondAssignDefault));
