@@ -667,7 +667,7 @@ def serve_once(ctx, mids, pats, ys, trace, opts, n_slots, local):
 
 
 def run_serve(args):
-    from paper_1004_0014_b300 import PR_LOOP_HOST, Context, default_opts
+    from paper_1004_0014_b300 import PR_BF16, PR_F32, PR_LOOP_HOST, Context, default_opts
 
     world, rank, local = dist_env()
     if world > 1:
@@ -680,7 +680,8 @@ def run_serve(args):
     mids = []
     for pt in pats:
         b = bases[pt["key"]]
-        mids.append(ctx.load_model(b["vol"], geom, b["f0"], pt["alpha"] * b["mean"], b["U"][:pt["K"]], b["c0"]))
+        mids.append(ctx.load_model(b["vol"], geom, b["f0"], pt["alpha"] * b["mean"], b["U"][:pt["K"]], b["c0"],
+                                   storage=PR_BF16 if args.storage == "bf16" else PR_F32))
     opts = default_opts(max_iters=10)
 
     slot_list = [int(x) for x in str(args.slots).split(",")]
@@ -730,8 +731,8 @@ def run_serve(args):
                          "p99_ms": float(np.percentile(r["lat"], 99)), "gpu_ms_mean": r["gpu_ms_mean"]}
                         for r in runs],
         "config": {"workload": "serving: %d patients, shapes %s, K 3-5, SI amplitude 8-20 mm (whole field scaled), "
-                               "512x384 detector, 10 iterations, warm start per patient" %
-                               (args.patients, sorted(set(str(p["key"]) for p in pats))),
+                               "512x384 detector, 10 iterations, warm start per patient, %s storage" %
+                               (args.patients, sorted(set(str(p["key"]) for p in pats)), args.storage),
                    "frames": "per patient: Poisson arrivals, 1 deg per frame from a random start, breathing phase "
                              "from the arrival time (%d bins per 4 s), 1%% noise" % SERVE_BINS},
         "latency": "scheduled arrival to result on the host clock (queue + solve)",
@@ -759,7 +760,7 @@ def run_serve(args):
 
 
 def run_batch(args):
-    from paper_1004_0014_b300 import PR_LOOP_HOST, Context, default_opts
+    from paper_1004_0014_b300 import PR_BF16, PR_F32, PR_LOOP_HOST, Context, default_opts
 
     world, rank, local = dist_env()
     if world > 1:
@@ -778,7 +779,8 @@ def run_batch(args):
     mids = []
     for pt in pats:
         b = bases[pt["key"]]
-        mids.append(ctx.load_model(b["vol"], geom, b["f0"], pt["alpha"] * b["mean"], b["U"][:pt["K"]], b["c0"]))
+        mids.append(ctx.load_model(b["vol"], geom, b["f0"], pt["alpha"] * b["mean"], b["U"][:pt["K"]], b["c0"],
+                                   storage=PR_BF16 if args.storage == "bf16" else PR_F32))
     opts = default_opts(max_iters=10)
     ids = [mids[i] for (_, i, _, _) in order]
     yl = [ys[(i, f)] for (_, i, f, _) in order]
@@ -818,7 +820,7 @@ def run_batch(args):
                                "detector, 10 iterations" % (sorted(set(str(p["key"]) for p in pats)),
                                                             [p["K"] for p in pats]),
                    "timed": "pr_reconstruct_batch with host frames (H2D staging and result read-back included), "
-                            "median of %d" % reps},
+                            "median of %d" % reps, "storage": args.storage},
         "one_at_a_time_graph": {"value": n / statistics.median(t_seq),
                                 "path": "pr_reconstruct per frame (on-device loop), same order"},
         "plain_fp32": {"value": n / statistics.median(t_plain),
