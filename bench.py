@@ -515,6 +515,7 @@ def run_ours(args):
             "plain_fp32": {"value": plain_value, "unit": UNIT, "p50_ms": float(np.percentile(plain, 50)),
                            "p99_ms": float(np.percentile(plain, 99)),
                            "path": "same kernels, host-driven loop (one device-to-host read per trial), no graph",
+                           "storage": "same as the served arm (FP32 arithmetic throughout)",
                            "speedup": value / plain_value},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "path": "pr_reconstruct with pinned host y, result copied back every step"},
@@ -744,7 +745,8 @@ def run_serve(args):
                        "p99_ms": float(np.percentile(plain_lat, 99)),
                        "mean_service_ms": 1000.0 * float(np.mean(svc)),
                        "path": "host-driven loop (PR_LOOP_HOST), one frame at a time in arrival order; latency from "
-                               "the measured service times with start = max(arrival, previous finish)"},
+                               "the measured service times with start = max(arrival, previous finish)",
+                       "storage": "%s, as the served arm (FP32 arithmetic throughout)" % args.storage},
         "results_identical_to_plain": bool(same),
         "gpu_ms_mean": head["gpu_ms_mean"],
         "clocks": clk_summary,
@@ -824,7 +826,8 @@ def run_batch(args):
         "one_at_a_time_graph": {"value": n / statistics.median(t_seq),
                                 "path": "pr_reconstruct per frame (on-device loop), same order"},
         "plain_fp32": {"value": n / statistics.median(t_plain),
-                       "path": "pr_reconstruct per frame with the host-driven loop, same order"},
+                       "path": "pr_reconstruct per frame with the host-driven loop, same order",
+                       "storage": "%s, as the batched arm (FP32 arithmetic throughout)" % args.storage},
         "results_identical_to_one_at_a_time": bool(same),
         "clocks": clk.summary(),
     }
