@@ -232,6 +232,22 @@ def flops_per_sample(nch: int) -> int:
     return 2 * 8 * nch + 19 + 6
 
 
+def warp_voxels_evaluated(vol, box, block_voxels: int = 1024) -> int:
+    """Voxels of the warp pass's blocks (block_voxels consecutive voxels of
+    the flat grid each) that meet the inclusive voxel box ((x0, y0, z0),
+    (x1, y1, z1)); the other blocks write zeros without reading a field."""
+    (x0, y0, z0), (x1, y1, z1) = box
+    ix, iy, iz = np.arange(vol.nx), np.arange(vol.ny), np.arange(vol.nz)
+    inside = (((iz >= z0) & (iz <= z1))[:, None, None] & ((iy >= y0) & (iy <= y1))[None, :, None]
+              & ((ix >= x0) & (ix <= x1))[None, None, :]).ravel()
+    n = inside.size
+    pad = np.zeros(-n % block_voxels, dtype=bool)
+    blocks = np.concatenate([inside, pad]).reshape(-1, block_voxels).any(axis=1)
+    sizes = np.full(blocks.size, block_voxels)
+    sizes[-1] = n - block_voxels * (blocks.size - 1)
+    return int(sizes[blocks].sum())
+
+
 def recorded_traffic(kernel: str, source: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, only
     if the kernel's source file is unchanged since the capture (else None)."""
@@ -467,13 +483,17 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": bytes_proj,
                 "achieved_gbs": bytes_proj / (kern["project_fh_trial"] / 1000.0) / 1e9}
     ts = 2 if bf16 else 4  # bytes per stored value of f0 and U
-    bytes_warp = N * (12 + 3 * ts * Km + ts + 4 * nch)
+    # the solver's warp evaluates the blocks that meet the support box at w;
+    # the others only write their zeros
+    n_eval = warp_voxels_evaluated(vol, ctx.warp_box(mid, w_start))
+    bytes_warp = n_eval * (12 + 3 * ts * Km + ts + 4 * nch) + (N - n_eval) * 4 * nch
     warp_gbs = bytes_warp / (kern["warp_fh"] / 1000.0) / 1e9
     roofline_warp = {"kernel": "k_warp<%d, f+h, %s>" % (Km, "bf16" if bf16 else "float"), "bound": "hbm",
                      "achieved": warp_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": warp_gbs / hbm_peak,
                      "traffic": recorded_traffic("k_warp<3,FH,float>", "warp.cu") if (Km == 3 and not bf16) else None,
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if peaks else "fallback",
-                     "algorithmic_bytes_per_launch": bytes_warp, "share_of_solve": share_warp}
+                     "algorithmic_bytes_per_launch": bytes_warp, "share_of_solve": share_warp,
+                     "voxels_evaluated": n_eval, "voxels": N}
 
     # Whole-grid DVF inversion (Section 2.3 with ref. 13), outside the solve:
     # x/dx synthesis (12 + 12K bytes read, 16 written per voxel), then the

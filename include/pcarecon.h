@@ -327,6 +327,16 @@ int pr_trial_log(pr_ctx* ctx, int model_id, unsigned char* out, int cap, int* n)
  * to be exactly zero. Synchronous. Errors: PR_EINVAL, PR_ENOMODEL, PR_ECUDA. */
 int pr_count_samples(pr_ctx* ctx, int model_id, double angle_rad, const double* w, long long* count);
 
+/* Measurement (no counterpart in the paper): the voxel box the solver's warp
+ * pass (Eq. 1 and the pull-back of Section 2.2) evaluates at coefficients w
+ * (K doubles, host): box[0..2] = lowest x, y, z voxel index, box[3..5] =
+ * highest, clamped to the grid (empty when box[c] > box[3 + c]). Voxels
+ * outside it lie farther than the displacement bound from every nonzero f0
+ * voxel and are exact zeros: a block of the pass (1024 consecutive voxels of
+ * the flat grid) none of whose voxels is in the box writes its zeros without
+ * reading a field. Synchronous. Errors: PR_EINVAL, PR_ENOMODEL, PR_ECUDA. */
+int pr_warp_box(pr_ctx* ctx, int model_id, const double* w, int box[6]);
+
 /* Section 5's fixed-angle geometry (fluoroscopy: the gantry does not move,
  * so P is the same matrix for every frame). Builds the model's table of the
  * transpose at angle_rad: for each voxel its detector footprint and the weight

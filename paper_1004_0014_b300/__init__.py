@@ -169,6 +169,10 @@ class Context:
         """Ray samples the solver-pass projector evaluates at this angle and w."""
         return capi.pr_count_samples(self._ctx, mid, angle_rad, w)
 
+    def warp_box(self, mid: int, w):
+        """Inclusive voxel box ((x0, y0, z0), (x1, y1, z1)) the solver's warp evaluates at w."""
+        return capi.pr_warp_box(self._ctx, mid, w)
+
     def fix_angle(self, mid: int, angle_rad: float) -> int:
         """Fixed-angle transpose table for the model at this angle (NaN drops it)."""
         return capi.pr_fix_angle(self._ctx, mid, angle_rad)

@@ -41,9 +41,8 @@ EXPORTED = [
     "pr_version", "pr_last_error", "pr_default_opts", "pr_create", "pr_destroy", "pr_load_model",
     "pr_release_model", "pr_model_footprint", "pr_reconstruct", "pr_reconstruct_batch", "pr_reconstruct_async",
     "pr_fetch_result", "pr_get_state", "pr_set_state", "pr_warp", "pr_project", "pr_backproject",
-    "pr_forward", "pr_vjp", "pr_cost_grad", "pr_tumor", "pr_invert_dvf", "pr_trial_log", "pr_fix_angle", "pr_count_samples",
-    "pr_time_kernel",
-    "pr_model_stats",
+    "pr_forward", "pr_vjp", "pr_cost_grad", "pr_tumor", "pr_invert_dvf", "pr_trial_log", "pr_fix_angle",
+    "pr_count_samples", "pr_warp_box", "pr_time_kernel", "pr_model_stats",
     "pr_io_bytes", "pr_cost_grad_static", "pr_serve_start", "pr_submit", "pr_poll", "pr_serve_stop",
 ]
 
@@ -158,6 +157,7 @@ def load_library(path: str | None = None):
         "pr_trial_log": (_I, [_P, _I, _P, _I, ctypes.POINTER(_I)]),
         "pr_fix_angle": (_I, [_P, _I, _D, ctypes.POINTER(ctypes.c_size_t)]),
         "pr_count_samples": (_I, [_P, _I, _D, _DP, ctypes.POINTER(ctypes.c_longlong)]),
+        "pr_warp_box": (_I, [_P, _I, _DP, ctypes.POINTER(ctypes.c_int)]),
         "pr_time_kernel": (_I, [_P, _I, _I, _D, _I, _DP]),
         "pr_model_stats": (_I, [_P, _I, ctypes.POINTER(Stats)]),
         "pr_io_bytes": (_I, [_P, _I, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
@@ -391,6 +391,14 @@ def pr_count_samples(ctx, model_id: int, angle_rad: float, w) -> int:
     n = ctypes.c_longlong()
     _check(_lib.pr_count_samples(ctx, int(model_id), float(angle_rad), pw, ctypes.byref(n)))
     return n.value
+
+
+def pr_warp_box(ctx, model_id: int, w):
+    """((x0, y0, z0), (x1, y1, z1)): inclusive voxel box the solver's warp evaluates at w."""
+    w, pw = _dvec(w)
+    box = (ctypes.c_int * 6)()
+    _check(_lib.pr_warp_box(ctx, int(model_id), pw, box))
+    return tuple(box[0:3]), tuple(box[3:6])
 
 
 def pr_fix_angle(ctx, model_id: int, angle_rad: float) -> int:

@@ -32,9 +32,16 @@ enum WarpMode : int {
 inline int fh_channels(int K) { return K <= 3 ? 4 : (K <= 5 ? 6 : 8); }
 
 // G1: x = mean + U w (Eq. 1), f(v) = F0(v + x(v)), h_k(v) (Section 2.2).
-// w_dev: K doubles in device memory.
+// w_dev: K doubles in device memory. sup (device, nullable; padded modes
+// only): the model's support record; voxels outside the support box at w_dev
+// are exact zeros and are written as zeros without reading their fields.
 cudaError_t launch_warp(Launcher& L, const ModelDev& m, const double* w_dev, int mode, float* out_pad,
-                        float* f_flat, float* h_flat);
+                        float* f_flat, float* h_flat, const Support* sup = nullptr);
+
+// Voxel box [lo, hi] (per axis, clamped to the grid; empty when lo > hi) that
+// the support-restricted warp evaluates at coefficients w_dev, written as six
+// ints (lo x, y, z, hi x, y, z) to box_dev.
+cudaError_t launch_warp_box(Launcher& L, const ModelDev& m, const double* w_dev, const Support* sup, int* box_dev);
 
 // Round float32 to bfloat16 (round-to-nearest-even), n elements.
 cudaError_t launch_to_bf16(Launcher& L, const float* src, __nv_bfloat16* dst, long long n);

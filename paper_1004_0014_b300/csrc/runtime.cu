@@ -397,7 +397,7 @@ int build_graph(pr_ctx* c, Model* m) {
     L.graph = m->graph;
     SolveState* st = m->st;
     CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
-    CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
+    CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseInit, m->hloop, 1, sref(m, st->wt), &m->ss));
     cudaGraphNodeParams cp = {};
@@ -409,7 +409,7 @@ int build_graph(pr_ctx* c, Model* m) {
     CK(cudaGraphAddNode(&cond, m->graph, &L.last, nullptr, 1, &cp));
     Launcher B;
     B.graph = cp.conditional.phGraph_out[0];
-    CK(launch_warp(B, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
+    CK(launch_warp(B, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup));
     CK(launch_project(B, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseTrial, m->hloop, 1, sref(m, st->wt), &m->ss));
     L.last = cond;
@@ -425,7 +425,7 @@ int host_loop(pr_ctx* c, Model* m, int opt_max_iters, int opt_max_bt) {
     L.stream = c->stream;
     SolveState* st = m->st;
     CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
-    CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
+    CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseInit, 0, 0, sref(m, st->wt), &m->ss));
     long long guard = 0, bound = (long long)(opt_max_iters + 1) * (opt_max_bt + 1) + 2;
@@ -434,7 +434,7 @@ int host_loop(pr_ctx* c, Model* m, int opt_max_iters, int opt_max_bt) {
         CK(cudaStreamSynchronize(c->stream));
         if (!m->st_host->running) break;
         if (++guard > bound) return fail(PR_ETIMEOUT, "host loop exceeded its trial bound");
-        CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
+        CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup));
         CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y,
                           st, m->partials, m->counter, kPhaseTrial, 0, 0, sref(m, st->wt), &m->ss));
         }
@@ -619,7 +619,7 @@ int add_solve_nodes(cudaGraph_t g, Model* m, const cudaGraphNode_t* dep, const f
     L.last = np;
     L.has_last = true;
     CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
-    CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
+    CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseInit, h, 1, sref(m, st->wt), &m->ss));
     cudaGraphNodeParams cp = {};
@@ -631,7 +631,7 @@ int add_solve_nodes(cudaGraph_t g, Model* m, const cudaGraphNode_t* dep, const f
     CK(cudaGraphAddNode(&cond, g, &L.last, nullptr, 1, &cp));
     Launcher B;
     B.graph = cp.conditional.phGraph_out[0];
-    CK(launch_warp(B, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr));
+    CK(launch_warp(B, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup));
     CK(launch_project(B, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseTrial, h, 1, sref(m, st->wt), &m->ss));
     L.last = cond;
@@ -1230,7 +1230,7 @@ int pr_forward(pr_ctx* c, int id, const double* w, double angle, float* p_dev) {
     TRY(set_rg(c, m->rg, m->vol, m->geom, angle));
     Launcher L;
     L.stream = c->stream;
-    CK(launch_warp(L, m->md, m->wdev, kWarpFPad, m->fpad, nullptr, nullptr));
+    CK(launch_warp(L, m->md, m->wdev, kWarpFPad, m->fpad, nullptr, nullptr, m->sup));
     CK(launch_project(L, m->md.vd, m->fpad, 1, 0, m->rg, m->order, m->geom.nu, m->geom.nv, p_dev, nullptr, nullptr, nullptr,
                       nullptr, nullptr, kPhaseNone, 0, 0, sref(m, m->wdev)));
     CK(cudaStreamSynchronize(c->stream));
@@ -1251,6 +1251,19 @@ int pr_count_samples(pr_ctx* c, int id, double angle, const double* w, long long
     CK(cudaMemcpyAsync(&host, dev, sizeof host, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     *count = (long long)host;
+    return PR_OK;
+}
+
+int pr_warp_box(pr_ctx* c, int id, const double* w, int box[6]) {
+    GET_MODEL(c, id, m);
+    if (!w || !box) return fail(PR_EINVAL, "null argument");
+    TRY(set_w(c, m, w));
+    Launcher L;
+    L.stream = c->stream;
+    int* dev = reinterpret_cast<int*>(m->partials);
+    CK(launch_warp_box(L, m->md, m->wdev, m->sup, dev));
+    CK(cudaMemcpyAsync(box, dev, 6 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     return PR_OK;
 }
 
@@ -1346,14 +1359,14 @@ int pr_cost_grad(pr_ctx* c, int id, const float* y_dev, double angle, const doub
     const int nu = m->geom.nu, nv = m->geom.nv;
     double res[8] = {0};
     if (mode == 0) {
-        CK(launch_warp(L, m->md, m->wdev, kWarpFH, m->fh, nullptr, nullptr));
+        CK(launch_warp(L, m->md, m->wdev, kWarpFH, m->fh, nullptr, nullptr, m->sup));
         CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, m->order, nu, nv, m->p, m->q, nullptr, nullptr, nullptr,
                           nullptr, kPhaseNone, 0, 0, sref(m, m->wdev), &m->ss));
         CK(launch_cost_grad(L, m->p, m->q, y_dev, m->R, m->K, m->out + 8, m->partials, m->counter, m->out));
         CK(cudaMemcpyAsync(res, m->out, sizeof(double) * (1 + m->K), cudaMemcpyDeviceToHost, c->stream));
     } else {
         TRY(ensure_hbuf(c, m));
-        CK(launch_warp(L, m->md, m->wdev, kWarpFPad, m->fpad, nullptr, nullptr));
+        CK(launch_warp(L, m->md, m->wdev, kWarpFPad, m->fpad, nullptr, nullptr, m->sup));
         CK(launch_warp(L, m->md, m->wdev, kWarpFlatFH, nullptr, nullptr, m->hbuf));
         CK(launch_project(L, m->md.vd, m->fpad, 1, 0, m->rg, m->order, nu, nv, m->p, nullptr, nullptr, nullptr, nullptr,
                           nullptr, kPhaseNone, 0, 0, sref(m, m->wdev)));
@@ -1402,6 +1415,8 @@ int pr_invert_dvf(pr_ctx* c, int id, const double* w, double tol, int max_iter, 
     unsigned int* stats = reinterpret_cast<unsigned int*>(m->partials);
     CK(cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned int), c->stream));
     CK(launch_invert(L, m->md, m->wdev, reinterpret_cast<float4*>(m->fh), tol, max_iter, y_dev, stats));
+    // the scratch field overwrote the solver volume's zero border
+    CK(cudaMemsetAsync(m->fh, 0, (size_t)m->md.vd.np * m->nch * 4, c->stream));
     unsigned int st[2] = {0, 0};
     CK(cudaMemcpyAsync(st, stats, sizeof st, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -1424,8 +1439,8 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
     double ab[2] = {1.0, 0.0};
     CK(cudaMemcpyAsync(m->out + 8, ab, sizeof ab, cudaMemcpyHostToDevice, c->stream));
     // Inputs the timed kernel reads: f/h at the warm-start w, p and q.
-    CK(launch_warp(L, m->md, m->st->w, kWarpFH, m->fh, nullptr, nullptr));
-    CK(launch_warp(L, m->md, m->st->w, kWarpFPad, m->fpad, nullptr, nullptr));
+    CK(launch_warp(L, m->md, m->st->w, kWarpFH, m->fh, nullptr, nullptr, m->sup));
+    CK(launch_warp(L, m->md, m->st->w, kWarpFPad, m->fpad, nullptr, nullptr, m->sup));
     if (which == PR_KERNEL_BACKPROJECT) CK(launch_warp(L, m->md, m->st->w, kWarpFlatFH, nullptr, nullptr, m->hbuf));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, m->order, nu, nv, m->p, m->q, nullptr, nullptr, nullptr, nullptr,
                       kPhaseNone, 0, 0, sref(m, m->st->w), &m->ss));
@@ -1442,7 +1457,7 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
     if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
     for (int i = 0; i < iters && err == cudaSuccess; ++i) {
         switch (which) {
-            case PR_KERNEL_WARP_FH: err = launch_warp(L, m->md, m->st->w, kWarpFH, m->fh, nullptr, nullptr); break;
+            case PR_KERNEL_WARP_FH: err = launch_warp(L, m->md, m->st->w, kWarpFH, m->fh, nullptr, nullptr, m->sup); break;
             case PR_KERNEL_PROJECT_FH:
                 err = launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, m->order, nu, nv, m->p, m->q, nullptr, nullptr,
                                      nullptr, nullptr, kPhaseNone, 0, 0, sref(m, m->st->w), &m->ss);
@@ -1454,7 +1469,7 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
                 err = launch_backproject(L, m->md.vd, m->rg, m->p, nullptr, m->hbuf, m->K, m->partials, m->counter,
                                          m->out, bp_table(m, angle));
                 break;
-            case PR_KERNEL_WARP_F: err = launch_warp(L, m->md, m->st->w, kWarpFPad, m->fpad, nullptr, nullptr); break;
+            case PR_KERNEL_WARP_F: err = launch_warp(L, m->md, m->st->w, kWarpFPad, m->fpad, nullptr, nullptr, m->sup); break;
             case PR_KERNEL_PROJECT_F:
                 err = launch_project(L, m->md.vd, m->fpad, 1, 0, m->rg, m->order, nu, nv, m->r, nullptr, nullptr, nullptr,
                                      nullptr, nullptr, kPhaseNone, 0, 0, sref(m, m->st->w));
@@ -1475,6 +1490,8 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
     if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    if (which == PR_KERNEL_INVERT && err == cudaSuccess)  // restore the zero border (the field was scratch)
+        err = cudaMemsetAsync(m->fh, 0, (size_t)m->md.vd.np * m->nch * 4, c->stream);
     if (ytmp || sst) {
         cudaError_t e2 = cudaStreamSynchronize(c->stream);
         if (ytmp) cudaFree(ytmp);

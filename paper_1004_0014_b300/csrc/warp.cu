@@ -9,6 +9,13 @@
 // with the eigenvector values already in registers. The pass is HBM-bound:
 // 12 + 12K bytes of field reads per voxel (float32) against 4 bytes of f
 // (+4K of h) written; the f0 taps hit L1/L2.
+//
+// For the padded outputs that only the projector reads, a block whose 1024
+// voxels all lie outside the support box of the warped volume at w (the
+// displacement bound around the nonzero voxels of f0) writes their zeros
+// without reading any field: the result is the same volume, and the field
+// stream shrinks to the blocks that meet the box. The decision is one per
+// block, so the evaluating threads carry no extra state.
 #include "internal.h"
 
 namespace pr {
@@ -26,8 +33,78 @@ struct WarpArgs {
     float* out_pad;  // kWarpFH: interleaved (nch floats per voxel); kWarpFPad: planar
     float* f_flat;
     float* h_flat;
+    const Support* sup;  // padded modes: skip the field reads outside the support box (nullable)
     int vec_ok;      // N % 4 == 0: planes are 16-byte aligned for vector loads
 };
+
+// Voxel box that may hold nonzero f or h at coefficients w. The pull-back
+// point of voxel v lies within |x_c| / dx_c <= d_c voxels of v, and f, h are
+// nonzero only where it is less than one cell from a nonzero f0 voxel, i.e.
+// for v_c in (lo_c - 1 - d_c, hi_c + 1 + d_c). support_box returns the
+// projector's sample box, one voxel wider on each side; that box, rounded
+// outward, is used here, so every voxel outside it is an exact zero.
+__device__ __forceinline__ void warp_box(const Support* sup, const VolDev& vd, const double* w, int K, int lo[3],
+                                         int hi[3]) {
+    const int n[3] = {vd.nx, vd.ny, vd.nz};
+    if (!sup) {
+        for (int c = 0; c < 3; ++c) lo[c] = 0, hi[c] = n[c] - 1;
+        return;
+    }
+    float flo[3], fhi[3];
+    const bool any = support_box(*sup, vd, w, K, flo, fhi);
+    for (int c = 0; c < 3; ++c) {
+        // flo, fhi lie in [-1, n] (NaN coefficients give the whole grid)
+        lo[c] = any ? max((int)floorf(flo[c]), 0) : 1;
+        hi[c] = any ? min((int)ceilf(fhi[c]), n[c] - 1) : 0;
+    }
+}
+
+// Whether any voxel of the flat range [vb, ve] lies in the inclusive box
+// (lo x, y, z, hi x, y, z): the range's rows are tested one by one.
+__device__ __forceinline__ bool range_in_box(const VolDev& vd, long long vb, long long ve, const int* box) {
+    for (long long r = vb / vd.nx; r <= ve / vd.nx; ++r) {
+        const int j = (int)(r % vd.ny), kz = (int)(r / vd.ny);
+        if (j < box[1] || j > box[4] || kz < box[2] || kz > box[5]) continue;
+        const long long row = r * vd.nx;
+        const int ia = (int)(max(vb, row) - row), ib = (int)(min(ve, row + vd.nx - 1) - row);
+        if (ib >= box[0] && ia <= box[3]) return true;
+    }
+    return false;
+}
+
+// Zeros for the voxels v0..v0+3 (those below n) in the padded output layout.
+template <int K, int MODE, typename TS>
+__device__ __forceinline__ void zero4(const WarpArgs<TS>& A, long long v0) {
+    constexpr int kNch = K <= 3 ? 4 : (K <= 5 ? 6 : 8);
+    const VolDev& vd = A.vd;
+    const long long jk = v0 / vd.nx;
+    int i = (int)(v0 - jk * vd.nx), j = (int)(jk % vd.ny), kz = (int)(jk / vd.ny);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (v0 + e < vd.n) {
+            const long long pidx = ((long long)(kz + 1) * vd.nyp + (j + 1)) * vd.nxp + (i + 1);
+            if (MODE == kWarpFH) {
+                if (kNch == 6) {
+                    reinterpret_cast<float4*>(A.out_pad)[pidx] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    reinterpret_cast<float2*>(A.out_pad + 4 * vd.np)[pidx] = make_float2(0.0f, 0.0f);
+                } else {
+                    float4* dst = reinterpret_cast<float4*>(A.out_pad + pidx * kNch);
+#pragma unroll
+                    for (int c4 = 0; c4 < kNch / 4; ++c4) dst[c4] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                }
+            } else {
+                A.out_pad[pidx] = 0.0f;
+            }
+        }
+        if (++i == vd.nx) {
+            i = 0;
+            if (++j == vd.ny) {
+                j = 0;
+                ++kz;
+            }
+        }
+    }
+}
 
 __device__ __forceinline__ float lerp(float a, float b, float t) { return __fmaf_rn(t, b - a, a); }
 
@@ -133,8 +210,26 @@ template <int K, int MODE, typename TS>
 __global__ void __launch_bounds__(kWarpThreads) k_warp(WarpArgs<TS> A) {
     const VolDev& vd = A.vd;
     long long v0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * 4;
-    if (v0 >= vd.n) return;
     const long long n = vd.n;
+
+    if ((MODE == kWarpFH || MODE == kWarpFPad) && A.sup) {
+        // one decision per block: a block none of whose voxels lies in the
+        // support box writes zeros and reads no field
+        __shared__ int block_in;
+        if (threadIdx.x == 0) {
+            int lo[3], hi[3];
+            warp_box(A.sup, vd, A.w, K, lo, hi);
+            const int box[6] = {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]};
+            const long long vb = blockIdx.x * (long long)blockDim.x * 4;
+            block_in = vb < n && range_in_box(vd, vb, min(vb + 4LL * blockDim.x, n) - 1, box);
+        }
+        __syncthreads();
+        if (!block_in) {
+            if (v0 < n) zero4<K, MODE, TS>(A, v0);
+            return;
+        }
+    }
+    if (v0 >= n) return;
 
     float w[K];
 #pragma unroll
@@ -167,9 +262,15 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp(WarpArgs<TS> A) {
     warp4<K, MODE, TS>(A, v0, w, mx, u);
 }
 
+__global__ void k_warp_box(VolDev vd, const double* __restrict__ w, int K, const Support* __restrict__ sup, int* box) {
+    int lo[3], hi[3];
+    warp_box(sup, vd, w, K, lo, hi);
+    for (int c = 0; c < 3; ++c) box[c] = lo[c], box[3 + c] = hi[c];
+}
+
 template <int K, typename TS>
 cudaError_t dispatch_mode(Launcher& L, const ModelDev& m, const double* w, int mode, float* out_pad,
-                          float* f_flat, float* h_flat) {
+                          float* f_flat, float* h_flat, const Support* sup) {
     WarpArgs<TS> A;
     A.f0p = static_cast<const TS*>(m.f0p);
     A.mean = m.mean;
@@ -179,6 +280,7 @@ cudaError_t dispatch_mode(Launcher& L, const ModelDev& m, const double* w, int m
     A.out_pad = out_pad;
     A.f_flat = f_flat;
     A.h_flat = h_flat;
+    A.sup = (mode == kWarpFH || mode == kWarpFPad) ? sup : nullptr;
     A.vec_ok = (m.vd.n % 4 == 0) ? 1 : 0;
     long long threads = (m.vd.n + 3) / 4;
     dim3 grid((unsigned)((threads + kWarpThreads - 1) / kWarpThreads));
@@ -193,15 +295,15 @@ cudaError_t dispatch_mode(Launcher& L, const ModelDev& m, const double* w, int m
 
 template <typename TS>
 cudaError_t dispatch_k(Launcher& L, const ModelDev& m, const double* w, int mode, float* out_pad,
-                       float* f_flat, float* h_flat) {
+                       float* f_flat, float* h_flat, const Support* sup) {
     switch (m.K) {
-        case 1: return dispatch_mode<1, TS>(L, m, w, mode, out_pad, f_flat, h_flat);
-        case 2: return dispatch_mode<2, TS>(L, m, w, mode, out_pad, f_flat, h_flat);
-        case 3: return dispatch_mode<3, TS>(L, m, w, mode, out_pad, f_flat, h_flat);
-        case 4: return dispatch_mode<4, TS>(L, m, w, mode, out_pad, f_flat, h_flat);
-        case 5: return dispatch_mode<5, TS>(L, m, w, mode, out_pad, f_flat, h_flat);
-        case 6: return dispatch_mode<6, TS>(L, m, w, mode, out_pad, f_flat, h_flat);
-        case 7: return dispatch_mode<7, TS>(L, m, w, mode, out_pad, f_flat, h_flat);
+        case 1: return dispatch_mode<1, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup);
+        case 2: return dispatch_mode<2, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup);
+        case 3: return dispatch_mode<3, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup);
+        case 4: return dispatch_mode<4, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup);
+        case 5: return dispatch_mode<5, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup);
+        case 6: return dispatch_mode<6, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup);
+        case 7: return dispatch_mode<7, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup);
     }
     return cudaErrorInvalidValue;
 }
@@ -228,9 +330,13 @@ cudaError_t launch_to_bf16(Launcher& L, const float* src, __nv_bfloat16* dst, lo
 }
 
 cudaError_t launch_warp(Launcher& L, const ModelDev& m, const double* w_dev, int mode, float* out_pad,
-                        float* f_flat, float* h_flat) {
-    if (m.storage == 1) return dispatch_k<__nv_bfloat16>(L, m, w_dev, mode, out_pad, f_flat, h_flat);
-    return dispatch_k<float>(L, m, w_dev, mode, out_pad, f_flat, h_flat);
+                        float* f_flat, float* h_flat, const Support* sup) {
+    if (m.storage == 1) return dispatch_k<__nv_bfloat16>(L, m, w_dev, mode, out_pad, f_flat, h_flat, sup);
+    return dispatch_k<float>(L, m, w_dev, mode, out_pad, f_flat, h_flat, sup);
+}
+
+cudaError_t launch_warp_box(Launcher& L, const ModelDev& m, const double* w_dev, const Support* sup, int* box_dev) {
+    return L(k_warp_box, dim3(1), dim3(1), 0, m.vd, w_dev, m.K, sup, box_dev);
 }
 
 cudaError_t launch_pad(Launcher& L, const VolDev& vd, const float* src, float* dst_pad) {
