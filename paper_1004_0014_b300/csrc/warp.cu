@@ -60,14 +60,22 @@ __device__ __forceinline__ void warp_box(const Support* sup, const VolDev& vd, c
 }
 
 // Whether any voxel of the flat range [vb, ve] lies in the inclusive box
-// (lo x, y, z, hi x, y, z): the range's rows are tested one by one.
-__device__ __forceinline__ bool range_in_box(const VolDev& vd, long long vb, long long ve, const int* box) {
-    for (long long r = vb / vd.nx; r <= ve / vd.nx; ++r) {
-        const int j = (int)(r % vd.ny), kz = (int)(r / vd.ny);
-        if (j < box[1] || j > box[4] || kz < box[2] || kz > box[5]) continue;
-        const long long row = r * vd.nx;
-        const int ia = (int)(max(vb, row) - row), ib = (int)(min(ve, row + vd.nx - 1) - row);
-        if (ib >= box[0] && ia <= box[3]) return true;
+// (lo x, y, z, hi x, y, z): the range's rows are tested one by one. 32-bit
+// index arithmetic: a model's padded grid has fewer than 2^29 voxels.
+__device__ __forceinline__ bool range_in_box(const VolDev& vd, int vb, int ve, const int* box) {
+    const int nx = vd.nx, ny = vd.ny;
+    const int r0 = vb / nx, r1 = ve / nx;
+    int j = r0 % ny, kz = r0 / ny;
+    for (int r = r0; r <= r1; ++r) {
+        if (j >= box[1] && j <= box[4] && kz >= box[2] && kz <= box[5]) {
+            const int row = r * nx;
+            const int ia = max(vb, row) - row, ib = min(ve, row + nx - 1) - row;
+            if (ib >= box[0] && ia <= box[3]) return true;
+        }
+        if (++j == ny) {
+            j = 0;
+            ++kz;
+        }
     }
     return false;
 }
@@ -77,18 +85,18 @@ template <int K, int MODE, typename TS>
 __device__ __forceinline__ void zero4(const WarpArgs<TS>& A, long long v0) {
     constexpr int kNch = K <= 3 ? 4 : (K <= 5 ? 6 : 8);
     const VolDev& vd = A.vd;
-    const long long jk = v0 / vd.nx;
-    int i = (int)(v0 - jk * vd.nx), j = (int)(jk % vd.ny), kz = (int)(jk / vd.ny);
+    const int jk = (int)v0 / vd.nx;
+    int i = (int)v0 - jk * vd.nx, j = jk % vd.ny, kz = jk / vd.ny;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         if (v0 + e < vd.n) {
-            const long long pidx = ((long long)(kz + 1) * vd.nyp + (j + 1)) * vd.nxp + (i + 1);
+            const int pidx = ((kz + 1) * vd.nyp + (j + 1)) * vd.nxp + (i + 1);
             if (MODE == kWarpFH) {
                 if (kNch == 6) {
                     reinterpret_cast<float4*>(A.out_pad)[pidx] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                     reinterpret_cast<float2*>(A.out_pad + 4 * vd.np)[pidx] = make_float2(0.0f, 0.0f);
                 } else {
-                    float4* dst = reinterpret_cast<float4*>(A.out_pad + pidx * kNch);
+                    float4* dst = reinterpret_cast<float4*>(A.out_pad + (long long)pidx * kNch);
 #pragma unroll
                     for (int c4 = 0; c4 < kNch / 4; ++c4) dst[c4] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 }
@@ -117,11 +125,12 @@ __device__ __forceinline__ void warp4(const WarpArgs<TS>& A, long long v0, const
     constexpr int kNch = K <= 3 ? 4 : (K <= 5 ? 6 : 8);
     const VolDev& vd = A.vd;
     const long long n = vd.n;
-    long long jk = v0 / vd.nx;
-    int i = (int)(v0 - jk * vd.nx);
-    int j = (int)(jk % vd.ny);
-    int kz = (int)(jk / vd.ny);
-    const long long plane = (long long)vd.nxp * vd.nyp;
+    // 32-bit index arithmetic: a model's padded grid has fewer than 2^29 voxels
+    const int jk = (int)v0 / vd.nx;
+    int i = (int)v0 - jk * vd.nx;
+    int j = jk % vd.ny;
+    int kz = jk / vd.ny;
+    const int plane = vd.nxp * vd.nyp;
 
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -149,7 +158,7 @@ __device__ __forceinline__ void warp4(const WarpArgs<TS>& A, long long v0, const
             int cx = in_x ? i + (int)fux : -2, cy = in_y ? j + (int)fuy : -2, cz = in_z ? kz + (int)fuz : -2;
             if ((cx > -1 || (cx == -1 && tx > 0.0f)) && cx < vd.nx && (cy > -1 || (cy == -1 && ty > 0.0f)) &&
                 cy < vd.ny && (cz > -1 || (cz == -1 && tz > 0.0f)) && cz < vd.nz) {
-                long long base = ((long long)(cz + 1) * vd.nyp + (cy + 1)) * vd.nxp + (cx + 1);
+                const int base = ((cz + 1) * vd.nyp + (cy + 1)) * vd.nxp + (cx + 1);
                 const TS* c0 = A.f0p + base;
                 float c000 = ld_val(c0), c100 = ld_val(c0 + 1);
                 float c010 = ld_val(c0 + vd.nxp), c110 = ld_val(c0 + vd.nxp + 1);
@@ -171,7 +180,7 @@ __device__ __forceinline__ void warp4(const WarpArgs<TS>& A, long long v0, const
             for (int k = 0; k < K; ++k)
                 h[k] = kH ? __fmaf_rn(gz, u[k][2][e], __fmaf_rn(gy, u[k][1][e], gx * u[k][0][e])) : 0.0f;
 
-            long long pidx = ((long long)(kz + 1) * vd.nyp + (j + 1)) * vd.nxp + (i + 1);
+            const int pidx = ((kz + 1) * vd.nyp + (j + 1)) * vd.nxp + (i + 1);
             if (MODE == kWarpFH) {
                 float o[kNch];
                 o[0] = val;
@@ -181,7 +190,7 @@ __device__ __forceinline__ void warp4(const WarpArgs<TS>& A, long long v0, const
                     reinterpret_cast<float4*>(A.out_pad)[pidx] = make_float4(o[0], o[1], o[2], o[3]);
                     reinterpret_cast<float2*>(A.out_pad + 4 * vd.np)[pidx] = make_float2(o[4], o[5 < kNch ? 5 : 0]);
                 } else {
-                    float4* dst = reinterpret_cast<float4*>(A.out_pad + pidx * kNch);
+                    float4* dst = reinterpret_cast<float4*>(A.out_pad + (long long)pidx * kNch);
 #pragma unroll
                     for (int c4 = 0; c4 < kNch / 4; ++c4)
                         dst[c4] = make_float4(o[4 * c4], o[4 * c4 + 1], o[4 * c4 + 2], o[4 * c4 + 3]);
@@ -221,7 +230,7 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp(WarpArgs<TS> A) {
             warp_box(A.sup, vd, A.w, K, lo, hi);
             const int box[6] = {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]};
             const long long vb = blockIdx.x * (long long)blockDim.x * 4;
-            block_in = vb < n && range_in_box(vd, vb, min(vb + 4LL * blockDim.x, n) - 1, box);
+            block_in = vb < n && range_in_box(vd, (int)vb, (int)(min(vb + 4LL * blockDim.x, n) - 1), box);
         }
         __syncthreads();
         if (!block_in) {
