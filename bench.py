@@ -484,9 +484,10 @@ def run_ours(args):
                 "achieved_gbs": bytes_proj / (kern["project_fh_trial"] / 1000.0) / 1e9}
     ts = 2 if bf16 else 4  # bytes per stored value of f0 and U
     # the solver's warp evaluates the blocks that meet the support box at w;
-    # the others only write their zeros
+    # with w repeated (the timing loop) the others hold zeros already and are
+    # left alone
     n_eval = warp_voxels_evaluated(vol, ctx.warp_box(mid, w_start))
-    bytes_warp = n_eval * (12 + 3 * ts * Km + ts + 4 * nch) + (N - n_eval) * 4 * nch
+    bytes_warp = n_eval * (12 + 3 * ts * Km + ts + 4 * nch)
     warp_gbs = bytes_warp / (kern["warp_fh"] / 1000.0) / 1e9
     roofline_warp = {"kernel": "k_warp<%d, f+h, %s>" % (Km, "bf16" if bf16 else "float"), "bound": "hbm",
                      "achieved": warp_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": warp_gbs / hbm_peak,

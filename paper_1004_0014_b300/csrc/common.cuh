@@ -91,6 +91,29 @@ __device__ __forceinline__ bool support_box(const Support& s, const VolDev& vd, 
     return any;
 }
 
+// Voxel box that may hold nonzero f or h at coefficients w. The pull-back
+// point of voxel v lies within |x_c| / dx_c <= d_c voxels of v, and f, h are
+// nonzero only where it is less than one cell from a nonzero f0 voxel, i.e.
+// for v_c in (lo_c - 1 - d_c, hi_c + 1 + d_c). support_box returns the
+// projector's sample box, one voxel wider on each side; that box, rounded
+// outward and widened by `grow` voxels, is returned, so every voxel outside it
+// is an exact zero. Without a support record: the whole grid.
+__device__ __forceinline__ void warp_box(const Support* sup, const VolDev& vd, const double* w, int K, int lo[3],
+                                         int hi[3], int grow = 0) {
+    const int n[3] = {vd.nx, vd.ny, vd.nz};
+    if (!sup) {
+        for (int c = 0; c < 3; ++c) lo[c] = 0, hi[c] = n[c] - 1;
+        return;
+    }
+    float flo[3], fhi[3];
+    const bool any = support_box(*sup, vd, w, K, flo, fhi);
+    for (int c = 0; c < 3; ++c) {
+        // flo, fhi lie in [-1, n] (NaN coefficients give the whole grid)
+        lo[c] = any ? max((int)floorf(flo[c]) - grow, 0) : 1;
+        hi[c] = any ? min((int)ceilf(fhi[c]) + grow, n[c] - 1) : 0;
+    }
+}
+
 // Solver phases handled by the controller in the last block of a reduction.
 enum Phase : int {
     kPhaseNone = 0,   // plain projection, no reduction
@@ -127,6 +150,11 @@ struct SolveState {
     double mu_next;  // first trial step of the next iteration or warm-started solve (0 = none)
     double w_prev[8];  // final w of the solve before the last one (for the predictor)
     int history;       // warm-started solves in a row with a known final w (0, 1, >= 2)
+    // Voxel box (lo x, y, z, hi x, y, z) that every 1024-voxel block of the
+    // model's (f, h) volume holding a nonzero meets; all zeros (a one-voxel
+    // box) is valid for the all-zero volume of a freshly loaded model. Written
+    // by the controller after each solver pass, read by the next warp pass.
+    int fh_box[6];
 };
 
 // ---------------------------------------------------------------------------

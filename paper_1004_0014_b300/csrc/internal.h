@@ -35,13 +35,20 @@ inline int fh_channels(int K) { return K <= 3 ? 4 : (K <= 5 ? 6 : 8); }
 // w_dev: K doubles in device memory. sup (device, nullable; padded modes
 // only): the model's support record; voxels outside the support box at w_dev
 // are exact zeros and are written as zeros without reading their fields.
+// dirty (device, 6 ints, nullable; with sup): a box that every 1024-voxel
+// block of out_pad holding a nonzero meets; blocks that miss both it and the
+// support box are not written. The caller keeps it valid after the pass (the
+// solve's controller records the pass's box; other callers use
+// launch_warp_box).
 cudaError_t launch_warp(Launcher& L, const ModelDev& m, const double* w_dev, int mode, float* out_pad,
-                        float* f_flat, float* h_flat, const Support* sup = nullptr);
+                        float* f_flat, float* h_flat, const Support* sup = nullptr, const int* dirty = nullptr);
 
 // Voxel box [lo, hi] (per axis, clamped to the grid; empty when lo > hi) that
-// the support-restricted warp evaluates at coefficients w_dev, written as six
-// ints (lo x, y, z, hi x, y, z) to box_dev.
-cudaError_t launch_warp_box(Launcher& L, const ModelDev& m, const double* w_dev, const Support* sup, int* box_dev);
+// the support-restricted warp evaluates at coefficients w_dev, widened by
+// `grow` voxels, written as six ints (lo x, y, z, hi x, y, z) to box_dev.
+// sup == nullptr gives the whole grid.
+cudaError_t launch_warp_box(Launcher& L, const ModelDev& m, const double* w_dev, const Support* sup, int grow,
+                            int* box_dev);
 
 // Round float32 to bfloat16 (round-to-nearest-even), n elements.
 cudaError_t launch_to_bf16(Launcher& L, const float* src, __nv_bfloat16* dst, long long n);

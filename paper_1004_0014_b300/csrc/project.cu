@@ -395,9 +395,18 @@ __device__ void finish_point(SolveState* st, const double* m, int K, cudaGraphCo
 
 template <int KM>
 __device__ void controller_project(SolveState* st, const double* m, int phase, cudaGraphConditionalHandle h,
-                                   int use_graph) {
+                                   int use_graph, const Support* sup, const VolDev& vd) {
     const int K = st->prm.K;
     double a, b;
+    // The (f, h) volume of this pass holds nonzeros only in blocks that meet
+    // the warp's support box at wt; recorded one voxel wider (the warp forms
+    // the same box in another kernel, where rounding may differ by an ulp)
+    // so that the next warp pass can leave the other blocks alone.
+    {
+        int lo[3], hi[3];
+        warp_box(sup, vd, st->wt, K, lo, hi, 1);
+        for (int c = 0; c < 3; ++c) st->fh_box[c] = lo[c], st->fh_box[3 + c] = hi[c];
+    }
     if (phase == kPhaseInit) {
         // Eq. 4 at the starting w, then the cost and gradient there
         if (st->stop == 0 && !fit_ab(st, m[2], m[1], &a, &b)) st->stop = 5;  // singular fit
@@ -589,7 +598,7 @@ __global__ void __launch_bounds__(kProjThreads, NCH == 4 ? 4 : 1) k_project(Proj
     total_partials<NV, kProjMom>(A.partials, nblocks, tot);
     if (threadIdx.x == 0) {
         *A.counter = 0;
-        controller_project<KM>(A.st, tot, A.phase, A.h, A.use_graph);
+        controller_project<KM>(A.st, tot, A.phase, A.h, A.use_graph, A.sup.sup, A.vd);
     }
 }
 
@@ -740,7 +749,7 @@ __device__ __noinline__ void finish_tile(const SplitArgs& A, int tile, int iu, i
     for (int m = 0; m < NV; ++m) tot[m] = warp_sum(tot[m]);
     if (lane == 0) {
         A.ctr[2] = 0;
-        controller_project<KM>(A.st, tot, A.phase, A.h, A.use_graph);
+        controller_project<KM>(A.st, tot, A.phase, A.h, A.use_graph, A.sup.sup, A.vd);
     }
 }
 

@@ -397,7 +397,7 @@ int build_graph(pr_ctx* c, Model* m) {
     L.graph = m->graph;
     SolveState* st = m->st;
     CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
-    CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup));
+    CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup, st->fh_box));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseInit, m->hloop, 1, sref(m, st->wt), &m->ss));
     cudaGraphNodeParams cp = {};
@@ -409,7 +409,7 @@ int build_graph(pr_ctx* c, Model* m) {
     CK(cudaGraphAddNode(&cond, m->graph, &L.last, nullptr, 1, &cp));
     Launcher B;
     B.graph = cp.conditional.phGraph_out[0];
-    CK(launch_warp(B, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup));
+    CK(launch_warp(B, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup, st->fh_box));
     CK(launch_project(B, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseTrial, m->hloop, 1, sref(m, st->wt), &m->ss));
     L.last = cond;
@@ -425,7 +425,7 @@ int host_loop(pr_ctx* c, Model* m, int opt_max_iters, int opt_max_bt) {
     L.stream = c->stream;
     SolveState* st = m->st;
     CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
-    CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup));
+    CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup, st->fh_box));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseInit, 0, 0, sref(m, st->wt), &m->ss));
     long long guard = 0, bound = (long long)(opt_max_iters + 1) * (opt_max_bt + 1) + 2;
@@ -434,7 +434,7 @@ int host_loop(pr_ctx* c, Model* m, int opt_max_iters, int opt_max_bt) {
         CK(cudaStreamSynchronize(c->stream));
         if (!m->st_host->running) break;
         if (++guard > bound) return fail(PR_ETIMEOUT, "host loop exceeded its trial bound");
-        CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup));
+        CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup, st->fh_box));
         CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y,
                           st, m->partials, m->counter, kPhaseTrial, 0, 0, sref(m, st->wt), &m->ss));
         }
@@ -619,7 +619,7 @@ int add_solve_nodes(cudaGraph_t g, Model* m, const cudaGraphNode_t* dep, const f
     L.last = np;
     L.has_last = true;
     CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
-    CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup));
+    CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup, st->fh_box));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseInit, h, 1, sref(m, st->wt), &m->ss));
     cudaGraphNodeParams cp = {};
@@ -631,7 +631,7 @@ int add_solve_nodes(cudaGraph_t g, Model* m, const cudaGraphNode_t* dep, const f
     CK(cudaGraphAddNode(&cond, g, &L.last, nullptr, 1, &cp));
     Launcher B;
     B.graph = cp.conditional.phGraph_out[0];
-    CK(launch_warp(B, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup));
+    CK(launch_warp(B, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup, st->fh_box));
     CK(launch_project(B, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseTrial, h, 1, sref(m, st->wt), &m->ss));
     L.last = cond;
@@ -1261,7 +1261,7 @@ int pr_warp_box(pr_ctx* c, int id, const double* w, int box[6]) {
     Launcher L;
     L.stream = c->stream;
     int* dev = reinterpret_cast<int*>(m->partials);
-    CK(launch_warp_box(L, m->md, m->wdev, m->sup, dev));
+    CK(launch_warp_box(L, m->md, m->wdev, m->sup, 0, dev));
     CK(cudaMemcpyAsync(box, dev, 6 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return PR_OK;
@@ -1359,7 +1359,8 @@ int pr_cost_grad(pr_ctx* c, int id, const float* y_dev, double angle, const doub
     const int nu = m->geom.nu, nv = m->geom.nv;
     double res[8] = {0};
     if (mode == 0) {
-        CK(launch_warp(L, m->md, m->wdev, kWarpFH, m->fh, nullptr, nullptr, m->sup));
+        CK(launch_warp(L, m->md, m->wdev, kWarpFH, m->fh, nullptr, nullptr, m->sup, m->st->fh_box));
+        CK(launch_warp_box(L, m->md, m->wdev, m->sup, 1, m->st->fh_box));  // what the volume now holds
         CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, m->order, nu, nv, m->p, m->q, nullptr, nullptr, nullptr,
                           nullptr, kPhaseNone, 0, 0, sref(m, m->wdev), &m->ss));
         CK(launch_cost_grad(L, m->p, m->q, y_dev, m->R, m->K, m->out + 8, m->partials, m->counter, m->out));
@@ -1439,7 +1440,8 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
     double ab[2] = {1.0, 0.0};
     CK(cudaMemcpyAsync(m->out + 8, ab, sizeof ab, cudaMemcpyHostToDevice, c->stream));
     // Inputs the timed kernel reads: f/h at the warm-start w, p and q.
-    CK(launch_warp(L, m->md, m->st->w, kWarpFH, m->fh, nullptr, nullptr, m->sup));
+    CK(launch_warp(L, m->md, m->st->w, kWarpFH, m->fh, nullptr, nullptr, m->sup, m->st->fh_box));
+    CK(launch_warp_box(L, m->md, m->st->w, m->sup, 1, m->st->fh_box));  // what the volume now holds
     CK(launch_warp(L, m->md, m->st->w, kWarpFPad, m->fpad, nullptr, nullptr, m->sup));
     if (which == PR_KERNEL_BACKPROJECT) CK(launch_warp(L, m->md, m->st->w, kWarpFlatFH, nullptr, nullptr, m->hbuf));
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, m->order, nu, nv, m->p, m->q, nullptr, nullptr, nullptr, nullptr,
@@ -1457,7 +1459,9 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
     if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
     for (int i = 0; i < iters && err == cudaSuccess; ++i) {
         switch (which) {
-            case PR_KERNEL_WARP_FH: err = launch_warp(L, m->md, m->st->w, kWarpFH, m->fh, nullptr, nullptr, m->sup); break;
+            case PR_KERNEL_WARP_FH:  // as in a solve: the blocks outside both boxes are left alone
+                err = launch_warp(L, m->md, m->st->w, kWarpFH, m->fh, nullptr, nullptr, m->sup, m->st->fh_box);
+                break;
             case PR_KERNEL_PROJECT_FH:
                 err = launch_project(L, m->md.vd, m->fh, m->nch, m->K, m->rg, m->order, nu, nv, m->p, m->q, nullptr, nullptr,
                                      nullptr, nullptr, kPhaseNone, 0, 0, sref(m, m->st->w), &m->ss);

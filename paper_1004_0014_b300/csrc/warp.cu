@@ -34,30 +34,9 @@ struct WarpArgs {
     float* f_flat;
     float* h_flat;
     const Support* sup;  // padded modes: skip the field reads outside the support box (nullable)
+    const int* dirty;    // with sup: box of the blocks that may still hold nonzeros (nullable, see k_warp)
     int vec_ok;      // N % 4 == 0: planes are 16-byte aligned for vector loads
 };
-
-// Voxel box that may hold nonzero f or h at coefficients w. The pull-back
-// point of voxel v lies within |x_c| / dx_c <= d_c voxels of v, and f, h are
-// nonzero only where it is less than one cell from a nonzero f0 voxel, i.e.
-// for v_c in (lo_c - 1 - d_c, hi_c + 1 + d_c). support_box returns the
-// projector's sample box, one voxel wider on each side; that box, rounded
-// outward, is used here, so every voxel outside it is an exact zero.
-__device__ __forceinline__ void warp_box(const Support* sup, const VolDev& vd, const double* w, int K, int lo[3],
-                                         int hi[3]) {
-    const int n[3] = {vd.nx, vd.ny, vd.nz};
-    if (!sup) {
-        for (int c = 0; c < 3; ++c) lo[c] = 0, hi[c] = n[c] - 1;
-        return;
-    }
-    float flo[3], fhi[3];
-    const bool any = support_box(*sup, vd, w, K, flo, fhi);
-    for (int c = 0; c < 3; ++c) {
-        // flo, fhi lie in [-1, n] (NaN coefficients give the whole grid)
-        lo[c] = any ? max((int)floorf(flo[c]), 0) : 1;
-        hi[c] = any ? min((int)ceilf(fhi[c]), n[c] - 1) : 0;
-    }
-}
 
 // Whether any voxel of the flat range [vb, ve] lies in the inclusive box
 // (lo x, y, z, hi x, y, z): the range's rows are tested one by one. 32-bit
@@ -222,19 +201,26 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp(WarpArgs<TS> A) {
     const long long n = vd.n;
 
     if ((MODE == kWarpFH || MODE == kWarpFPad) && A.sup) {
-        // one decision per block: a block none of whose voxels lies in the
-        // support box writes zeros and reads no field
-        __shared__ int block_in;
+        // One decision per block: a block that meets the support box at w is
+        // evaluated; one that does not writes zeros and reads no field, unless
+        // it also misses the dirty box (A.dirty: every block that may still
+        // hold a nonzero from an earlier pass meets it), so that it holds
+        // zeros already and is left alone.
+        __shared__ int action;  // 0: already zero, 1: write zeros, 2: evaluate
         if (threadIdx.x == 0) {
+            int old[6];
+            if (A.dirty)
+                for (int c = 0; c < 6; ++c) old[c] = __ldcg(A.dirty + c);
             int lo[3], hi[3];
             warp_box(A.sup, vd, A.w, K, lo, hi);
             const int box[6] = {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]};
-            const long long vb = blockIdx.x * (long long)blockDim.x * 4;
-            block_in = vb < n && range_in_box(vd, (int)vb, (int)(min(vb + 4LL * blockDim.x, n) - 1), box);
+            const int vb = (int)(blockIdx.x * (long long)blockDim.x * 4);
+            const int ve = (int)(min((long long)vb + 4LL * blockDim.x, n) - 1);
+            action = range_in_box(vd, vb, ve, box) ? 2 : (!A.dirty || range_in_box(vd, vb, ve, old) ? 1 : 0);
         }
         __syncthreads();
-        if (!block_in) {
-            if (v0 < n) zero4<K, MODE, TS>(A, v0);
+        if (action != 2) {
+            if (action == 1 && v0 < n) zero4<K, MODE, TS>(A, v0);
             return;
         }
     }
@@ -271,15 +257,16 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp(WarpArgs<TS> A) {
     warp4<K, MODE, TS>(A, v0, w, mx, u);
 }
 
-__global__ void k_warp_box(VolDev vd, const double* __restrict__ w, int K, const Support* __restrict__ sup, int* box) {
+__global__ void k_warp_box(VolDev vd, const double* __restrict__ w, int K, const Support* __restrict__ sup, int grow,
+                           int* box) {
     int lo[3], hi[3];
-    warp_box(sup, vd, w, K, lo, hi);
+    warp_box(sup, vd, w, K, lo, hi, grow);
     for (int c = 0; c < 3; ++c) box[c] = lo[c], box[3 + c] = hi[c];
 }
 
 template <int K, typename TS>
 cudaError_t dispatch_mode(Launcher& L, const ModelDev& m, const double* w, int mode, float* out_pad,
-                          float* f_flat, float* h_flat, const Support* sup) {
+                          float* f_flat, float* h_flat, const Support* sup, const int* dirty) {
     WarpArgs<TS> A;
     A.f0p = static_cast<const TS*>(m.f0p);
     A.mean = m.mean;
@@ -290,6 +277,7 @@ cudaError_t dispatch_mode(Launcher& L, const ModelDev& m, const double* w, int m
     A.f_flat = f_flat;
     A.h_flat = h_flat;
     A.sup = (mode == kWarpFH || mode == kWarpFPad) ? sup : nullptr;
+    A.dirty = A.sup ? dirty : nullptr;
     A.vec_ok = (m.vd.n % 4 == 0) ? 1 : 0;
     long long threads = (m.vd.n + 3) / 4;
     dim3 grid((unsigned)((threads + kWarpThreads - 1) / kWarpThreads));
@@ -304,15 +292,15 @@ cudaError_t dispatch_mode(Launcher& L, const ModelDev& m, const double* w, int m
 
 template <typename TS>
 cudaError_t dispatch_k(Launcher& L, const ModelDev& m, const double* w, int mode, float* out_pad,
-                       float* f_flat, float* h_flat, const Support* sup) {
+                       float* f_flat, float* h_flat, const Support* sup, const int* dirty) {
     switch (m.K) {
-        case 1: return dispatch_mode<1, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup);
-        case 2: return dispatch_mode<2, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup);
-        case 3: return dispatch_mode<3, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup);
-        case 4: return dispatch_mode<4, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup);
-        case 5: return dispatch_mode<5, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup);
-        case 6: return dispatch_mode<6, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup);
-        case 7: return dispatch_mode<7, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup);
+        case 1: return dispatch_mode<1, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup, dirty);
+        case 2: return dispatch_mode<2, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup, dirty);
+        case 3: return dispatch_mode<3, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup, dirty);
+        case 4: return dispatch_mode<4, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup, dirty);
+        case 5: return dispatch_mode<5, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup, dirty);
+        case 6: return dispatch_mode<6, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup, dirty);
+        case 7: return dispatch_mode<7, TS>(L, m, w, mode, out_pad, f_flat, h_flat, sup, dirty);
     }
     return cudaErrorInvalidValue;
 }
@@ -339,13 +327,14 @@ cudaError_t launch_to_bf16(Launcher& L, const float* src, __nv_bfloat16* dst, lo
 }
 
 cudaError_t launch_warp(Launcher& L, const ModelDev& m, const double* w_dev, int mode, float* out_pad,
-                        float* f_flat, float* h_flat, const Support* sup) {
-    if (m.storage == 1) return dispatch_k<__nv_bfloat16>(L, m, w_dev, mode, out_pad, f_flat, h_flat, sup);
-    return dispatch_k<float>(L, m, w_dev, mode, out_pad, f_flat, h_flat, sup);
+                        float* f_flat, float* h_flat, const Support* sup, const int* dirty) {
+    if (m.storage == 1) return dispatch_k<__nv_bfloat16>(L, m, w_dev, mode, out_pad, f_flat, h_flat, sup, dirty);
+    return dispatch_k<float>(L, m, w_dev, mode, out_pad, f_flat, h_flat, sup, dirty);
 }
 
-cudaError_t launch_warp_box(Launcher& L, const ModelDev& m, const double* w_dev, const Support* sup, int* box_dev) {
-    return L(k_warp_box, dim3(1), dim3(1), 0, m.vd, w_dev, m.K, sup, box_dev);
+cudaError_t launch_warp_box(Launcher& L, const ModelDev& m, const double* w_dev, const Support* sup, int grow,
+                            int* box_dev) {
+    return L(k_warp_box, dim3(1), dim3(1), 0, m.vd, w_dev, m.K, sup, grow, box_dev);
 }
 
 cudaError_t launch_pad(Launcher& L, const VolDev& vd, const float* src, float* dst_pad) {
