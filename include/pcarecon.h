@@ -334,7 +334,8 @@ int pr_count_samples(pr_ctx* ctx, int model_id, double angle_rad, const double* 
  * outside it lie farther than the displacement bound from every nonzero f0
  * voxel and are exact zeros: a block of the pass (1024 consecutive voxels of
  * the flat grid) none of whose voxels is in the box writes its zeros without
- * reading a field. Synchronous. Errors: PR_EINVAL, PR_ENOMODEL, PR_ECUDA. */
+ * reading a field, or is left alone where no earlier pass can have left a
+ * nonzero in it. Synchronous. Errors: PR_EINVAL, PR_ENOMODEL, PR_ECUDA. */
 int pr_warp_box(pr_ctx* ctx, int model_id, const double* w, int box[6]);
 
 /* Section 5's fixed-angle geometry (fluoroscopy: the gantry does not move,
