@@ -253,6 +253,81 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float bhi, float bl
     hi = t;
 }
 
+// Recursive-halving warp sums of NV values (NV <= 32), P = NV rounded up to a
+// power of two. At each of log2(P) exchange levels (lane strides 16, 8, ...)
+// every lane gives half of its remaining values to its partner and adds the
+// partner's copy of the half it keeps; plain butterfly levels over the
+// remaining strides then finish the sums. Each lane ends with one total: that
+// of value `idx` (the return value; idx >= NV is padding), the same in the
+// 32 / P lanes lane / (32 / P) == idx. P - 1 + log2(32 / P) additions per
+// lane instead of 5 NV, and the sums come out spread over the lanes, so their
+// stores go out in parallel. The order of every addition is fixed by lane.
+template <int NV>
+struct Halving {
+    static_assert(NV >= 1 && NV <= 32, "1..32 values");
+    static constexpr int P = NV <= 1 ? 1 : NV <= 2 ? 2 : NV <= 4 ? 4 : NV <= 8 ? 8 : NV <= 16 ? 16 : 32;
+    static constexpr int kSpan = 32 / P;  // lanes holding the same total
+};
+
+template <int NV>
+__device__ __forceinline__ int warp_halving_sum(const double (&v)[NV], double& out) {
+    constexpr int P = Halving<NV>::P;
+    const int lane = threadIdx.x & 31;
+    double x[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) x[i] = i < NV ? v[i < NV ? i : 0] : 0.0;
+    int idx = 0;
+#pragma unroll
+    for (int lev = 0; (P >> lev) > 1; ++lev) {
+        const int half = P >> (lev + 1), s = 16 >> lev;
+        const bool up = (lane & s) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const double give = up ? x[i] : x[half + i], keep = up ? x[half + i] : x[i];
+            x[i] = keep + __shfl_xor_sync(0xffffffffu, give, s);
+        }
+        idx += up ? half : 0;
+    }
+#pragma unroll
+    for (int s = Halving<NV>::kSpan >> 1; s >= 1; s >>= 1) x[0] += __shfl_xor_sync(0xffffffffu, x[0], s);
+    out = x[0];
+    return idx;
+}
+
+// The same for float-float values (hi, lo); lane / (32 / P) == idx holds it.
+template <int NV>
+__device__ __forceinline__ int warp_halving_sum_ff(const float (&hi)[NV], const float (&lo)[NV], float& oh, float& ol) {
+    constexpr int P = Halving<NV>::P;
+    const int lane = threadIdx.x & 31;
+    float h[P], l[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        h[i] = i < NV ? hi[i < NV ? i : 0] : 0.0f;
+        l[i] = i < NV ? lo[i < NV ? i : 0] : 0.0f;
+    }
+    int idx = 0;
+#pragma unroll
+    for (int lev = 0; (P >> lev) > 1; ++lev) {
+        const int half = P >> (lev + 1), s = 16 >> lev;
+        const bool up = (lane & s) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float gh = up ? h[i] : h[half + i], gl = up ? l[i] : l[half + i];
+            float kh = up ? h[half + i] : h[i], kl = up ? l[half + i] : l[i];
+            ff_add(kh, kl, __shfl_xor_sync(0xffffffffu, gh, s), __shfl_xor_sync(0xffffffffu, gl, s));
+            h[i] = kh;
+            l[i] = kl;
+        }
+        idx += up ? half : 0;
+    }
+#pragma unroll
+    for (int s = Halving<NV>::kSpan >> 1; s >= 1; s >>= 1)
+        ff_add(h[0], l[0], __shfl_xor_sync(0xffffffffu, h[0], s), __shfl_xor_sync(0xffffffffu, l[0], s));
+    oh = h[0];
+    ol = l[0];
+    return idx;
+}
+
 // Block sum of NV float-float values in a fixed order: float-float within
 // each warp, FP64 across the warps; thread 0 gets the totals in out.
 template <int NV>

@@ -644,6 +644,58 @@ struct SplitArgs {
     SupportRef sup;
 };
 
+// The warp that completed a tile group: sums the group's tile moments in tile
+// order and, if it also completed the last group, the group sums in group
+// order, then runs the controller. Out of line and apart from finish_tile:
+// only one warp per group runs it, so its code and registers stay out of the
+// per-tile path.
+template <int NCH>
+__device__ __noinline__ void finish_group(const SplitArgs& A, int group) {
+    constexpr int KM = NCH == 8 ? 7 : (NCH == 6 ? 5 : 3);
+    constexpr int NV = 3 + 3 * KM;
+    const int lane = threadIdx.x & 31;
+    const int gsize = min(kGroupTiles, A.ntiles - group * kGroupTiles);
+    unsigned int prev = 0;
+    __threadfence();
+    if (lane == 0) A.ctr[4 + group] = 0;
+    double gm[NV];
+#pragma unroll
+    for (int m = 0; m < NV; ++m) gm[m] = 0.0;
+    for (int t = lane; t < gsize; t += 32)
+#pragma unroll
+        for (int m = 0; m < NV; ++m) gm[m] += __ldcg(A.tile_mom + (size_t)(group * kGroupTiles + t) * kProjMom + m);
+    {
+        double gs;
+        const int idx = warp_halving_sum<NV>(gm, gs);
+        if (lane % Halving<NV>::kSpan == 0 && idx < NV) A.group_mom[(size_t)group * kProjMom + idx] = gs;
+    }
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) prev = atomicAdd(A.ctr + 2, 1u);
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev != (unsigned int)A.ngroups - 1) return;
+
+    // ---- this warp completed the last group: totals in group order, controller ----
+    __threadfence();
+    double tot[NV];
+#pragma unroll
+    for (int m = 0; m < NV; ++m) tot[m] = 0.0;
+    for (int gg = lane; gg < A.ngroups; gg += 32)
+#pragma unroll
+        for (int m = 0; m < NV; ++m) tot[m] += __ldcg(A.group_mom + (size_t)gg * kProjMom + m);
+    {
+        double ts;
+        warp_halving_sum<NV>(tot, ts);
+        // gather the totals into lane 0 (total m sits in lane m * kSpan)
+#pragma unroll
+        for (int m = 0; m < NV; ++m) tot[m] = __shfl_sync(0xffffffffu, ts, m * Halving<NV>::kSpan);
+    }
+    if (lane == 0) {
+        A.ctr[2] = 0;
+        controller_project<KM>(A.st, tot, A.phase, A.h, A.use_graph, A.sup.sup, A.vd);
+    }
+}
+
 // The warp that completed a tile: adds its parts in part order, writes p and
 // q, and (solver phases) forms the tile's moments and carries the fixed-order
 // group and total sums. Kept out of line so that its registers do not weigh on
@@ -679,7 +731,8 @@ __device__ __noinline__ void finish_tile(const SplitArgs& A, int tile, int iu, i
     }
     if (A.phase == kPhaseNone) return;
 
-    // tile moments (see cost_at): exact float-float products, float-float warp sums
+    // tile moments (see cost_at): exact float-float products, float-float warp
+    // sums by recursive halving (each moment's total ends in its own lanes)
     float mh[NV], ml[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) mh[i] = ml[i] = 0.0f;
@@ -698,59 +751,18 @@ __device__ __noinline__ void finish_tile(const SplitArgs& A, int tile, int iu, i
             }
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int m = 0; m < NV; ++m) {
-            float bh = __shfl_down_sync(0xffffffffu, mh[m], o), bl = __shfl_down_sync(0xffffffffu, ml[m], o);
-            ff_add(mh[m], ml[m], bh, bl);
-        }
-    if (lane == 0) {
-#pragma unroll
-        for (int m = 0; m < NV; ++m) A.tile_mom[(size_t)tile * kProjMom + m] = (double)mh[m] + (double)ml[m];
-        __threadfence();
+    {
+        float th, tl;
+        const int idx = warp_halving_sum_ff<NV>(mh, ml, th, tl);
+        if (lane % Halving<NV>::kSpan == 0 && idx < NV)
+            A.tile_mom[(size_t)tile * kProjMom + idx] = (double)th + (double)tl;
     }
+    __threadfence();
     __syncwarp();
     const int group = tile / kGroupTiles;
-    const int gsize = min(kGroupTiles, A.ntiles - group * kGroupTiles);
     if (lane == 0) prev = atomicAdd(A.ctr + 4 + group, 1u);
     prev = __shfl_sync(0xffffffffu, prev, 0);
-    if (prev != (unsigned int)gsize - 1) return;
-
-    // ---- this warp completed the group: its tiles in tile order ----
-    __threadfence();
-    if (lane == 0) A.ctr[4 + group] = 0;
-    double gm[NV];
-#pragma unroll
-    for (int m = 0; m < NV; ++m) gm[m] = 0.0;
-    for (int t = lane; t < gsize; t += 32)
-#pragma unroll
-        for (int m = 0; m < NV; ++m) gm[m] += __ldcg(A.tile_mom + (size_t)(group * kGroupTiles + t) * kProjMom + m);
-#pragma unroll
-    for (int m = 0; m < NV; ++m) gm[m] = warp_sum(gm[m]);
-    if (lane == 0) {
-#pragma unroll
-        for (int m = 0; m < NV; ++m) A.group_mom[(size_t)group * kProjMom + m] = gm[m];
-        __threadfence();
-        prev = atomicAdd(A.ctr + 2, 1u);
-    }
-    prev = __shfl_sync(0xffffffffu, prev, 0);
-    if (prev != (unsigned int)A.ngroups - 1) return;
-
-    // ---- this warp completed the last group: totals in group order, controller ----
-    __threadfence();
-    double tot[NV];
-#pragma unroll
-    for (int m = 0; m < NV; ++m) tot[m] = 0.0;
-    for (int gg = lane; gg < A.ngroups; gg += 32)
-#pragma unroll
-        for (int m = 0; m < NV; ++m) tot[m] += __ldcg(A.group_mom + (size_t)gg * kProjMom + m);
-#pragma unroll
-    for (int m = 0; m < NV; ++m) tot[m] = warp_sum(tot[m]);
-    if (lane == 0) {
-        A.ctr[2] = 0;
-        controller_project<KM>(A.st, tot, A.phase, A.h, A.use_graph, A.sup.sup, A.vd);
-    }
+    if (prev == (unsigned int)min(kGroupTiles, A.ntiles - group * kGroupTiles) - 1) finish_group<NCH>(A, group);
 }
 
 template <int NCH>
