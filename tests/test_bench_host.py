@@ -1,0 +1,46 @@
+"""Host-side arithmetic of the benchmark's rooflines (no GPU): the count of
+voxels the support-restricted warp pass evaluates (blocks of 1024 consecutive
+voxels of the flat grid that meet the warp box) against a brute-force count,
+and the algorithmic flops per projector sample."""
+
+import numpy as np
+import pytest
+
+from phantom import Volume
+
+
+def _brute(vol, box, block=1024):
+    (x0, y0, z0), (x1, y1, z1) = box
+    n = vol.nx * vol.ny * vol.nz
+    total = 0
+    for b0 in range(0, n, block):
+        vs = np.arange(b0, min(b0 + block, n))
+        i, jk = vs % vol.nx, vs // vol.nx
+        j, k = jk % vol.ny, jk // vol.ny
+        hit = (i >= x0) & (i <= x1) & (j >= y0) & (j <= y1) & (k >= z0) & (k <= z1)
+        if hit.any():
+            total += len(vs)
+    return total
+
+
+@pytest.mark.parametrize("shape", [(13, 11, 9), (40, 36, 28), (256, 7, 5), (1, 1, 3000), (37, 1, 1)])
+def test_warp_voxels_evaluated_matches_brute_force(shape):
+    import bench
+
+    vol = Volume(*shape, 2.0, 2.0, 2.5)
+    rng = np.random.default_rng(sum(shape))
+    boxes = [((0, 0, 0), (vol.nx - 1, vol.ny - 1, vol.nz - 1)),  # whole grid
+             ((1, 1, 1), (0, 0, 0))]                              # empty box (all-zero volume)
+    for _ in range(12):
+        lo = [int(rng.integers(0, n)) for n in (vol.nx, vol.ny, vol.nz)]
+        hi = [int(rng.integers(l, n)) for l, n in zip(lo, (vol.nx, vol.ny, vol.nz))]
+        boxes.append((tuple(lo), tuple(hi)))
+    for box in boxes:
+        assert bench.warp_voxels_evaluated(vol, box) == _brute(vol, box), box
+
+
+def test_flops_per_sample():
+    import bench
+
+    # 8 corners x nch channels x multiply-add, 19 for the trilinear weights, 6 for the position
+    assert [bench.flops_per_sample(c) for c in (4, 6, 8)] == [89, 121, 153]
