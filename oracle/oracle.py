@@ -17,6 +17,7 @@ Functions and the passages they follow:
   gradient     gradient formula after Eq. 4: 2 U^T (df/dx) P^T (P f - a y - b 1)
   reconstruct  Section 2.2: alternate Eq. 3 (Armijo step on w) and Eq. 4
   tumor        Section 2.3 with the fixed-point inversion of ref. 13
+  invert       Section 2.3 with ref. 13: the push-forward field on the whole grid
 
 Readings of the paper where it is silent (the CUDA path uses the same):
   * Armijo rule (Section 2.2 names it, gives no constants): sufficient
