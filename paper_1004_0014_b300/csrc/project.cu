@@ -19,6 +19,7 @@
 #include "internal.h"
 
 #include <algorithm>
+#include <atomic>
 #include <utility>
 #include <vector>
 
@@ -1032,11 +1033,15 @@ void project_warp_tile_order(int nu, int nv, int* order) {
 namespace {
 // Resident blocks of the split projector on this device (computed once per device).
 int split_grid(int nch) {
-    static int cached[3][64] = {};
+    // per device and channel count; several host threads may ask at once (the
+    // serving worker and callers), and any of them may fill an entry: they all
+    // compute the same value
+    static std::atomic<int> cached[3][64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-    int& c = cached[nch == 8 ? 2 : (nch == 6 ? 1 : 0)][dev];
-    if (c == 0) {
+    std::atomic<int>& c = cached[nch == 8 ? 2 : (nch == 6 ? 1 : 0)][dev];
+    int v = c.load(std::memory_order_relaxed);
+    if (v == 0) {
         int sms = 0, per = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (nch == 8)
@@ -1045,9 +1050,10 @@ int split_grid(int nch) {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_project_split<6>, kSplitThreads, 0);
         else
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_project_split<4>, kSplitThreads, 0);
-        c = sms * (per > 0 ? per : 1);
+        v = sms * (per > 0 ? per : 1);
+        c.store(v, std::memory_order_relaxed);
     }
-    return c;
+    return v;
 }
 }  // namespace
 
