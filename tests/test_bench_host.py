@@ -1,7 +1,9 @@
-"""Host-side arithmetic of the benchmark's rooflines (no GPU): the count of
-voxels the support-restricted warp pass evaluates (blocks of 1024 consecutive
-voxels of the flat grid that meet the warp box) against a brute-force count,
-and the algorithmic flops per projector sample."""
+"""Host-side arithmetic of the benchmark (no GPU): the count of voxels the
+support-restricted warp pass evaluates (blocks of 1024 consecutive voxels of
+the flat grid that meet the warp box) against a brute-force count, the
+algorithmic flops per projector sample, the reading of the clock samples taken
+during the timed region (a run that saw a slowdown reason must say so), and
+the oracle's time per reconstruction."""
 
 import numpy as np
 import pytest
@@ -44,3 +46,39 @@ def test_flops_per_sample():
 
     # 8 corners x nch channels x multiply-add, 19 for the trilinear weights, 6 for the position
     assert [bench.flops_per_sample(c) for c in (4, 6, 8)] == [89, 121, 153]
+
+
+def _sampler(lines):
+    import bench
+
+    c = bench.ClockSampler(0)
+    c.lines = lines
+    return c.summary()
+
+
+def test_clock_summary_reports_slowdowns_and_busy_median():
+    # index, sm, max sm, power, active, hw_slowdown, hw_thermal, sw_thermal, sw_power_cap
+    lines = ["0, 2032, 2032, 700.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "0, 2032, 2032, 910.4, 0x4, Not Active, Not Active, Not Active, Active",
+             "0, 1980, 2032, 1050.0, 0x4, Not Active, Not Active, Not Active, Active",
+             "0, 345, 2032, 120.0, 0x0, Not Active, Not Active, Not Active, Not Active",  # idle sample
+             "garbage line",
+             "0, 2010, 2032, 990.0, 0x20, Not Active, Active, Not Active, Not Active"]
+    s = _sampler(lines)
+    assert s["samples"] == 5
+    assert s["sm_max_mhz"] == 2032.0
+    assert s["sm_mhz"] == 2021.0  # median of the busy samples (the 345 MHz one is idle)
+    assert s["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+
+
+def test_clock_summary_without_samples():
+    s = _sampler([])
+    assert s["samples"] == 0 and s["sm_mhz"] is None and s["reasons"] == ["no samples"]
+
+
+def test_oracle_reconstruction_time():
+    import bench
+
+    # Eq. 4 at the start costs one evaluation and one gradient; each trial one
+    # evaluation; each accepted step one gradient
+    assert bench.oracle_recon_seconds(2.0, 5.0, iters=10, trials=11) == 12 * 2.0 + 11 * 5.0
