@@ -21,32 +21,38 @@ Functions and the passages they follow:
 
 Readings of the paper where it is silent (the CUDA path uses the same):
   * Armijo rule (Section 2.2 names it, gives no constants): sufficient
-    decrease J(w - mu g; a, b) <= J(w; a, b) - c1 mu |g|^2 with c1 = 1e-4,
-    backtracking mu <- beta mu with beta = 0.5, at most 8 backtracks. The
-    first trial step is mu = step0_mm / |g| (moves w by step0_mm). Each trial
-    at mu measures the curvature of J along -g, curv = 2 (J(mu) - J + mu |g|^2)
-    / mu^2, and the quadratic model's minimiser |g|^2 / curv (the model is used
-    only where mu |g|^2 > 1e-6 J, i.e. where the step can visibly change J;
-    elsewhere the plain factors apply). With step_model 1
-    (default) steps are rounded down to powers of two of mu (so a step's
-    size cannot depend on the last bits of a cost): a rejected trial
-    backtracks to mu x pow2_floor(clamp(minimiser / mu, 1/16, beta)), and
-    after an accepted step the next first trial is mu x pow2_floor(clamp(
-    minimiser / mu, 1/2, step_growth)) (step_growth = 2: an accepted step is
-    at most halved, since near convergence the curvature of a cost
-    difference is mostly rounding); with step_model 0
-    backtracking is mu <- beta mu and the next first trial is step_growth x mu
-    if mu was accepted at its first trial, else step_growth_bt x mu. A solve
-    warm-started from the previous frame starts with that frame's next trial
-    step, as its w starts from that frame's w (Section 4 initialises each
-    frame from the previous one). No accepted step: w is kept, the solve
-    stops with stop reason "line search failed" and the next trial step is
-    forgotten.
+    decrease J(w - mu g; a, b) <= J(w; a, b) - c1 mu |g|^2 with c1 = 1e-4, at
+    most 8 backtracks. The first trial step is mu = step0_mm / |g| (moves w by
+    step0_mm). A solve warm-started from the previous frame starts with that
+    frame's next trial step, as its w starts from that frame's w (Section 4
+    initialises each frame from the previous one). No accepted step: w is
+    kept, the solve stops with stop reason "line search failed" and the next
+    trial step is forgotten.
+  * Trial steps, SolveOptions.step_model (one trial's decision is the pure
+    function step_choice):
+      0 (the default: plain backtracking, the textbook form of Armijo's rule)
+        a rejected trial backtracks mu <- beta mu (beta = 0.5); after an
+        accepted step the next first trial is step_growth x mu (2) if mu was
+        accepted at its first trial, else step_growth_bt x mu (1).
+      1 (the CUDA library's default rule) each trial at mu also measures the
+        curvature of J along -g, curv = 2 (J(mu) - J + mu |g|^2) / mu^2, whose
+        quadratic model J - mu |g|^2 + curv mu^2 / 2 has its minimum at
+        |g|^2 / curv; steps are that minimiser rounded down to a power of two
+        times mu: a rejected trial backtracks to mu x pow2_floor(clamp(
+        minimiser / mu, 1/16, beta)), and after an accepted step the next first
+        trial is mu x pow2_floor(clamp(minimiser / mu, 1/2, step_growth)).
+        Without a positive curvature the plain factors beta and step_growth
+        apply.
+  * Resolvability guard, SolveOptions.min_decrease (0 = off, the default;
+    the CUDA library runs step_model 1 with 1e-6, the relative resolution of
+    its FP32 cost at paper scale): the quadratic model is trusted only where
+    the trial's predicted decrease mu |g|^2 exceeds min_decrease |J|, and a
+    rejected trial below that threshold stops the solve ("resolved": no step
+    along -g can then lower J by an amount the cost resolves).
   * (a, b) before the first step 1: Eq. 4 at the starting w.
   * Stop (Section 2.2: gradient "sufficiently small" or the iteration cap):
-    |g| <= grad_tol * |g_0|, or max_iters accepted steps, or (step_model 1) a
-    rejected trial whose predicted decrease mu |g|^2 is already at most
-    1e-6 J: no step along -g can lower J by a resolvable amount.
+    |g| <= grad_tol * |g_0|, or max_iters accepted steps, or (with the guard
+    on) the resolved stop above.
 """
 
 from __future__ import annotations
@@ -62,10 +68,6 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
-
-# The quadratic step model is trusted only where a step's predicted decrease
-# mu |g|^2 exceeds this fraction of J.
-MODEL_MIN_DECREASE = 1e-6
 
 STOP_GRAD_TOL = 1
 STOP_MAX_ITERS = 2
@@ -292,6 +294,9 @@ def pow2_floor(x: float) -> float:
 
 @dataclasses.dataclass
 class SolveOptions:
+    """Section 2.2's solver constants. The defaults are the paper's rule:
+    Armijo backtracking by beta, stop on a small gradient or the cap."""
+
     max_iters: int = 10
     grad_tol: float = 1e-6
     c1: float = 1e-4
@@ -300,9 +305,37 @@ class SolveOptions:
     step0_mm: float = 1.0
     step_growth: float = 2.0
     step_growth_bt: float = 1.0
-    step_model: int = 1
+    step_model: int = 0        # 0: plain factors; 1: quadratic model, power-of-two steps
+    min_decrease: float = 0.0  # resolvability guard (0 = off), see the module docstring
     tumor_tol: float = 1e-6
     tumor_max_iter: int = 100
+
+
+def step_choice(J: float, J_t: float, mu: float, gn2: float, bt: int, o: SolveOptions):
+    """One line-search trial's decisions (Section 2.2, Armijo's rule) from the
+    cost J at w, the cost J_t at the trial w - mu g (same a, b), the step mu,
+    |g|^2 and the backtracks bt already taken in this step.
+
+    Returns (accepted, stop, factor): accepted is Armijo's sufficient-decrease
+    test; stop is the guard's resolved stop (rejected trials only); factor
+    scales mu for the next trial (the backtrack after a rejection, the next
+    step's first trial after an acceptance)."""
+    ok = J_t <= J - o.c1 * mu * gn2
+    resolvable = o.min_decrease <= 0.0 or mu * gn2 > o.min_decrease * abs(J)
+    # curvature of J along -g from this trial: J(mu) = J - mu |g|^2 + (curv/2) mu^2
+    curv = 2.0 * (J_t - J + mu * gn2) / (mu * mu)
+    use_model = o.step_model == 1 and resolvable and curv > 0.0 and math.isfinite(curv)
+    if ok:
+        if o.step_model == 1:
+            ratio = min(o.step_growth, gn2 / curv / mu) if use_model else o.step_growth
+            return True, False, pow2_floor(max(ratio, 0.5))
+        return True, False, (o.step_growth if bt == 0 else o.step_growth_bt)
+    if not resolvable:
+        return False, True, 1.0
+    if o.step_model == 1:
+        ratio = min(o.beta, max(1.0 / 16.0, gn2 / curv / mu)) if use_model else o.beta
+        return False, False, pow2_floor(ratio)
+    return False, False, o.beta
 
 
 @dataclasses.dataclass
@@ -366,32 +399,11 @@ def reconstruct(model, geom, angle, y, w0, opts: SolveOptions | None = None,
         for bt in range(o.max_backtracks + 1):
             trial = evaluate(model, geom, angle, w - mu * g)
             J_t = cost(trial.p, y, a, b)
-            # curvature of J along -g from this trial: J(mu) ~ J - mu |g|^2 + (curv/2) mu^2;
-            # used only where the step's predicted decrease is resolvable in J
-            curv_raw = 2.0 * (J_t - J + mu * gn * gn) / (mu * mu)
-            model_ok = mu * gn * gn > MODEL_MIN_DECREASE * abs(J)
-            curv = curv_raw if model_ok else 0.0
-            ok = J_t <= J - o.c1 * mu * gn * gn
             # this trial's own choices (see the docstring)
-            if ok:
-                if o.step_model == 1:
-                    ratio = min(o.step_growth, gn * gn / curv / mu) if curv > 0 else o.step_growth
-                    factor = pow2_floor(max(ratio, 0.5))
-                else:
-                    factor = o.step_growth if bt == 0 else o.step_growth_bt
-                own = (True, False, _exp2(factor) if o.step_model == 1 else 0)
-            elif o.step_model == 1 and not model_ok:
-                factor = 1.0
-                own = (False, True, 0)
-            else:
-                if o.step_model == 1:  # quadratic model's minimiser, as a power-of-two fraction of mu
-                    ratio = min(o.beta, max(1.0 / 16.0, gn * gn / curv / mu)) if curv > 0 else o.beta
-                    factor = pow2_floor(ratio)
-                else:
-                    factor = o.beta
-                own = (False, False, _exp2(factor) if o.step_model == 1 else 0)
-            trace.append(dict(J=J, J_t=J_t, mu=mu, gn2=gn * gn, curv=curv_raw, model_ok=model_ok, bt=bt,
-                              own=own, margin=J_t - (J - o.c1 * mu * gn * gn)))
+            ok, stop_t, factor = step_choice(J, J_t, mu, gn * gn, bt, o)
+            own = (ok, stop_t, _exp2(factor) if (o.step_model == 1 and not stop_t) else 0)
+            trace.append(dict(J=J, J_t=J_t, mu=mu, gn2=gn * gn, curv=2.0 * (J_t - J + mu * gn * gn) / (mu * mu),
+                              bt=bt, own=own, margin=J_t - (J - o.c1 * mu * gn * gn)))
             choice = own
             if replay is not None and len(log) < len(replay):
                 choice = tuple(replay[len(log)])

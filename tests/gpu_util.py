@@ -58,8 +58,8 @@ RAGGED_GEOM = Geometry(1000.0, 1500.0, 37, 21, 2.1, 2.7, 1.3)
 # A GPU choice that differs from the oracle's own is accepted only as a tie:
 #   - Armijo: |J_t - (J - c1 mu |g|^2)| <= TIE_J |J| in FP64, TIE_J ten times the
 #     largest cost error measured against the oracle at equal w (about 1e-6);
-#   - comparisons on |g| (the model's resolvability test mu |g|^2 > 1e-6 J and the
-#     gradient stop): within TIE_G relative, the gradient tolerance;
+#   - comparisons on |g| (the guard's resolvability test mu |g|^2 > min_decrease J
+#     and the gradient stop): within TIE_G relative, the gradient tolerance;
 #   - the step exponent: one that the FP64 trial allows once J and J_t carry
 #     TIE_J each.
 # The oracle then replays the GPU's choices in FP64, and the GPU's result is
@@ -67,7 +67,18 @@ RAGGED_GEOM = Geometry(1000.0, 1500.0, 37, 21, 2.1, 2.7, 1.3)
 # ----------------------------------------------------------------------------
 TIE_J = 1e-5
 TIE_G = 1e-4
-MODEL_MIN_DECREASE = 1e-6
+
+
+def library_opts(**kw):
+    """Oracle options with the CUDA library's default line-search rule: the
+    quadratic step model with power-of-two steps (step_model 1) and the
+    resolvability guard at 1e-6 of J. The oracle's own default is the paper's
+    plain Armijo backtracking."""
+    from oracle import oracle as O
+
+    kw.setdefault("step_model", 1)
+    kw.setdefault("min_decrease", 1e-6)
+    return O.SolveOptions(**kw)
 
 
 def _exp2(f: float) -> int:
@@ -82,8 +93,10 @@ def _pow2_floor(x: float) -> float:
     return math.ldexp(1.0, math.frexp(x)[1] - 1)
 
 
-def _model_choices(t) -> set:
-    pred, thr = t["mu"] * t["gn2"], MODEL_MIN_DECREASE * abs(t["J"])
+def _model_choices(t, opts) -> set:
+    if opts.min_decrease <= 0.0:
+        return {True}
+    pred, thr = t["mu"] * t["gn2"], opts.min_decrease * abs(t["J"])
     if abs(pred - thr) <= TIE_G * max(pred, thr):
         return {True, False}
     return {pred > thr}
@@ -94,7 +107,7 @@ def allowed_exponents(t, accepted: bool, opts) -> set:
     mu, gn2, J, Jt = t["mu"], t["gn2"], t["J"], t["J_t"]
     dJ = TIE_J * abs(J)
     out = set()
-    for model in _model_choices(t):
+    for model in _model_choices(t, opts):
         for s in (-2.0 * dJ, 0.0, 2.0 * dJ):
             c = 2.0 * (Jt - J + mu * gn2 + s) / (mu * mu)
             use = model and c > 0
@@ -108,12 +121,13 @@ def allowed_exponents(t, accepted: bool, opts) -> set:
 
 
 def checked_oracle_solve(gpu_log, run_oracle, opts):
-    """The oracle solve to compare a GPU solve with, and the number of ties the
-    GPU broke the other way. run_oracle(replay) runs the oracle's reconstruct
-    with replay=None (its own choices) or the GPU's trial log."""
+    """The oracle solve to compare a GPU solve with, the number of ties the
+    GPU broke the other way, and the oracle's own (un-replayed) solve.
+    run_oracle(replay) runs the oracle's reconstruct with replay=None (its own
+    choices) or the GPU's trial log."""
     ores = run_oracle(None)
     if [tuple(x) for x in ores.log] == list(gpu_log):
-        return ores, 0
+        return ores, 0, ores
     rep = run_oracle(list(gpu_log))
     assert [tuple(x) for x in rep.log] == list(gpu_log), "the oracle could not follow the GPU's path"
     ties = 0
@@ -123,7 +137,7 @@ def checked_oracle_solve(gpu_log, run_oracle, opts):
             assert abs(t["margin"]) <= TIE_J * abs(t["J"]), ("Armijo choice %d is not a tie" % i, t)
             ties += 1
         if not g[0] and g[1] != own[1]:
-            assert len(_model_choices(t)) == 2, ("resolvability stop %d is not a tie" % i, t)
+            assert len(_model_choices(t, opts)) == 2, ("resolvability stop %d is not a tie" % i, t)
             ties += 1
         if g[0] and g[1] != t.get("own_grad_stop", False):
             gn, thr = t["gn_after"], opts.grad_tol * t["g0"]
@@ -132,4 +146,15 @@ def checked_oracle_solve(gpu_log, run_oracle, opts):
         if opts.step_model == 1 and not g[1] and (g[0] != own[0] or g[2] != own[2]):
             assert g[2] in allowed_exponents(t, g[0], opts), ("step exponent %d is not a tie" % i, t)
             ties += int(g[0] == own[0])
-    return rep, ties
+    return rep, ties, ores
+
+
+def own_path_errors(res, own) -> dict:
+    """Distance of a GPU solve from the oracle's own solve (its own line-search
+    choices, not the GPU's): relative J, relative w and tumor distance (mm).
+    After a tie broken the other way the two paths part; J, the quantity the
+    method minimises, stays within the projection tolerance, while w may move
+    along a flat valley of J."""
+    return dict(own_J_rel=abs(res["J"] - own.J) / abs(own.J), own_w_rel=rel(res["w"], own.w),
+                own_tumor_mm=float(np.max(np.abs(np.asarray(res["tumor"]) - own.tumor))),
+                own_iters=own.iters, own_stop=own.stop_reason)

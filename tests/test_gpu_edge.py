@@ -5,7 +5,8 @@ one-slice volume, each against the oracle or the method's defined stop."""
 import numpy as np
 import pytest
 
-from gpu_util import TOL_GRAD, TOL_PROJ, TOL_W, checked_oracle_solve, noisy, rel, report
+from gpu_util import (TOL_GRAD, TOL_PROJ, TOL_W, checked_oracle_solve, library_opts, noisy, own_path_errors, rel,
+                      report)
 from oracle import oracle as O
 from phantom import Geometry, Volume
 
@@ -42,12 +43,14 @@ def test_single_mode_model(ctx, small_case):
             J, g = ctx.cost_grad(mid, yd, c["angle"], np.array([0.8]), 1.0, 0.0, mode)
             assert abs(J - Jo) / Jo < TOL_PROJ and rel(g, go) < TOL_GRAD
         res = ctx.reconstruct(mid, y, c["angle"], default_opts(max_iters=10, cold_start=1))
-        so = O.SolveOptions(max_iters=10)
-        ores, ties = checked_oracle_solve(
+        so = library_opts(max_iters=10)
+        ores, ties, own = checked_oracle_solve(
             ctx.trial_log(mid),
             lambda rp: O.reconstruct(om, c["geom"], c["angle"], y.astype(np.float64), np.zeros(1), so, replay=rp),
             so)
-        report("k1_solve", w_rel=rel(res["w"], ores.w), J_rel=abs(res["J"] - ores.J) / ores.J, ties=ties)
+        eo = own_path_errors(res, own)
+        report("k1_solve", w_rel=rel(res["w"], ores.w), J_rel=abs(res["J"] - ores.J) / ores.J, ties=ties, **eo)
+        assert eo["own_J_rel"] < TOL_PROJ
         assert res["iters"] == ores.iters and rel(res["w"], ores.w) < TOL_W
     finally:
         ctx.release_model(mid)
@@ -67,7 +70,7 @@ def test_all_zero_reference_volume(ctx, small_case):
     try:
         w0 = [0.3, -0.1, 0.05]
         res = ctx.reconstruct(mid, y, 0.4, default_opts(max_iters=5, cold_start=1, w0=w0))
-        ores = O.reconstruct(om, c["geom"], 0.4, y.astype(np.float64), np.array(w0), O.SolveOptions(max_iters=5))
+        ores = O.reconstruct(om, c["geom"], 0.4, y.astype(np.float64), np.array(w0), library_opts(max_iters=5))
         assert res["stop_reason"] == ores.stop_reason == PR_STOP_GRAD_TOL
         assert res["iters"] == ores.iters == 0
         assert np.array_equal(res["w"], np.array(w0))

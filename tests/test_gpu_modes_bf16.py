@@ -6,7 +6,8 @@ quantisation error against the float32 inputs is reported, not asserted."""
 import numpy as np
 import pytest
 
-from gpu_util import TOL_GRAD, TOL_PROJ, TOL_TUMOR_MM, TOL_W, checked_oracle_solve, noisy, rel, report
+from gpu_util import (TOL_GRAD, TOL_PROJ, TOL_TUMOR_MM, TOL_W, checked_oracle_solve, library_opts, noisy,
+                      own_path_errors, rel, report)
 from oracle import oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -69,14 +70,16 @@ def test_k5_solve(k5, name):
 
     mid, om = k5["models"][name]
     res = k5["ctx"].reconstruct(mid, k5["y"], k5["th"], default_opts(max_iters=12, cold_start=1))
-    so = O.SolveOptions(max_iters=12)
-    ores, ties = checked_oracle_solve(
+    so = library_opts(max_iters=12)
+    ores, ties, own = checked_oracle_solve(
         k5["ctx"].trial_log(mid),
         lambda rp: O.reconstruct(om, k5["geom"], k5["th"], k5["y"].astype(np.float64), np.zeros(5), so, replay=rp),
         so)
     et = float(np.max(np.abs(res["tumor"] - ores.tumor)))
+    eo = own_path_errors(res, own)
     report("k5_solve_" + name, w_rel=rel(res["w"], ores.w), J_rel=abs(res["J"] - ores.J) / ores.J, tumor_mm=et,
-           backtracks=res["backtracks"], oracle_backtracks=ores.backtracks, ties=ties)
+           backtracks=res["backtracks"], oracle_backtracks=ores.backtracks, ties=ties, **eo)
+    assert eo["own_J_rel"] < TOL_PROJ
     assert res["iters"] == ores.iters
     assert abs(res["J"] - ores.J) / ores.J < TOL_PROJ
     assert rel(res["w"], ores.w) < TOL_W
@@ -84,7 +87,7 @@ def test_k5_solve(k5, name):
     if name == "bf16":  # quantisation error of the bfloat16 model (reported)
         om32 = k5["models"]["f32"][1]
         o32 = O.reconstruct(om32, k5["geom"], k5["th"], k5["y"].astype(np.float64), np.zeros(5),
-                            O.SolveOptions(max_iters=12))
+                            library_opts(max_iters=12))
         report("k5_bf16_quantisation", w_rel=rel(res["w"], o32.w), J_rel=abs(res["J"] - o32.J) / o32.J,
                tumor_mm=float(np.max(np.abs(res["tumor"] - o32.tumor))))
 
@@ -161,12 +164,14 @@ def test_k4_cost_gradient_and_solve(k5):
             assert abs(J - Jo) / Jo < TOL_PROJ
             assert rel(g, go) < TOL_GRAD
         res = ctx.reconstruct(mid, k5["y"], th, default_opts(max_iters=8, cold_start=1))
-        so = O.SolveOptions(max_iters=8)
-        ores, ties = checked_oracle_solve(
+        so = library_opts(max_iters=8)
+        ores, ties, own = checked_oracle_solve(
             ctx.trial_log(mid),
             lambda rp: O.reconstruct(om, geom, th, k5["y"].astype(np.float64), np.zeros(4), so, replay=rp), so)
+        eo = own_path_errors(res, own)
         report("k4_solve", w_rel=rel(res["w"], ores.w), J_rel=abs(res["J"] - ores.J) / ores.J,
-               backtracks=res["backtracks"], oracle_backtracks=ores.backtracks, ties=ties)
+               backtracks=res["backtracks"], oracle_backtracks=ores.backtracks, ties=ties, **eo)
+        assert eo["own_J_rel"] < TOL_PROJ
         assert res["iters"] == ores.iters
         assert abs(res["J"] - ores.J) / ores.J < TOL_PROJ
         assert rel(res["w"], ores.w) < TOL_W

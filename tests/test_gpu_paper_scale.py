@@ -8,7 +8,8 @@ import math
 import numpy as np
 import pytest
 
-from gpu_util import TOL_GRAD, TOL_PROJ, TOL_TUMOR_MM, TOL_W, checked_oracle_solve, rel, report
+from gpu_util import (TOL_GRAD, TOL_PROJ, TOL_TUMOR_MM, TOL_W, checked_oracle_solve, library_opts, own_path_errors,
+                      rel, report)
 from oracle import oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -58,15 +59,17 @@ def test_paper_scale_solve(paper):
     p = paper
     it = 5
     res = p["ctx"].reconstruct(p["mid"], p["y"], p["th"], default_opts(max_iters=it, cold_start=1))
-    so = O.SolveOptions(max_iters=it)
-    ores, ties = checked_oracle_solve(
+    so = library_opts(max_iters=it)
+    ores, ties, own = checked_oracle_solve(
         p["ctx"].trial_log(p["mid"]),
         lambda rp: O.reconstruct(p["om"], p["geom"], p["th"], p["y"].astype(np.float64), np.zeros(3), so,
                                  replay=rp), so)
     et = float(np.max(np.abs(res["tumor"] - ores.tumor)))
+    eo = own_path_errors(res, own)
     report("paper_solve", iters=res["iters"], J_rel=abs(res["J"] - ores.J) / ores.J, w_rel=rel(res["w"], ores.w),
            tumor_mm=et, trials=res["trials"], oracle_backtracks=ores.backtracks, backtracks=res["backtracks"],
-           ties=ties)
+           ties=ties, **eo)
+    assert eo["own_J_rel"] < TOL_PROJ
     assert res["iters"] == ores.iters == it
     assert res["backtracks"] == ores.backtracks
     assert abs(res["J"] - ores.J) / ores.J < TOL_PROJ

@@ -340,13 +340,20 @@ def test_gradient_equals_forward_mode_contraction():
 # ----------------------------------------------------------------------------
 
 
-def test_cost_never_increases_across_steps(small_case):
+# The two rules the solver offers: the paper's plain Armijo backtracking (the
+# oracle's default) and the quadratic step model with power-of-two steps and the
+# resolvability guard that the CUDA library runs by default.
+RULES = {"plain": dict(), "model": dict(step_model=1, min_decrease=1e-6)}
+
+
+@pytest.mark.parametrize("rule", sorted(RULES))
+def test_cost_never_increases_across_steps(small_case, rule):
     c = small_case
     m = O.Model(c["vol"], c["f0"], c["pca"].mean, c["pca"].U, c["c0"])
     f_t = O.warp(c["vol"], c["f0"], c["x_test"])
     p_t = O.project(c["vol"], c["geom"], c["angle"], f_t)
     y = p_t + 0.01 * p_t * np.random.default_rng(0).standard_normal(p_t.shape)
-    res = O.reconstruct(m, c["geom"], c["angle"], y, np.zeros(3), O.SolveOptions(max_iters=6))
+    res = O.reconstruct(m, c["geom"], c["angle"], y, np.zeros(3), O.SolveOptions(max_iters=6, **RULES[rule]))
     a0, b0 = O.fit_ab(O.evaluate(m, c["geom"], c["angle"], np.zeros(3)).p, y)
     J_prev = O.cost(O.evaluate(m, c["geom"], c["angle"], np.zeros(3)).p, y, a0, b0)
     assert res.iters == 6
@@ -364,9 +371,154 @@ def test_single_mode_recovers_true_coefficient():
     th = 0.2
     w_true = np.array([0.9])
     y = O.evaluate(m, geom, th, w_true).p
-    res = O.reconstruct(m, geom, th, y, np.zeros(1), O.SolveOptions(max_iters=40, grad_tol=1e-9))
-    assert abs(res.w[0] - w_true[0]) < 1e-4
-    assert abs(res.a - 1.0) < 1e-5 and abs(res.b) < 1e-5
+    for rule in RULES.values():
+        res = O.reconstruct(m, geom, th, y, np.zeros(1), O.SolveOptions(max_iters=40, grad_tol=1e-9, **rule))
+        assert abs(res.w[0] - w_true[0]) < 1e-4
+        assert abs(res.a - 1.0) < 1e-5 and abs(res.b) < 1e-5
+
+
+# ---- one trial's decisions (step_choice), on hand-derived cases ----
+#
+# Along -g the cost of an exact quadratic is J(mu) = J0 - mu G + kappa mu^2 / 2
+# (G = |g|^2), whose minimiser is mu* = G / kappa. The numbers below are chosen
+# so that every quantity is exact in binary floating point and the expected
+# factor is read off by hand.
+
+PLAIN = O.SolveOptions()
+MODEL = O.SolveOptions(step_model=1)  # quadratic model, guard off
+
+
+def _quad(J0, G, kappa, mu):
+    return J0 - mu * G + 0.5 * kappa * mu * mu
+
+
+@pytest.mark.parametrize("kappa, expected", [
+    (32.0, 0.125),   # mu* = 1/8 of mu: backtrack exactly to the minimiser
+    (20.0, 0.125),   # mu* = 0.2 mu: rounded DOWN to a power of two (nearest would be 1/4)
+    (64.0, 0.0625),  # mu* = 1/16 of mu: the lower clamp's edge
+    (400.0, 0.0625),  # mu* = 0.01 mu: clamped up to 1/16
+])
+def test_step_choice_backtracks_to_the_quadratic_minimiser(kappa, expected):
+    J0, G, mu = 10.0, 4.0, 1.0
+    ok, stop, f = O.step_choice(J0, _quad(J0, G, kappa, mu), mu, G, 0, MODEL)
+    assert (ok, stop) == (False, False)
+    assert f == expected
+
+
+def test_step_choice_backtrack_is_capped_by_beta():
+    # mu* = 0.3 mu on a rejected trial; with beta = 1/8 the cap binds (1/8,
+    # where the uncapped power-of-two floor of 0.3 would be 1/4)
+    J0, G, mu = 10.0, 4.0, 1.0
+    kappa = G / 0.3
+    o = O.SolveOptions(step_model=1, beta=0.125)
+    ok, stop, f = O.step_choice(J0, _quad(J0, G, kappa, mu), mu, G, 0, o)
+    assert (ok, stop, f) == (False, False, 0.125)
+
+
+@pytest.mark.parametrize("mu, kappa, expected", [
+    (1.0, 4.0 / 1.5, 1.0),  # mu* = 1.5 mu: next first trial = mu (power-of-two floor)
+    (1.0, 0.8, 2.0),        # mu* = 5 mu: capped at step_growth = 2 (uncapped floor would be 4)
+    (2.0, 1.0, 2.0),        # mu* = 4 = exactly 2 mu: the cap's edge
+])
+def test_step_choice_next_step_after_acceptance(mu, kappa, expected):
+    J0, G = 10.0, 4.0
+    ok, stop, f = O.step_choice(J0, _quad(J0, G, kappa, mu), mu, G, 0, MODEL)
+    assert (ok, stop) == (True, False)
+    assert f == expected
+
+
+def test_step_choice_without_positive_curvature_grows_by_the_plain_factor():
+    # J(mu) at or below the tangent line: no quadratic minimiser, growth factor 2
+    ok, stop, f = O.step_choice(10.0, 5.0, 1.0, 4.0, 0, MODEL)
+    assert (ok, stop, f) == (True, False, 2.0)
+
+
+def test_step_choice_armijo_test_flips_exactly_at_the_sufficient_decrease_line():
+    # J = 10, mu = 1/2, |g|^2 = 8, c1 = 1/4: the line J - c1 mu |g|^2 is 9
+    o = O.SolveOptions(c1=0.25)
+    assert O.step_choice(10.0, 9.0, 0.5, 8.0, 0, o)[0] is True
+    assert O.step_choice(10.0, float(np.nextafter(9.0, 10.0)), 0.5, 8.0, 0, o)[0] is False
+    assert O.step_choice(10.0, float(np.nextafter(9.0, 0.0)), 0.5, 8.0, 0, o)[0] is True
+
+
+def test_step_choice_plain_rule_uses_fixed_factors():
+    o = O.SolveOptions(beta=0.3, step_growth=2.0, step_growth_bt=1.0)
+    J0, G, mu = 10.0, 4.0, 1.0
+    rej = _quad(J0, G, 32.0, mu)   # rejected (J rises)
+    acc = _quad(J0, G, 0.8, mu)    # accepted
+    assert O.step_choice(J0, rej, mu, G, 0, o) == (False, False, 0.3)   # beta, not a power of two
+    assert O.step_choice(J0, acc, mu, G, 0, o) == (True, False, 2.0)    # first-try acceptance
+    assert O.step_choice(J0, acc, mu, G, 3, o) == (True, False, 1.0)    # after backtracking
+    assert O.step_choice(J0, rej, mu, G, 0, PLAIN)[:2] == (False, False)  # no guard: never a stop
+
+
+def test_step_choice_resolvability_guard():
+    # guard at 2^-20 of J = 2^20: a trial resolves a decrease above exactly 1
+    o = O.SolveOptions(step_model=1, min_decrease=2.0 ** -20)
+    J = 2.0 ** 20
+    # predicted decrease mu G = 1, not above the threshold: a rejected trial stops
+    assert O.step_choice(J, J, 1.0, 1.0, 0, o) == (False, True, 1.0)
+    # the same trial with the guard off backtracks (to the model's minimiser,
+    # mu* = mu / 2 here: kappa = 2 G / mu)
+    assert O.step_choice(J, J, 1.0, 1.0, 0, MODEL) == (False, False, 0.5)
+    # just above the threshold the guard lets the trial backtrack
+    G = float(np.nextafter(1.0, 2.0))
+    assert O.step_choice(J, J, 1.0, G, 0, o)[:2] == (False, False)
+    # an accepted trial below the threshold ignores the model (mu* = 0.75 mu
+    # would give 1/2) and grows by the plain factor 2
+    G = 0.5
+    Jt = _quad(J, G, G / 0.75, 1.0)
+    assert O.step_choice(J, Jt, 1.0, G, 0, MODEL) == (True, False, 0.5)
+    assert O.step_choice(J, Jt, 1.0, G, 0, o) == (True, False, 2.0)
+
+
+def _quadratic_problem(K=2):
+    """A model whose projections are exactly affine in w: f0 is an affine
+    image and the modes vanish near the grid faces, so every pull-back point
+    stays inside the grid, where trilinear interpolation reproduces the affine
+    f0 exactly: f = f0 + s . x (s = f0's slope), p(w) = p(0) + A w, and J is an
+    exact quadratic in (w, a, b)."""
+    vol = Volume(16, 16, 16, 4.0, 4.0, 4.0)
+    Z, Y, X = _grid_points(vol)
+    f0 = 0.02 + 1e-4 * X + 2e-4 * Y - 1.5e-4 * Z
+    bump = np.exp(-(X ** 2 + Y ** 2 + Z ** 2) / (2 * 12.0 ** 2))
+    bump *= (np.abs(X) < 20) & (np.abs(Y) < 20) & (np.abs(Z) < 20)  # 2 voxels of zero margin
+    U = np.zeros((K, 3) + vol.shape)
+    U[0, 2] = 3.0 * bump                 # SI
+    U[1, 1] = 2.0 * bump * (X / 20.0)    # AP, sheared laterally
+    m = O.Model(vol, f0, np.zeros((3,) + vol.shape), U, np.zeros(3))
+    return m, vol
+
+
+def test_solve_reaches_the_closed_form_minimiser_of_an_exact_quadratic():
+    m, vol = _quadratic_problem()
+    geom = Geometry(1000.0, 1500.0, 24, 24, 4.0, 4.0, 2.0)
+    th = 0.7
+    p0 = O.evaluate(m, geom, th, np.zeros(2)).p.ravel()
+    A = np.stack([O.evaluate(m, geom, th, e).p.ravel() - p0 for e in np.eye(2)], axis=1)
+    w_true = np.array([0.8, -0.6])
+    # the model really is affine in w (brute force at another point)
+    assert _rel(O.evaluate(m, geom, th, w_true).p.ravel(), p0 + A @ w_true) < 1e-12
+    y = (p0 + A @ w_true) * (1.0 + 0.01 * RNG.standard_normal(p0.size))
+    # closed form: min over (w, a, b) of |p0 + A w - a y - b|^2, by least squares
+    M = np.concatenate([A, -y[:, None], -np.ones((p0.size, 1))], axis=1)
+    sol = np.linalg.lstsq(M, -p0, rcond=None)[0]
+    w_star, a_star, b_star = sol[:2], sol[2], sol[3]
+    J_star = float(np.sum((p0 + A @ w_star - a_star * y - b_star) ** 2))
+    yy = y.reshape(geom.nv, geom.nu)
+    # the paper's plain backtracking and the quadratic step model (guard off)
+    # both reach the minimiser
+    for rule in (dict(), dict(step_model=1)):
+        res = O.reconstruct(m, geom, th, yy, np.zeros(2), O.SolveOptions(max_iters=200, grad_tol=1e-10, **rule))
+        assert _rel(res.w, w_star) < 1e-6, (rule, res.w, w_star, res.iters, res.stop_reason)
+        assert abs(res.a - a_star) < 1e-6 * abs(a_star)
+        assert (res.J - J_star) <= 1e-9 * J_star
+    # with the resolvability guard at 1e-6 the solve stops once no step can
+    # lower J by more than that fraction: J is then within 1e-6 of the minimum,
+    # while w may still lie anywhere along the valley's flat direction
+    res = O.reconstruct(m, geom, th, yy, np.zeros(2), O.SolveOptions(max_iters=200, grad_tol=1e-10, **RULES["model"]))
+    assert res.stop_reason == O.STOP_RESOLVED
+    assert 0.0 <= res.J - J_star <= 1e-6 * J_star
 
 
 # ----------------------------------------------------------------------------

@@ -5,7 +5,7 @@ rounding tie is rejected."""
 import numpy as np
 import pytest
 
-from gpu_util import TIE_J, checked_oracle_solve
+from gpu_util import TIE_J, checked_oracle_solve, library_opts
 from oracle import oracle as O
 
 
@@ -16,7 +16,7 @@ def solve(small_case):
 
     m = O.Model(c["vol"], c["f0"], c["pca"].mean, c["pca"].U, c["c0"])
     y = noisy(O.project(c["vol"], c["geom"], c["angle"], O.warp(c["vol"], m.f0, c["x_test"])), c["seed"])
-    so = O.SolveOptions(max_iters=8)
+    so = library_opts(max_iters=8)
 
     def run(replay):
         return O.reconstruct(m, c["geom"], c["angle"], y, np.zeros(3), so, replay=replay)
@@ -29,8 +29,8 @@ def test_replaying_own_choices_is_bitwise(solve):
     r = run(None)
     rr = run(r.log)
     assert rr.log == r.log and np.array_equal(rr.w, r.w) and rr.J == r.J
-    res, ties = checked_oracle_solve(r.log, run, so)
-    assert ties == 0 and np.array_equal(res.w, r.w)
+    res, ties, own = checked_oracle_solve(r.log, run, so)
+    assert ties == 0 and np.array_equal(res.w, r.w) and own is res
 
 
 def test_flipping_a_clear_choice_is_rejected(solve):
