@@ -374,10 +374,12 @@ int pr_invert_dvf(pr_ctx* ctx, int model_id, const double* w, double tol, int ma
  * synchronise the device and stall a frame), an application whose device
  * memory belongs to another allocator, or code where allocating is not
  * allowed at all. It computes, from projections the caller already has,
- *   out_dev[0]   = J = sum over pixels of (p - a y - b)^2             (Eq. 2)
- *   out_dev[1+k] = dJ/dw_k = 2 sum over pixels of (p - a y - b) q_k   (the
- *                  gradient after Eq. 4 in forward form, q_k = P h_k)
- * with p_dev [R], q_dev [K][R], y_dev [R] float32 and out_dev [1 + K] double,
+ *   out_dev[0]   = the cost: the sum over pixels of (p - a y - b)^2
+ *   out_dev[1+k] = its derivative with respect to PCA coefficient k: twice
+ *                  the sum over pixels of (p - a y - b) q_k, where q_k is the
+ *                  projection of the image's derivative along mode k
+ * with p_dev [R], q_dev [K][R], y_dev [R] float32 and out_dev [1 + K] double
+ * (entries of out_dev past 1 + K are not touched),
  * all device memory of `device`, enqueued on `stream` (a cudaStream_t; NULL =
  * the legacy default stream) without a host synchronisation. It needs no
  * pr_ctx and allocates nothing: its scratch (block sums, a completion counter

@@ -435,11 +435,17 @@ struct Launcher {
     cudaError_t operator()(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
                            Args&&... args) {
         ++count;
-        if (!graph) {
-            kern<<<grid, block, smem, stream>>>(std::forward<Args>(args)...);
-            return cudaGetLastError();
-        }
+        if (!graph) return launch(kern, grid, block, smem, static_cast<KArgs>(args)...);
         return node(kern, grid, block, smem, static_cast<KArgs>(args)...);
+    }
+
+    // cudaLaunchKernel reports this launch's own error; the process-wide
+    // last-error state (which may hold an unrelated earlier error of the
+    // caller's) is neither read nor cleared.
+    template <typename... KArgs>
+    cudaError_t launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, KArgs... args) {
+        void* ptrs[sizeof...(KArgs) + 1] = {(void*)&args...};
+        return cudaLaunchKernel((const void*)kern, grid, block, ptrs, smem, stream);
     }
 
     template <typename... KArgs>

@@ -81,10 +81,11 @@ extern "C" int pr_cost_grad_static(int device, void* stream, const float* p_dev,
             rc = err(PR_ECUDA, "clearing the static counter failed");
             break;
         }
-        k_store_ab<<<1, 1, 0, s>>>(ab, a, b);
+        // Launch errors come from each launch's own return code, so an
+        // unrelated error the caller left pending is not taken for this call's.
         pr::Launcher L;
         L.stream = s;
-        if (cudaGetLastError() != cudaSuccess ||
+        if (L(k_store_ab, dim3(1), dim3(1), 0, ab, a, b) != cudaSuccess ||
             pr::launch_cost_grad(L, p_dev, q_dev, y_dev, R, K, ab, partials, counter, out) != cudaSuccess) {
             rc = err(PR_ECUDA, "kernel launch failed");
             break;

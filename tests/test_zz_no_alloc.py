@@ -57,3 +57,32 @@ def test_static_cost_grad_matches_allocating_entry_point(small_case):
         assert e.value.code == -1 and "K must be 1..7" in str(e.value)
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("R, K", [(20011, 7), (1, 7), (1, 1), (37, 3)])
+def test_static_cost_grad_limits_against_float64_sums(R, K):
+    """At the header's limits: K = 7 fills every per-block sum slot, and with
+    R = 1 nearly all of the reduction's blocks publish empty rows. Seeded
+    synthetic p, q, y (no model needed), two calls in a row, each against
+    float64 sums, and the out_dev entries past 1 + K keep a sentinel."""
+    import torch
+
+    from paper_1004_0014_b300 import capi
+
+    gen = torch.Generator(device="cpu").manual_seed(1000 * K + R)
+    p = (1.0 + torch.rand(R, generator=gen, dtype=torch.float32)).cuda()
+    q = torch.randn((K, R), generator=gen, dtype=torch.float32).cuda()
+    y = (1.0 + torch.rand(R, generator=gen, dtype=torch.float32)).cuda()
+    stream = torch.cuda.Stream()
+    for a, b in ((0.9, 0.05), (1.1, -0.02)):
+        out = torch.full((1 + K + 3,), -7.25, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        capi.pr_cost_grad_static(0, stream.cuda_stream, p, q, y, R, K, a, b, out)
+        stream.synchronize()
+        r = p.double() - a * y.double() - b
+        J_ref = float(torch.sum(r * r))
+        g_ref = (2.0 * (q.double() * r[None, :]).sum(dim=1)).cpu().numpy()
+        o = out.cpu().numpy()
+        assert abs(o[0] - J_ref) / J_ref < TOL_PROJ
+        assert rel(o[1:1 + K], g_ref) < TOL_GRAD
+        assert np.all(o[1 + K:] == -7.25)
