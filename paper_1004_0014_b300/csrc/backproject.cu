@@ -5,7 +5,7 @@
 // is nonzero) can be listed from v alone: project the corners of v's support
 // box onto the detector, visit every pixel of that footprint, intersect the
 // pixel's ray with the box, and enumerate the samples inside. Each sample
-// uses the projector's own ray_dir_index / sample_pos, so both operators see
+// uses the projector's own ray_dir_index / ray_lattice, so both operators see
 // the same points and the pair is an exact transpose up to FP32 summation
 // order.
 //
@@ -65,16 +65,21 @@ __device__ __forceinline__ void voxel_footprint(const RayGeom& g, int i, int j, 
 __device__ __forceinline__ float pixel_weight(const RayGeom& g, int i, int j, int k, int iu, int iv) {
     const float lo[3] = {(float)(i - 1), (float)(j - 1), (float)(k - 1)};
     const float hi[3] = {(float)(i + 1), (float)(j + 1), (float)(k + 1)};
-    const float fi = (float)i, fj = (float)j, fk = (float)k;
+    // voxel centres in the lattice's cell-origin coordinates (q - 1/2): the
+    // hat weights 1 - |q - i| below are then formed exactly as the
+    // projector's corner weights, from the same lattice values
+    const float fi = (float)i - 0.5f, fj = (float)j - 0.5f, fk = (float)k - 0.5f;
     float b[3], t0, t1;
     ray_dir_index(g, iu, iv, b);
     if (!ray_box(g.a, b, lo, hi, t0, t1)) return 0.0f;
     int s0 = (int)fminf(fmaxf(ceilf(t0 / g.ds - 0.5f), 0.0f), 1.0e7f);
     int s1 = (int)fminf(floorf(t1 / g.ds - 0.5f), 1.0e7f);
+    RayLattice L;
+    ray_lattice(g, b, L);
     float wsum = 0.0f;
     for (int s = s0; s <= s1; ++s) {
         float q[3];
-        sample_pos(g, b, s, q);
+        lattice_point(L, (float)s, q);
         float wx = 1.0f - fabsf(q[0] - fi), wy = 1.0f - fabsf(q[1] - fj), wz = 1.0f - fabsf(q[2] - fk);
         if (wx > 0.0f && wy > 0.0f && wz > 0.0f) wsum = __fmaf_rn(wx * wy, wz, wsum);
     }

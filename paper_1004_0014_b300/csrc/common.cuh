@@ -174,12 +174,40 @@ __device__ __forceinline__ void ray_dir_index(const RayGeom& g, int iu, int iv, 
     b[2] = __fmul_rn(__fmul_rn(d2, inv), g.inv_sp[2]);
 }
 
-// Index-space position of sample s of a ray: a + (s + 1/2) ds b.
-__device__ __forceinline__ void sample_pos(const RayGeom& g, const float b[3], int s, float q[3]) {
-    float t = __fmul_rn((float)s + 0.5f, g.ds);
-    q[0] = __fmaf_rn(t, b[0], g.a[0]);
-    q[1] = __fmaf_rn(t, b[1], g.a[1]);
-    q[2] = __fmaf_rn(t, b[2], g.a[2]);
+// Sample lattice of one ray: sample s (at distance (s + 1/2) ds from the
+// source) lies at index position q_s = o + s d + 1/2, with the step d = ds b
+// and o = a + (ds / 2) b - 1/2, each rounded once per ray. The projector works
+// in cell-origin coordinates q_s - 1/2 = o + s d (one multiply-add per axis
+// and sample; the nearest integer of q_s - 1/2 is the lower corner of the
+// trilinear cell of q_s), and the transpose evaluates the same values.
+struct RayLattice {
+    float o[3];  // q_0 - 1/2
+    float d[3];  // step between samples, index units
+};
+
+__device__ __forceinline__ void ray_lattice(const RayGeom& g, const float b[3], RayLattice& L) {
+    const float hs = 0.5f * g.ds;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        L.d[c] = __fmul_rn(g.ds, b[c]);
+        L.o[c] = __fsub_rn(__fmaf_rn(hs, b[c], g.a[c]), 0.5f);
+    }
+}
+
+// q_s - 1/2 for sample index sf (an integer held as a float, |sf| < 2^24).
+__device__ __forceinline__ void lattice_point(const RayLattice& L, float sf, float qm[3]) {
+    qm[0] = __fmaf_rn(sf, L.d[0], L.o[0]);
+    qm[1] = __fmaf_rn(sf, L.d[1], L.o[1]);
+    qm[2] = __fmaf_rn(sf, L.d[2], L.o[2]);
+}
+
+// Index-space position q_s of sample s (adding 1/2 back is exact for
+// |q| < 2^22, i.e. anywhere near a grid).
+__device__ __forceinline__ void sample_pos(const RayLattice& L, int s, float q[3]) {
+    lattice_point(L, (float)s, q);
+    q[0] = __fadd_rn(q[0], 0.5f);
+    q[1] = __fadd_rn(q[1], 0.5f);
+    q[2] = __fadd_rn(q[2], 0.5f);
 }
 
 // Ray parameter interval (mm) inside the index box [lo_c, hi_c] per axis.

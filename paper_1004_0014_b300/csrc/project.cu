@@ -151,9 +151,9 @@ __device__ __forceinline__ int cell(float q, int n, float& t) {
 // Only exact zeros are skipped; at most kTraceSteps look-ups per end.
 constexpr int kTraceSteps = 32;
 
-__device__ __forceinline__ float brick_slack(const RayGeom& g, const float b[3], int s, const SupportRef& sr) {
+__device__ __forceinline__ float brick_slack(const RayLattice& L, int s, const SupportRef& sr) {
     float q[3];
-    sample_pos(g, b, s, q);
+    sample_pos(L, s, q);
     const int bx = min(max((int)floorf(q[0] * 0.25f), 0), sr.bn[0] - 1);
     const int by = min(max((int)floorf(q[1] * 0.25f), 0), sr.bn[1] - 1);
     const int bz = min(max((int)floorf(q[2] * 0.25f), 0), sr.bn[2] - 1);
@@ -161,41 +161,79 @@ __device__ __forceinline__ float brick_slack(const RayGeom& g, const float b[3],
     return 4.0f * (float)(k - 1);
 }
 
-__device__ __forceinline__ void trace_range(const RayGeom& g, const float b[3], const SupportRef& sr, float margin,
-                                            int& s_lo, int& s_hi) {
+__device__ __forceinline__ void trace_range(const RayLattice& L, const SupportRef& sr, float margin, int& s_lo,
+                                            int& s_hi) {
     if (!sr.lev || s_lo > s_hi) return;
-    const float step = g.ds * fmaxf(fabsf(b[0]), fmaxf(fabsf(b[1]), fabsf(b[2])));
+    const float step = fmaxf(fabsf(L.d[0]), fmaxf(fabsf(L.d[1]), fabsf(L.d[2])));
     if (!(step > 1.0e-6f)) return;
     for (int it = 0; it < kTraceSteps && s_lo <= s_hi; ++it) {
-        const float slack = brick_slack(g, b, s_lo, sr) - margin;
+        const float slack = brick_slack(L, s_lo, sr) - margin;
         if (!(slack > 0.0f)) break;
         s_lo += max(1, (int)fminf(slack / step, 1.0e6f));
     }
     for (int it = 0; it < kTraceSteps && s_lo <= s_hi; ++it) {
-        const float slack = brick_slack(g, b, s_hi, sr) - margin;
+        const float slack = brick_slack(L, s_hi, sr) - margin;
         if (!(slack > 0.0f)) break;
         s_hi -= max(1, (int)fminf(slack / step, 1.0e6f));
     }
 }
 
+// Cells by rounding: for |x| < 2^22, the float sum x + 1.5 * 2^23 holds the
+// nearest integer of x in its low mantissa bits, and subtracting the constant
+// again gives that integer as a float, exactly. In cell-origin coordinates
+// x = q - 1/2 the nearest integer is the lower corner i0 of q's trilinear cell
+// and t = x - i0 is in [-1/2, 1/2], so the corner weights are 1/2 - t and
+// 1/2 + t, all without a float/int conversion. (At an exact integer q either
+// neighbouring cell may be taken; the interpolated value is the same.)
+constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
+constexpr int kRoundBits = 0x4B400000; // its bit pattern
+
 // Sample accumulation that keeps the eight corners of the last trilinear cell
 // in registers: consecutive samples 1 mm apart often fall in the same 2-2.5 mm
 // cell, and then a lane that stays in its cell does not touch L1 for that
-// sample. Used for the 4-channel (f, h_1..h_3) volume, where the corners are
-// 32 registers; index arithmetic is 32-bit (volumes below 2^29 padded voxels).
-struct CellCache4 {
-    int base = -1;
-    float c[8][4];  // corners: index = dx + 2 dy + 4 dz
+// sample. NCH = 4: one float4 (f, h_1..h_3) per corner; NCH = 6: a float4 and a
+// float2 (h_4, h_5) per corner. Index arithmetic is 32-bit (volumes below
+// 2^29 padded voxels).
+//
+// kClamp = false requires every sample to lie inside the index box
+// (-1, n) of its axis: its cell is then within the padded volume. With kClamp
+// the corner is clamped to [-1, n - 1] and the weights saturated, so a point
+// anywhere lands on the zero border and adds exactly zero.
+template <int NCH>
+struct CellCache {
+    unsigned int base = 0xffffffffu;
+    float c[8][NCH];     // corners: index = dx + 2 dy + 4 dz
+    float comp = 0.0f;   // running compensation of acc[0]
 
-    __device__ __forceinline__ void sample(const float* __restrict__ vol, const VolDev& vd, const float q[3],
-                                           float (&acc)[4]) {
-        float tx, ty, tz;
-        int ix = cell(q[0], vd.nx, tx), iy = cell(q[1], vd.ny, ty), iz = cell(q[2], vd.nz, tz);
-        int b = ((iz + 1) * vd.nyp + (iy + 1)) * vd.nxp + (ix + 1);
+    // bias: the padded index of the corner whose rounded coordinates have the
+    // bit patterns of kRound, i.e. (1 - kRoundBits) (plane + row + 1) mod 2^32
+    template <bool kClamp>
+    __device__ __forceinline__ void sample(const float* __restrict__ vol, const VolDev& vd, unsigned int bias,
+                                           const float qm[3], float (&acc)[NCH]) {
+        float w0[3], w1[3];
+        unsigned int bits[3];
+        const int n[3] = {vd.nx, vd.ny, vd.nz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float m = __fadd_rn(qm[a], kRound);
+            int bb = __float_as_int(m);
+            float r;
+            if (kClamp) {
+                bb = min(max(bb, kRoundBits - 1), kRoundBits + n[a] - 1);
+                r = __fsub_rn(__int_as_float(bb), kRound);
+            } else {
+                r = __fsub_rn(m, kRound);
+            }
+            const float t = __fsub_rn(qm[a], r);
+            w1[a] = kClamp ? __saturatef(__fadd_rn(t, 0.5f)) : __fadd_rn(t, 0.5f);
+            w0[a] = kClamp ? __saturatef(__fsub_rn(0.5f, t)) : __fsub_rn(0.5f, t);
+            bits[a] = (unsigned int)bb;
+        }
+        const unsigned int plane = (unsigned int)(vd.nxp * vd.nyp);
+        const unsigned int b = bits[2] * plane + bits[1] * (unsigned int)vd.nxp + bits[0] + bias;
         if (b != base) {
             base = b;
-            const int plane = vd.nxp * vd.nyp;
-            const int off[4] = {0, vd.nxp, plane, plane + vd.nxp};
+            const unsigned int off[4] = {0u, (unsigned int)vd.nxp, plane, plane + (unsigned int)vd.nxp};
             const float4* v4 = reinterpret_cast<const float4*>(vol);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -203,65 +241,34 @@ struct CellCache4 {
                 c[2 * k][0] = a0.x, c[2 * k][1] = a0.y, c[2 * k][2] = a0.z, c[2 * k][3] = a0.w;
                 c[2 * k + 1][0] = a1.x, c[2 * k + 1][1] = a1.y, c[2 * k + 1][2] = a1.z, c[2 * k + 1][3] = a1.w;
             }
-        }
-        float wy0 = 1.0f - ty, wz0 = 1.0f - tz;
-        const float wyz[4] = {wy0 * wz0, ty * wz0, wy0 * tz, ty * tz};
-        float s0 = 0.0f;  // this sample's f value, added to the ray sum with compensation
+            if constexpr (NCH == 6) {
+                const float2* v2 = reinterpret_cast<const float2*>(vol + 4 * vd.np);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float w0 = wyz[k] * (1.0f - tx), w1 = wyz[k] * tx;
-            s0 = __fmaf_rn(w1, c[2 * k + 1][0], __fmaf_rn(w0, c[2 * k][0], s0));
-#pragma unroll
-            for (int ch = 1; ch < 4; ++ch)
-                acc[ch] = __fmaf_rn(w1, c[2 * k + 1][ch], __fmaf_rn(w0, c[2 * k][ch], acc[ch]));
-        }
-        kahan_add(acc[0], comp, s0);
-    }
-    float comp = 0.0f;  // running compensation of acc[0]
-};
-
-// The same for the 6-channel volume (K = 4, 5): a float4 and a float2 per
-// corner, 48 registers of corners.
-struct CellCache6 {
-    int base = -1;
-    float c[8][6];  // corners: index = dx + 2 dy + 4 dz
-
-    __device__ __forceinline__ void sample(const float* __restrict__ vol, const VolDev& vd, const float q[3],
-                                           float (&acc)[6]) {
-        float tx, ty, tz;
-        int ix = cell(q[0], vd.nx, tx), iy = cell(q[1], vd.ny, ty), iz = cell(q[2], vd.nz, tz);
-        int b = ((iz + 1) * vd.nyp + (iy + 1)) * vd.nxp + (ix + 1);
-        if (b != base) {
-            base = b;
-            const int plane = vd.nxp * vd.nyp;
-            const int off[4] = {0, vd.nxp, plane, plane + vd.nxp};
-            const float4* v4 = reinterpret_cast<const float4*>(vol);
-            const float2* v2 = reinterpret_cast<const float2*>(vol + 4 * vd.np);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float4 a0 = __ldg(v4 + b + off[k]), a1 = __ldg(v4 + b + off[k] + 1);
-                float2 e0 = __ldg(v2 + b + off[k]), e1 = __ldg(v2 + b + off[k] + 1);
-                c[2 * k][0] = a0.x, c[2 * k][1] = a0.y, c[2 * k][2] = a0.z, c[2 * k][3] = a0.w;
-                c[2 * k][4] = e0.x, c[2 * k][5] = e0.y;
-                c[2 * k + 1][0] = a1.x, c[2 * k + 1][1] = a1.y, c[2 * k + 1][2] = a1.z, c[2 * k + 1][3] = a1.w;
-                c[2 * k + 1][4] = e1.x, c[2 * k + 1][5] = e1.y;
+                for (int k = 0; k < 4; ++k) {
+                    float2 e0 = __ldg(v2 + b + off[k]), e1 = __ldg(v2 + b + off[k] + 1);
+                    c[2 * k][4] = e0.x, c[2 * k][5] = e0.y;
+                    c[2 * k + 1][4] = e1.x, c[2 * k + 1][5] = e1.y;
+                }
             }
         }
-        float wy0 = 1.0f - ty, wz0 = 1.0f - tz;
-        const float wyz[4] = {wy0 * wz0, ty * wz0, wy0 * tz, ty * tz};
+        const float wyz[4] = {__fmul_rn(w0[1], w0[2]), __fmul_rn(w1[1], w0[2]), __fmul_rn(w0[1], w1[2]),
+                              __fmul_rn(w1[1], w1[2])};
         float s0 = 0.0f;  // this sample's f value, added to the ray sum with compensation
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            float w0 = wyz[k] * (1.0f - tx), w1 = wyz[k] * tx;
-            s0 = __fmaf_rn(w1, c[2 * k + 1][0], __fmaf_rn(w0, c[2 * k][0], s0));
+            const float a = __fmul_rn(wyz[k], w0[0]), e = __fmul_rn(wyz[k], w1[0]);
+            s0 = __fmaf_rn(e, c[2 * k + 1][0], __fmaf_rn(a, c[2 * k][0], s0));
 #pragma unroll
-            for (int ch = 1; ch < 6; ++ch)
-                acc[ch] = __fmaf_rn(w1, c[2 * k + 1][ch], __fmaf_rn(w0, c[2 * k][ch], acc[ch]));
+            for (int ch = 1; ch < NCH; ++ch)
+                acc[ch] = __fmaf_rn(e, c[2 * k + 1][ch], __fmaf_rn(a, c[2 * k][ch], acc[ch]));
         }
         kahan_add(acc[0], comp, s0);
     }
-    float comp = 0.0f;  // running compensation of acc[0]
 };
+
+__device__ __forceinline__ unsigned int cell_bias(const VolDev& vd) {
+    return (1u - (unsigned int)kRoundBits) * (unsigned int)(vd.nxp * vd.nyp + vd.nxp + 1);
+}
 
 template <int NCH>
 __device__ __forceinline__ void accumulate(const float* __restrict__ vol, const VolDev& vd, const float q[3],
@@ -517,6 +524,8 @@ __global__ void __launch_bounds__(kProjThreads, NCH == 4 ? 4 : 1) k_project(Proj
 
     float b[3];
     ray_dir_index(g, valid ? iu : 0, valid ? iv : 0, b);
+    RayLattice L;
+    ray_lattice(g, b, L);
     float lo[3] = {-1.0f, -1.0f, -1.0f}, hi[3] = {g.nmax[0], g.nmax[1], g.nmax[2]};
     bool nonzero = true;
     float margin = 0.0f;
@@ -528,7 +537,7 @@ __global__ void __launch_bounds__(kProjThreads, NCH == 4 ? 4 : 1) k_project(Proj
         // conversion and the loop counter far from overflow.
         s_lo = (int)fminf(fmaxf(ceilf(t0 / g.ds - 0.5f), 0.0f), (float)kMaxSamples);
         s_hi = (int)fminf(floorf(t1 / g.ds - 0.5f), (float)kMaxSamples);
-        if (A.sup.w) trace_range(g, b, A.sup, margin, s_lo, s_hi);
+        if (A.sup.w) trace_range(L, A.sup, margin, s_lo, s_hi);
         if (s_lo > s_hi) s_lo = 0x7fffffff, s_hi = -1;
     }
 #pragma unroll
@@ -540,17 +549,18 @@ __global__ void __launch_bounds__(kProjThreads, NCH == 4 ? 4 : 1) k_project(Proj
 #pragma unroll
     for (int c = 0; c < NCH; ++c) acc[c] = 0.0f;
     if constexpr (NCH == 4) {
-        CellCache4 cache;
+        CellCache<4> cache;
+        const unsigned int bias = cell_bias(A.vd);
         for (int s = s_lo; s <= s_hi; ++s) {
-            float q[3];
-            sample_pos(g, b, s, q);
-            cache.sample(A.vol, A.vd, q, acc);
+            float qm[3];
+            lattice_point(L, (float)s, qm);
+            cache.template sample<true>(A.vol, A.vd, bias, qm, acc);
         }
     } else {
         float comp = 0.0f;
         for (int s = s_lo; s <= s_hi; ++s) {
             float q[3];
-            sample_pos(g, b, s, q);
+            sample_pos(L, s, q);
             accumulate<NCH>(A.vol, A.vd, q, acc, comp);
         }
     }
@@ -621,6 +631,10 @@ __global__ void __launch_bounds__(kProjThreads, NCH == 4 ? 4 : 1) k_project(Proj
 // by tile and part index, never by timing, so results are deterministic.
 // No warp ever waits for another.
 constexpr int kParts = 4;        // sample-range parts per warp tile
+// A march runs without clamps when its end samples lie this far (index units)
+// inside the box where every cell is within the padded volume: far above the
+// rounding of a sample position, so every sample between them is inside too.
+constexpr float kInsideMargin = 1.0f / 64.0f;
 constexpr int kGroupTiles = 64;  // tiles per fixed-order moment group
 constexpr int kSplitThreads = 256;
 
@@ -791,12 +805,14 @@ __global__ void __launch_bounds__(kSplitThreads, NCH == 4 ? 4 : 2) k_project_spl
 
         float b[3];
         ray_dir_index(g, valid ? iu : 0, valid ? iv : 0, b);
+        RayLattice L;
+        ray_lattice(g, b, L);
         float t0, t1;
         int s_lo = 0x7fffffff, s_hi = -1;
         if (valid && nonzero && ray_box(g.a, b, lo, hi, t0, t1)) {
             s_lo = (int)fminf(fmaxf(ceilf(t0 / g.ds - 0.5f), 0.0f), (float)kMaxSamples);
             s_hi = (int)fminf(floorf(t1 / g.ds - 0.5f), (float)kMaxSamples);
-            if (A.sup.w) trace_range(g, b, A.sup, margin, s_lo, s_hi);
+            if (A.sup.w) trace_range(L, A.sup, margin, s_lo, s_hi);
             if (s_lo > s_hi) s_lo = 0x7fffffff, s_hi = -1;
         }
 #pragma unroll
@@ -809,28 +825,45 @@ __global__ void __launch_bounds__(kSplitThreads, NCH == 4 ? 4 : 2) k_project_spl
         for (int c = 0; c < NCH; ++c) acc[c] = 0.0f;
         float comp = 0.0f;
         if (s_hi >= s_lo) {
-            const int L = s_hi - s_lo + 1;
-            const int s_a = s_lo + (L * part) / kParts, s_e = s_lo + (L * (part + 1)) / kParts;
-            if constexpr (NCH == 4) {
-                CellCache4 cache;
-                for (int s = s_a; s < s_e; ++s) {
-                    float q[3];
-                    sample_pos(g, b, s, q);
-                    cache.sample(A.vol, A.vd, q, acc);
+            const int Ls = s_hi - s_lo + 1;
+            const int s_a = s_lo + (Ls * part) / kParts, s_e = s_lo + (Ls * (part + 1)) / kParts;
+            if constexpr (NCH == 4 || NCH == 6) {
+                // Every lane marches the warp's range [s_a, s_e); where all of
+                // those samples of all 32 rays lie inside the grid (checked at
+                // both ends: the samples of a ray lie on a segment) the cells
+                // need no clamps. Otherwise (rays grazing a face of the grid,
+                // a ragged detector edge) the clamped march runs.
+                bool inside = true;
+                if (s_e > s_a) {
+                    float q0[3], q1[3];
+                    lattice_point(L, (float)s_a, q0);
+                    lattice_point(L, (float)(s_e - 1), q1);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float top = g.nmax[c] - 0.5f - kInsideMargin, bot = -1.5f + kInsideMargin;
+                        inside = inside && q0[c] >= bot && q0[c] <= top && q1[c] >= bot && q1[c] <= top;
+                    }
                 }
-                comp = cache.comp;
-            } else if constexpr (NCH == 6) {
-                CellCache6 cache;
-                for (int s = s_a; s < s_e; ++s) {
-                    float q[3];
-                    sample_pos(g, b, s, q);
-                    cache.sample(A.vol, A.vd, q, acc);
+                const unsigned int bias = cell_bias(A.vd);
+                CellCache<NCH> cache;
+                if (__all_sync(0xffffffffu, inside)) {
+                    for (float sf = (float)s_a, se = (float)s_e; sf < se; sf += 1.0f) {
+                        float qm[3];
+                        lattice_point(L, sf, qm);
+                        cache.template sample<false>(A.vol, A.vd, bias, qm, acc);
+                    }
+                } else {
+                    for (float sf = (float)s_a, se = (float)s_e; sf < se; sf += 1.0f) {
+                        float qm[3];
+                        lattice_point(L, sf, qm);
+                        cache.template sample<true>(A.vol, A.vd, bias, qm, acc);
+                    }
                 }
                 comp = cache.comp;
             } else {
                 for (int s = s_a; s < s_e; ++s) {
                     float q[3];
-                    sample_pos(g, b, s, q);
+                    sample_pos(L, s, q);
                     accumulate<NCH>(A.vol, A.vd, q, acc, comp);
                 }
             }
@@ -1143,10 +1176,12 @@ __global__ void __launch_bounds__(256) k_count_samples(VolDev vd, const RayGeom*
     if (r < nu * nv && nonzero) {
         float b[3], t0, t1;
         ray_dir_index(g, r % nu, r / nu, b);
+        RayLattice L;
+        ray_lattice(g, b, L);
         if (ray_box(g.a, b, lo, hi, t0, t1)) {
             int s_lo = (int)fminf(fmaxf(ceilf(t0 / g.ds - 0.5f), 0.0f), (float)kMaxSamples);
             int s_hi = (int)fminf(floorf(t1 / g.ds - 0.5f), (float)kMaxSamples);
-            if (sr.w) trace_range(g, b, sr, margin, s_lo, s_hi);
+            if (sr.w) trace_range(L, sr, margin, s_lo, s_hi);
             if (s_hi >= s_lo) c = (unsigned long long)(s_hi - s_lo + 1);
         }
     }

@@ -136,9 +136,13 @@ def checked_oracle_solve(gpu_log, run_oracle, opts):
         if g[0] != own[0]:
             assert abs(t["margin"]) <= TIE_J * abs(t["J"]), ("Armijo choice %d is not a tie" % i, t)
             ties += 1
-        if not g[0] and g[1] != own[1]:
-            assert len(_model_choices(t, opts)) == 2, ("resolvability stop %d is not a tie" % i, t)
-            ties += 1
+        if not g[0]:
+            # a rejected trial stops exactly when the guard finds its predicted
+            # decrease unresolvable (whatever the oracle's own Armijo choice)
+            stops = {not m for m in _model_choices(t, opts)}
+            assert g[1] in stops, ("resolvability stop %d is not a tie" % i, t)
+            if len(stops) == 2 and not own[0] and g[1] != own[1]:
+                ties += 1
         if g[0] and g[1] != t.get("own_grad_stop", False):
             gn, thr = t["gn_after"], opts.grad_tol * t["g0"]
             assert abs(gn - thr) <= TIE_G * max(gn, thr), ("gradient stop %d is not a tie" % i, t)
