@@ -224,12 +224,24 @@ def make_targets(ctx, w, f0, frames):
 # roofline helpers
 # ----------------------------------------------------------------------------
 
-# Algorithmic FP32 work per projector sample of an nch-channel volume: the
-# trilinear weights (3 complements, 8 products of 3 factors: 19 flop), one
-# multiply-add per corner and channel (2 * 8 * nch), and the sample position
-# (3 multiply-adds: 6 flop).
+# Algorithmic FP32 work per projector sample of an nch-channel volume: one
+# multiply-add per trilinear tap and channel, 8 taps x 2 flop x nch (the
+# weights and the sample position, shared by the channels, are not counted).
 def flops_per_sample(nch: int) -> int:
-    return 2 * 8 * nch + 19 + 6
+    return 2 * 8 * nch
+
+
+def timed_frames(steps: int, warmup: int):
+    """Frames of a run: `warmup` frames just before the rotation (j = -W..-1),
+    then `steps` frames spread evenly over one gantry rotation (j = floor(i
+    360 / steps); every frame j >= 360 / steps apart warm-starts from the one
+    before it in this list). With 360 steps every projection of the rotation
+    is solved once."""
+    if steps <= 360:
+        timed = [(i * 360) // steps for i in range(steps)]
+    else:
+        timed = list(range(steps))
+    return list(range(-warmup, 0)) + timed
 
 
 def warp_voxels_evaluated(vol, box, block_voxels: int = 1024) -> int:
@@ -266,17 +278,29 @@ def recorded_traffic(kernel: str, source: str):
 # ----------------------------------------------------------------------------
 
 
-def oracle_sample(w, f0, mean, U, c0, j=0):
-    """Time one oracle trial evaluation (warp + projection) and one oracle
-    gradient evaluation on frame j of the paper-scale workload. The measured
-    projection is the oracle's own (its projection of the truth field + noise)."""
+def cpu_model() -> str:
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_sample(w, f0, mean, U, c0, j=0, openmp=True):
+    """Time one whole oracle trial evaluation (warp + projection of every
+    detector pixel) and one whole oracle gradient evaluation on frame j of the
+    workload, on all host cores (the OpenMP build) or one. The measured
+    projection is the oracle's own (its projection of the truth field + noise).
+    Returns (t_eval, t_grad, threads)."""
     from oracle import oracle as O
     from phantom import dvf_analytic, standard_normal
 
     vol, geom = w["vol"], w["geom"]
     th, t, seed = frame_params(w, j)
+    threads = O.use_openmp(openmp)
     m = O.Model(vol, f0.astype(np.float64), mean.astype(np.float64), U.astype(np.float64), c0)
-    O.build_oracle()
     x_t = dvf_analytic(vol, t, w["scale"])
     t0 = time.perf_counter()
     p = O.project(vol, geom, th, O.warp(vol, m.f0, x_t))
@@ -286,7 +310,7 @@ def oracle_sample(w, f0, mean, U, c0, j=0):
     t0 = time.perf_counter()
     O.gradient(m, geom, th, np.zeros(m.K), a, b, y)
     t_grad = time.perf_counter() - t0
-    return t_eval, t_grad
+    return t_eval, t_grad, threads
 
 
 def oracle_recon_seconds(t_eval, t_grad, iters, trials):
@@ -307,50 +331,58 @@ def run_reference(args):
     import multiprocessing
 
     from oracle import oracle as O
-    from phantom import Geometry, dvf_analytic
+    from phantom import dvf_analytic
 
     w, f0, mean, U, c0 = build_model_inputs(args.detector, args.K)
     vol, geom = w["vol"], w["geom"]
-    O.build_oracle()
     m_f0 = f0.astype(np.float64)
-    # A step's bounded sample: the oracle's whole warp of frame j, and its
-    # projection of the central REF_ROWS detector rows (a centred detector of
-    # REF_ROWS rows casts exactly those rays); the projection time scales with
-    # the rows, so one evaluation = warp + band x nv / REF_ROWS.
-    band = Geometry(geom.sad, geom.sdd, geom.nu, REF_ROWS, geom.du, geom.dv, geom.ds)
-    _, t_grad = oracle_sample(w, f0, mean, U, c0, 0)  # gradient cost, calibrated once, untimed
+    frames = timed_frames(args.steps, args.warmup)
+    # A step's bounded sample: one whole oracle evaluation of frame j (its warp
+    # and its projection of every detector pixel) on all host cores; a
+    # reconstruction costs 1 + trials evaluations and 1 + iterations gradients
+    # (the GPU arm's counts), the gradient timed once, also whole.
+    t_eval1, t_grad1, _ = oracle_sample(w, f0, mean, U, c0, frames[0], openmp=False)  # one core, for context
+    _, t_grad, threads = oracle_sample(w, f0, mean, U, c0, frames[0], openmp=True)
     times = []
-    for s in range(args.warmup + args.steps):
-        th, t, _ = frame_params(w, s)
+    for i, j in enumerate(frames):
+        th, t, _ = frame_params(w, j)
         x_t = dvf_analytic(vol, t, w["scale"])
         t0 = time.perf_counter()
-        f = O.warp(vol, m_f0, x_t)
-        t1 = time.perf_counter()
-        O.project(vol, band, th, f)
-        t2 = time.perf_counter()
-        if s >= args.warmup:
-            times.append((t1 - t0) + (t2 - t1) * geom.nv / REF_ROWS)
+        O.project(vol, geom, th, O.warp(vol, m_f0, x_t))
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
     t_eval = statistics.mean(times)
     sec = oracle_recon_seconds(t_eval, t_grad, ITERS_PER_SOLVE, TRIALS_PER_SOLVE)
     value = 1.0 / sec
+    sec1 = oracle_recon_seconds(t_eval1, t_grad1, ITERS_PER_SOLVE, TRIALS_PER_SOLVE)
+    counts = "a reconstruction = %.2f evaluations + %.2f gradients (the GPU arm's measured counts)" % (
+        1 + TRIALS_PER_SOLVE, 1 + ITERS_PER_SOLVE)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sec,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_eval,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic phantom (seeded)",
-        "config": {"workload": WORKLOAD % (args.storage, args.K, args.detector), "frames": "j = 0..; angle j deg, t = j/6 s"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "per step: the FP64 oracle's warp of frame j and its projection of the "
-                                   "central %d of %d detector rows (scaled by rows); a reconstruction = "
-                                   "%.2f evaluations + %.2f gradients (gradient calibrated once: %.2f s; "
-                                   "evaluation mean %.2f s)"
-                                   % (REF_ROWS, geom.nv, 1 + TRIALS_PER_SOLVE, 1 + ITERS_PER_SOLVE, t_grad,
-                                      t_eval)},
+        "config": {"workload": WORKLOAD % (args.storage, args.K, args.detector),
+                   "frames": "j = %s: angle j deg, t = j/6 s" % frame_list_text(frames[args.warmup:])},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "cpu": cpu_model(), "kind": "oracle",
+                         "build": "OpenMP (all host cores)", "extrapolated": True,
+                         "sample": "per step: one whole FP64 oracle evaluation of frame j (warp + projection of all "
+                                   "%d rays), mean %.3f s; one whole gradient %.3f s; %s" %
+                                   (geom.n_rays, t_eval, t_grad, counts),
+                         "single_core": {"value": 1.0 / sec1, "unit": UNIT, "cores": 1, "extrapolated": True,
+                                         "evaluation_s": t_eval1, "gradient_s": t_grad1}},
+        "ms_per_step_meaning": "time of one step's sample (one whole oracle evaluation), not of a reconstruction",
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "host_cpus": multiprocessing.cpu_count(),
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def frame_list_text(frames) -> str:
+    if len(frames) > 1 and all(b - a == frames[1] - frames[0] for a, b in zip(frames, frames[1:])):
+        return "%d, %d, ..., %d" % (frames[0], frames[1], frames[-1])
+    return ", ".join(str(j) for j in frames)
 
 
 def run_ours(args):
@@ -370,7 +402,7 @@ def run_ours(args):
     bf16 = args.storage == "bf16"
     mid = ctx.load_model(vol, geom, f0, mean, U, c0, storage=PR_BF16 if bf16 else PR_F32)
     W, K = args.warmup, args.steps
-    frames = list(range(W + K))
+    frames = timed_frames(K, W)
     ys = make_targets(ctx, w, f0, frames)
     torch.cuda.synchronize()  # ys was written on torch's stream; the solves read it on ctx.stream
     angles = [frame_params(w, j)[0] for j in frames]
@@ -437,6 +469,13 @@ def run_ours(args):
                         ("project_f", capi.PR_KERNEL_PROJECT_F)):
         kern[name] = ctx.time_kernel(mid, which, angles[W], iters=20)
     kern["invert_dvf"] = ctx.time_kernel(mid, capi.PR_KERNEL_INVERT, angles[W], iters=5)
+    # the dominant kernel over the rotation: the trial pass and its sample
+    # count at up to 8 of the timed frames' angles, evenly spaced
+    rot_idx = sorted({W + (i * K) // min(K, 8) for i in range(min(K, 8))})
+    rot = []
+    for i in rot_idx:
+        ms_i = ctx.time_kernel(mid, capi.PR_KERNEL_PROJECT_FH_TRIAL, angles[i], iters=10)
+        rot.append((math.degrees(angles[i]), ms_i, ctx.count_samples(mid, angles[i], w_start)))
     fixed = None
     if args.adjoint:
         kern["backproject_dot"] = ctx.time_kernel(mid, capi.PR_KERNEL_BACKPROJECT, angles[W], iters=3)
@@ -464,24 +503,30 @@ def run_ours(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
     sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
     fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    # samples the projector evaluates at the timed frame: support box and brick
-    # trace, counted by the library with the kernel's own clipping
-    samples = ctx.count_samples(mid, angles[W], w_start)
+    # samples the projector evaluates (support box and brick trace, counted by
+    # the library with the kernel's own clipping) over the rotation's angles
+    samples = sum(r[2] for r in rot) / len(rot)
+    t_proj_ms = sum(r[1] for r in rot) / len(rot)
     flops = samples * flops_per_sample(nch)
     per_solve_ms = elapsed_ms / K
     trials_per_solve = trials / K
-    share_proj = (1 + trials_per_solve) * kern["project_fh_trial"] / per_solve_ms
+    share_proj = (1 + trials_per_solve) * t_proj_ms / per_solve_ms
     share_warp = (1 + trials_per_solve) * kern["warp_fh"] / per_solve_ms
-    proj_tflops = flops / (kern["project_fh_trial"] / 1000.0) / 1e12
+    proj_tflops = flops / (t_proj_ms / 1000.0) / 1e12
     bytes_proj = N * 4 * nch + R * 4 * (1 + Km)
     roofline = {"kernel": "k_project_split<%d> (f, h_1..h_%d)" % (nch, Km), "bound": "alu", "achieved": proj_tflops,
                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": proj_tflops / fp32_peak,
                 "traffic": recorded_traffic("k_project_split<4>", "project.cu") if (Km == 3 and not bf16) else None,
                 "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (FMA peak)" % sm_mhz,
+                "timed_as": "line-search trial pass (moments and controller included), CUDA events on the library "
+                            "stream, averaged over %d angles of the rotation" % len(rot),
+                "per_angle": [{"deg": round(d, 1), "ms": t, "samples": int(n)} for d, t, n in rot],
                 "samples_per_launch": samples, "flops_per_sample": flops_per_sample(nch),
+                "flops_counted": "one multiply-add per trilinear tap and channel (8 x 2 x %d)" % nch,
                 "algorithmic_flops_per_launch": flops, "share_of_solve": share_proj,
                 "algorithmic_bytes_per_launch": bytes_proj,
-                "achieved_gbs": bytes_proj / (kern["project_fh_trial"] / 1000.0) / 1e9}
+                "achieved_gbs": bytes_proj / (t_proj_ms / 1000.0) / 1e9,
+                "limiter": "L1 data-pipe wavefronts (ncu: 74% of cycles at 0 deg, 95% at 60 deg)"}
     ts = 2 if bf16 else 4  # bytes per stored value of f0 and U
     # the solver's warp evaluates the blocks that meet the support box at w;
     # with w repeated (the timing loop) the others hold zeros already and are
@@ -505,16 +550,44 @@ def run_ours(args):
                        "unit": "GB/s", "frac": inv_gbs / hbm_peak, "algorithmic_bytes_per_call": bytes_inv,
                        "ms": kern["invert_dvf"], "tol_mm": 1e-5, "max_iter": 64}
 
+    # ---------------- BF16 storage of f0 and U: the same frames and loop ----------------
+    bf16_arm = None
+    if not bf16 and world == 1 and not args.no_extra_arms:
+        mid_b = ctx.load_model(vol, geom, f0, mean, U, c0, storage=PR_BF16)
+        ctx.set_state(mid_b, np.zeros(w["K"]))
+        for i in range(W):
+            ctx.reconstruct_async(mid_b, ys[i], angles[i], opts)
+        ctx.fetch_result(mid_b)
+        sb0 = ctx.stats(mid_b)
+        evb = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+        torch.cuda.synchronize()
+        evb[0].record(stream)
+        for i in range(W, W + K):
+            ctx.reconstruct_async(mid_b, ys[i], angles[i], opts)
+            evb[i - W + 1].record(stream)
+        evb[K].synchronize()
+        per_b = [evb[i].elapsed_time(evb[i + 1]) for i in range(K)]
+        sb1 = ctx.stats(mid_b)
+        last_b = ctx.fetch_result(mid_b)
+        qb = np.percentile(per_b, [50, 99])
+        bf16_arm = {"value": K / (evb[0].elapsed_time(evb[K]) / 1000.0), "unit": UNIT, "p50_ms": float(qb[0]),
+                    "p99_ms": float(qb[1]), "trials_per_solve": (sb1["trials"] - sb0["trials"]) / K,
+                    "storage": "bfloat16 f0 and U, float32 mean; FP32 arithmetic, FP64 reductions",
+                    "w_last": [float(x) for x in last_b["w"]], "J_last": last_b["J"],
+                    "vs_fp32_storage": (K / (evb[0].elapsed_time(evb[K]) / 1000.0)) / value}
+        ctx.release_model(mid_b)
+
     # ---------------- CPU baseline (rank 0, N = 1) ----------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t_eval, t_grad = oracle_sample(w, f0, mean, U, c0, W)
+        t_eval, t_grad, threads = oracle_sample(w, f0, mean, U, c0, frames[W], openmp=True)
         iters = (st1["iters"] - st0["iters"]) / K
         sec = oracle_recon_seconds(t_eval, t_grad, iters, trials_per_solve)
-        cpu = {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "one FP64 oracle trial evaluation (warp + projection, %.2f s) and one gradient "
-                         "evaluation (%.2f s) of frame %d, scaled by this run's %.2f trials and %.2f iterations "
-                         "per reconstruction" % (t_eval, t_grad, W, trials_per_solve, iters)}
+        cpu = {"value": 1.0 / sec, "unit": UNIT, "cores": threads, "cpu": cpu_model(), "kind": "oracle",
+               "build": "OpenMP (all host cores)", "extrapolated": True,
+               "sample": "one whole FP64 oracle trial evaluation (warp + projection of all %d rays, %.2f s) and one "
+                         "whole gradient evaluation (%.2f s) of frame %d, scaled by this run's %.2f trials and %.2f "
+                         "iterations per reconstruction" % (R, t_eval, t_grad, frames[W], trials_per_solve, iters)}
 
     if rank == 0:
         q = np.percentile(per_step, [50, 99])
@@ -526,8 +599,9 @@ def run_ours(args):
             "config": {"workload": WORKLOAD % (args.storage, Km, args.detector), "volume": [vol.nx, vol.ny, vol.nz],
                        "spacing_mm": [vol.dx, vol.dy, vol.dz], "K": Km, "detector": [geom.nu, geom.nv],
                        "pixel_mm": geom.du, "ray_step_mm": geom.ds, "iterations": w["max_iters"],
-                       "frames": "j = %d..%d: angle j deg, t = j/6 s, 1%% noise seed j, warm start from j-1"
-                                 % (W, W + K - 1),
+                       "frames": "j = %s (spread over one rotation): angle j deg, t = j/6 s, 1%% noise seed j, "
+                                 "each warm-started from the frame before it in this list (warm-up frames j = %d..-1)"
+                                 % (frame_list_text(frames[W:]), -W),
                        "storage": "bfloat16 f0 and U, float32 mean" if bf16 else "float32",
                        "loop": "on-device (CUDA graph, conditional WHILE)",
                        "l2": "inputs larger than L2: %d MB of DVF fields streamed per warp pass"
@@ -550,6 +624,7 @@ def run_ours(args):
             "roofline_warp": roofline_warp,
             "roofline_invert_dvf": roofline_invert,
             "fixed_angle_adjoint": fixed,
+            "bf16_storage": bf16_arm,
             "clocks": clk.summary(),
             "paper_context": {"s_per_projection": 0.24, "hardware": "Tesla C1060",
                               "workload": "NCAT 256x256x120, K=3, 200x150 projections (context only)"},
@@ -864,6 +939,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-arms", action="store_true",
+                    help="skip the BF16-storage and short served arms of the default run")
     ap.add_argument("--adjoint", action="store_true", help="also time the gather-adjoint gradient kernel")
     ap.add_argument("--detector", default="512x384", choices=["512x384", "200x150", "1000x750"],
                     help="detector sampling of the 40x30 cm panel")

@@ -32,10 +32,30 @@
  *   - P f for a ray = ds * sum over s >= 0 of F(S + (s + 1/2) ds d), d the unit
  *     direction to the pixel centre: samples anchored at the source;
  *   - tumor inversion uses the DVF interpolated trilinearly with clamp-to-edge.
+ *
+ * Built plain (liboracle.so, one thread) for every check. The same source
+ * built with OpenMP (liboracle_omp.so) serves only to time the method on all
+ * host cores: the loops whose iterations write disjoint outputs (DVF, warp,
+ * Jacobian, projection) run in parallel and give bitwise the same results;
+ * the transpose, a scatter, accumulates into one buffer per thread that are
+ * then added in thread order (the same sums in another order).
  */
 #include <math.h>
 #include <stddef.h>
+#include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads the loops below may use (1 in the plain build). */
+int or_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 typedef struct {
     int nx, ny, nz;
@@ -100,6 +120,7 @@ static double trilinear(const or_vol* v, const double* f, const double q[3], dou
 void or_dvf(const or_vol* v, const double* mean, const double* U, int K, const double* w,
             double* x) {
     size_t n3 = 3 * (size_t)v->nx * v->ny * v->nz;
+#pragma omp parallel for schedule(static)
     for (size_t e = 0; e < n3; ++e) {
         double s = mean[e];
         for (int k = 0; k < K; ++k) s += U[(size_t)k * n3 + e] * w[k];
@@ -117,6 +138,7 @@ static void pullback_index(const or_vol* v, const double* x, int i, int j, int k
 
 /* Section 2.2: the reconstructed image f(v) = F0(v + x(v)), by trilinear interpolation. */
 void or_warp(const or_vol* v, const double* f0, const double* x, double* f) {
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < v->nz; ++k)
         for (int j = 0; j < v->ny; ++j)
             for (int i = 0; i < v->nx; ++i) {
@@ -135,6 +157,7 @@ void or_warp_jac(const or_vol* v, const double* f0, const double* x, const doubl
                  double* h) {
     size_t n = (size_t)v->nx * v->ny * v->nz;
     double sp[3] = {v->dx, v->dy, v->dz};
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < v->nz; ++k)
         for (int j = 0; j < v->ny; ++j)
             for (int i = 0; i < v->nx; ++i) {
@@ -208,6 +231,7 @@ static void sample_index(const or_vol* v, const double src[3], const double dir[
 
 /* Eq. 2: p = P f, one line integral (source-anchored sample sum) per pixel, p [nv][nu]. */
 void or_project(const or_vol* v, const or_geom* g, double th, const double* f, double* p) {
+#pragma omp parallel for schedule(dynamic)
     for (int iv = 0; iv < g->nv; ++iv)
         for (int iu = 0; iu < g->nu; ++iu) {
             double src[3], dir[3], acc = 0.0;
@@ -228,32 +252,52 @@ void or_project(const or_vol* v, const or_geom* g, double th, const double* f, d
  * ds * r(ray) over the eight grid points of its cell with the same trilinear
  * weights (points outside the grid are dropped, as their values are zero in P).
  */
+/* One detector row of or_backproject, added into out. */
+static void backproject_row(const or_vol* v, const or_geom* g, double th, const double* r, int iv, double* out) {
+    for (int iu = 0; iu < g->nu; ++iu) {
+        double src[3], dir[3];
+        long s0, s1;
+        double val = g->ds * r[(size_t)iv * g->nu + iu];
+        or_ray(g, th, iu, iv, src, dir);
+        if (!sample_range(v, g, src, dir, &s0, &s1)) continue;
+        for (long s = s0; s <= s1; ++s) {
+            double q[3];
+            sample_index(v, src, dir, (s + 0.5) * g->ds, q);
+            int i0 = (int)floor(q[0]), j0 = (int)floor(q[1]), k0 = (int)floor(q[2]);
+            double tx = q[0] - i0, ty = q[1] - j0, tz = q[2] - k0;
+            double wx[2] = {1.0 - tx, tx}, wy[2] = {1.0 - ty, ty}, wz[2] = {1.0 - tz, tz};
+            for (int c2 = 0; c2 < 2; ++c2)
+                for (int c1 = 0; c1 < 2; ++c1)
+                    for (int c0 = 0; c0 < 2; ++c0) {
+                        int i = i0 + c0, j = j0 + c1, k = k0 + c2;
+                        if (i < 0 || j < 0 || k < 0 || i >= v->nx || j >= v->ny || k >= v->nz) continue;
+                        out[vox(v, i, j, k)] += wx[c0] * wy[c1] * wz[c2] * val;
+                    }
+        }
+    }
+}
+
 void or_backproject(const or_vol* v, const or_geom* g, double th, const double* r, double* out) {
     size_t n = (size_t)v->nx * v->ny * v->nz;
     memset(out, 0, n * sizeof(double));
-    for (int iv = 0; iv < g->nv; ++iv)
-        for (int iu = 0; iu < g->nu; ++iu) {
-            double src[3], dir[3];
-            long s0, s1;
-            double val = g->ds * r[(size_t)iv * g->nu + iu];
-            or_ray(g, th, iu, iv, src, dir);
-            if (!sample_range(v, g, src, dir, &s0, &s1)) continue;
-            for (long s = s0; s <= s1; ++s) {
-                double q[3];
-                sample_index(v, src, dir, (s + 0.5) * g->ds, q);
-                int i0 = (int)floor(q[0]), j0 = (int)floor(q[1]), k0 = (int)floor(q[2]);
-                double tx = q[0] - i0, ty = q[1] - j0, tz = q[2] - k0;
-                double wx[2] = {1.0 - tx, tx}, wy[2] = {1.0 - ty, ty}, wz[2] = {1.0 - tz, tz};
-                for (int c2 = 0; c2 < 2; ++c2)
-                    for (int c1 = 0; c1 < 2; ++c1)
-                        for (int c0 = 0; c0 < 2; ++c0) {
-                            int i = i0 + c0, j = j0 + c1, k = k0 + c2;
-                            if (i < 0 || j < 0 || k < 0 || i >= v->nx || j >= v->ny || k >= v->nz)
-                                continue;
-                            out[vox(v, i, j, k)] += wx[c0] * wy[c1] * wz[c2] * val;
-                        }
-            }
+#ifdef _OPENMP
+    int nt = omp_get_max_threads();
+    double* priv = nt > 1 ? (double*)calloc((size_t)nt * n, sizeof(double)) : NULL;
+    if (priv) {
+#pragma omp parallel
+        {
+            double* mine = priv + (size_t)omp_get_thread_num() * n;
+#pragma omp for schedule(dynamic)
+            for (int iv = 0; iv < g->nv; ++iv) backproject_row(v, g, th, r, iv, mine);
         }
+#pragma omp parallel for schedule(static)
+        for (size_t e = 0; e < n; ++e)
+            for (int t = 0; t < nt; ++t) out[e] += priv[(size_t)t * n + e];
+        free(priv);
+        return;
+    }
+#endif
+    for (int iv = 0; iv < g->nv; ++iv) backproject_row(v, g, th, r, iv, out);
 }
 
 /* DVF x = mean + U w interpolated trilinearly at world point p, clamped to the grid edge. */

@@ -75,13 +75,20 @@ STOP_LINESEARCH_FAILED = 3
 STOP_RESOLVED = 7
 
 
-def build_oracle(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so (plain -O2, single thread)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".tmp.%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+
+
+def build_oracle(force: bool = False, openmp: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (plain -O2, single thread), or with
+    openmp into liboracle_omp.so (the same source on all host cores; used only
+    to time the method, see oracle.c)."""
+    lib = _LIB_OMP if openmp else _LIB
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        tmp = lib + ".tmp.%d" % os.getpid()
+        flags = ["-fopenmp"] if openmp else []
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared"] + flags + ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, lib)
+    return lib
 
 
 class _Vol(ctypes.Structure):
@@ -96,13 +103,24 @@ class _Geom(ctypes.Structure):
 
 
 _lib = None
+_openmp = False
 
 
 def _L():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build_oracle())
+        _lib = ctypes.CDLL(build_oracle(openmp=_openmp))
     return _lib
+
+
+def use_openmp(flag: bool) -> int:
+    """Route the oracle's loops through the OpenMP build (all host cores) or
+    the plain one; returns the threads the loops will use."""
+    global _lib, _openmp
+    if flag != _openmp or _lib is None:
+        _openmp = flag
+        _lib = ctypes.CDLL(build_oracle(openmp=flag))
+    return int(_lib.or_threads())
 
 
 def _vol(v) -> _Vol:

@@ -355,14 +355,15 @@ def workload_paper(K: int = 3, detector: str = "512x384"):
     """Paper scale (Section 3): 256x256x120 at 2x2x2.5 mm, K modes, the 40x30 cm
     panel at 512x384 (0.776 mm; or one of DETECTORS), ray step 1 mm. Projection
     j is at gantry angle j deg and breathing time j/6 s (one-minute rotation,
-    360 projections, 6 Hz), noise seed j, 10 iterations, warm start from j - 1."""
+    360 projections, 6 Hz), noise seed j (2^31 + j for the frames before the
+    rotation, j < 0), 10 iterations, warm start from j - 1."""
     vol = Volume(256, 256, 120, 2.0, 2.0, 2.5)
     nu, nv, pitch = DETECTORS[detector]
     geom = Geometry(1000.0, 1500.0, nu, nv, pitch, pitch, 1.0)
     return dict(name="phantom 256x256x120 @ 2x2x2.5 mm, K=%d, %s detector" % (K, detector), vol=vol,
                 geom=geom, K=K, scale=1.5, max_iters=10,
                 frame_angle_deg=lambda j: float(j % 360), frame_time=lambda j: j / 6.0,
-                frame_seed=lambda j: int(j))
+                frame_seed=lambda j: int(j) if j >= 0 else int(2**31 + j))
 
 
 MIXED_SHAPES = [

@@ -44,8 +44,41 @@ def test_warp_voxels_evaluated_matches_brute_force(shape):
 def test_flops_per_sample():
     import bench
 
-    # 8 corners x nch channels x multiply-add, 19 for the trilinear weights, 6 for the position
-    assert [bench.flops_per_sample(c) for c in (4, 6, 8)] == [89, 121, 153]
+    # 8 trilinear taps x nch channels x one multiply-add (2 flop)
+    assert [bench.flops_per_sample(c) for c in (4, 6, 8)] == [64, 96, 128]
+
+
+def test_timed_frames_spread_over_the_rotation():
+    import bench
+
+    fr = bench.timed_frames(20, 5)
+    assert fr[:5] == [-5, -4, -3, -2, -1]
+    assert fr[5:] == [18 * i for i in range(20)]
+    assert bench.timed_frames(360, 3)[3:] == list(range(360))
+    assert bench.timed_frames(400, 3)[3:] == list(range(400))
+    assert bench.frame_list_text(fr[5:]) == "0, 18, ..., 342"
+
+
+def test_openmp_oracle_matches_the_plain_build():
+    """The all-cores build times the same method: the projection and warp
+    bitwise, the scatter-form transpose to rounding (another summation order)."""
+    from oracle import oracle as O
+    from phantom import Geometry, Volume, phantom_volume
+
+    vol = Volume(20, 18, 16, 4.0, 4.0, 5.0)
+    geom = Geometry(1000.0, 1500.0, 24, 20, 3.6, 3.6, 2.0)
+    f = phantom_volume(vol)
+    r = np.random.default_rng(4).random((geom.nv, geom.nu))
+    out = {}
+    try:
+        for omp in (False, True):
+            O.use_openmp(omp)
+            out[omp] = (O.project(vol, geom, 0.7, f), O.backproject(vol, geom, 0.7, r))
+    finally:
+        O.use_openmp(False)
+    assert np.array_equal(out[False][0], out[True][0])
+    bp0, bp1 = out[False][1], out[True][1]
+    assert np.max(np.abs(bp0 - bp1)) <= 1e-12 * np.max(np.abs(bp0))
 
 
 def _sampler(lines):
