@@ -577,6 +577,17 @@ def run_ours(args):
                     "vs_fp32_storage": (K / (evb[0].elapsed_time(evb[K]) / 1000.0)) / value}
         ctx.release_model(mid_b)
 
+    # ---------------- short served arm: 16 mixed patients, 8 Hz each, 5 s ----------------
+    served = None
+    if world == 1 and not args.no_extra_arms:
+        sm = serve_measure(16, 8.0, 5.0, "f32", local, ["batched:2:2", "slots:2"])
+        served = {"patients": 16, "rate_hz_each": 8.0, "seconds": 5.0, "frames": len(sm["trace"]),
+                  "results_identical_to_plain": bool(sm["same"]),
+                  "plain_fp32_one_at_a_time": sm["plain"]}
+        for md, r in zip(("batched_2lanes_2frames_per_tick", "slots_2"), sm["runs"]):
+            served[md] = {"value": r["value"], "unit": UNIT, "p50_ms": float(np.percentile(r["lat"], 50)),
+                          "p99_ms": float(np.percentile(r["lat"], 99)), "gpu_ms_mean": r["gpu_ms_mean"]}
+
     # ---------------- CPU baseline (rank 0, N = 1) ----------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -625,6 +636,7 @@ def run_ours(args):
             "roofline_invert_dvf": roofline_invert,
             "fixed_angle_adjoint": fixed,
             "bf16_storage": bf16_arm,
+            "served": served,
             "clocks": clk.summary(),
             "paper_context": {"s_per_projection": 0.24, "hardware": "Tesla C1060",
                               "workload": "NCAT 256x256x120, K=3, 200x150 projections (context only)"},
@@ -645,26 +657,42 @@ def run_ours(args):
 SERVE_BINS = 8  # breathing phases per 4 s cycle used to synthesise the frames
 
 
-def serve_patients(n_pat: int):
+def _patient_base(vol):
+    """One phantom and its K=5 PCA model at the training amplitude (a process
+    pool worker: host arithmetic only)."""
+    from phantom import build_pca, phantom_volume, training_dvfs, tumor_centre
+
+    pca = build_pca(training_dvfs(vol), 5)
+    return dict(vol=vol, f0=phantom_volume(vol).astype(np.float32), mean=pca.mean.astype(np.float32),
+                U=pca.U.astype(np.float32), c0=tumor_centre(vol))
+
+
+def serve_patients(n_pat: int, workers: int = 0):
     """Patient models of mixed sizes: shape, K and SI amplitude from
     workload_mixed(i). One phantom and K=5 PCA per distinct shape at the
     training amplitude (10 mm SI, 3 mm AP); a patient of amplitude A scales the
     whole field by A / 10 (mean x A / 10, the same unit-norm modes), and keeps
-    the first K modes."""
-    from phantom import build_pca, phantom_volume, training_dvfs, tumor_centre, workload_mixed
+    the first K modes. workers > 0 builds the shapes in that many spawned
+    processes."""
+    from phantom import workload_mixed
 
-    bases, pats = {}, []
+    pats, vols = [], {}
     for i in range(n_pat):
         wl = workload_mixed(i)
         vol = wl["vol"]
         key = (vol.nx, vol.ny, vol.nz)
-        if key not in bases:
-            pca = build_pca(training_dvfs(vol), 5)
-            bases[key] = dict(vol=vol, f0=phantom_volume(vol).astype(np.float32), mean=pca.mean.astype(np.float32),
-                              U=pca.U.astype(np.float32), c0=tumor_centre(vol))
-        alpha = wl["amp_si"] / 10.0
-        pats.append(dict(wl=wl, key=key, alpha=alpha, K=wl["K"]))
-    return bases, pats
+        vols.setdefault(key, vol)
+        pats.append(dict(wl=wl, key=key, alpha=wl["amp_si"] / 10.0, K=wl["K"]))
+    keys = list(vols)
+    if workers > 0 and len(keys) > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+
+        with cf.ProcessPoolExecutor(min(workers, len(keys)), mp_context=mp.get_context("spawn")) as ex:
+            built = list(ex.map(_patient_base, [vols[k] for k in keys]))
+    else:
+        built = [_patient_base(vols[k]) for k in keys]
+    return dict(zip(keys, built)), pats
 
 
 def serve_trace(n_pat: int, rate_hz: float, seconds: float, seed: int = 77):
@@ -716,9 +744,11 @@ def serve_targets(ctx, bases, pats, trace, geom):
     return ys
 
 
-def serve_once(ctx, mids, pats, ys, trace, opts, n_slots, local):
-    """One served pass of the trace with n_slots concurrent solve streams, every
-    patient starting from w = 0; latencies from the scheduled arrivals."""
+def serve_once(ctx, mids, pats, ys, trace, opts, n_slots, local, lanes=0, tick_frames=0):
+    """One served pass of the trace with n_slots concurrent solve streams (or,
+    lanes > 0, tick-batched with that many ticks in flight and at most
+    tick_frames frames per tick), every patient starting from w = 0; latencies
+    from the scheduled arrivals."""
     import threading
 
     for pt, mid in zip(pats, mids):
@@ -739,7 +769,7 @@ def serve_once(ctx, mids, pats, ys, trace, opts, n_slots, local):
             t_submit[n] = time.perf_counter()
             submitted[0] = n + 1
 
-    ctx.serve_start(slots=n_slots)
+    ctx.serve_start(slots=n_slots, batched_lanes=lanes, tick_frames=tick_frames)
     with ClockSampler(local) as clk:
         th_feed = threading.Thread(target=feeder)
         th_feed.start()
@@ -760,51 +790,47 @@ def serve_once(ctx, mids, pats, ys, trace, opts, n_slots, local):
     for n, (t, i, f, th) in enumerate(trace):
         final[i] = done[n][1]["w"]
     return dict(lat=lat, late=late, value=len(trace) / (t_end - t_start[0]), final=final, clocks=clk.summary(),
-                slots=n_slots, gpu_ms_mean=float(np.mean([done[n][1]["gpu_ms"] for n in range(len(trace))])))
+                slots=n_slots, lanes=lanes,
+                gpu_ms_mean=float(np.mean([done[n][1]["gpu_ms"] for n in range(len(trace))])))
 
 
-def run_serve(args):
+def serve_measure(patients: int, rate: float, seconds: float, storage: str, local: int, modes, workers: int = 8):
+    """Serve a Poisson trace of `patients` mixed patients at `rate` Hz each for
+    `seconds` once per mode in `modes` ("batched:L:F" = tick-batched with L
+    lanes and at most F frames per tick (0 or absent = all), "slots:S" = S solve
+    streams), then the plain FP32 path (host-driven loop,
+    one frame at a time in arrival order) on the same trace. Returns the runs
+    and the plain path's figures."""
     from paper_1004_0014_b300 import PR_BF16, PR_F32, PR_LOOP_HOST, Context, default_opts
 
-    world, rank, local = dist_env()
-    if world > 1:
-        raise SystemExit("--serve runs on one GPU")
-    bases, pats = serve_patients(args.patients)
+    bases, pats = serve_patients(patients, workers)
     geom = pats[0]["wl"]["geom"]
-    trace = serve_trace(args.patients, args.rate, args.seconds)
+    trace = serve_trace(patients, rate, seconds)
     ctx = Context(local)
     ys = serve_targets(ctx, bases, pats, trace, geom)
     mids = []
     for pt in pats:
         b = bases[pt["key"]]
         mids.append(ctx.load_model(b["vol"], geom, b["f0"], pt["alpha"] * b["mean"], b["U"][:pt["K"]], b["c0"],
-                                   storage=PR_BF16 if args.storage == "bf16" else PR_F32))
+                                   storage=PR_BF16 if storage == "bf16" else PR_F32))
     opts = default_opts(max_iters=10)
-
-    slot_list = [int(x) for x in str(args.slots).split(",")]
-    # warm-up: a few frames per patient, then every patient restarts from w = 0
-    ctx.serve_start(slots=slot_list[0])
+    # warm-up: two frames per patient, then every patient restarts from w = 0
+    ctx.serve_start(slots=4)
     for i, mid in enumerate(mids):
         for f in range(2):
             ctx.submit(mid, ys[next(k for k in ys if k[0] == i)], 0.0, opts, tag=f)
     for _ in range(2 * len(mids)):
         ctx.poll(timeout_ms=120000)
     ctx.serve_stop()
-    for pt, mid in zip(pats, mids):
-        ctx.set_state(mid, np.zeros(pt["K"]))
-
-    runs = [serve_once(ctx, mids, pats, ys, trace, opts, n_slots, local) for n_slots in slot_list]
-    head = runs[0]
-    lat, late, served_value, final_served, clk_summary = (head["lat"], head["late"], head["value"], head["final"],
-                                                          head["clocks"])
-
-    # plain FP32 path: host-driven loop, one frame at a time, same trace; the
-    # queue (start = max(arrival, previous finish)) uses the measured service times
+    runs = []
+    for mode in modes:
+        kind, n, *rest = mode.split(":")
+        runs.append(serve_once(ctx, mids, pats, ys, trace, opts, int(n) if kind == "slots" else 4, local,
+                               lanes=int(n) if kind == "batched" else 0, tick_frames=int(rest[0]) if rest else 0))
     plain_opts = default_opts(max_iters=10, loop_mode=PR_LOOP_HOST)
     for pt, mid in zip(pats, mids):
         ctx.set_state(mid, np.zeros(pt["K"]))
-    svc = []
-    final_plain = {}
+    svc, final_plain = [], {}
     for (t, i, f, th) in trace:
         t0 = time.perf_counter()
         res = ctx.reconstruct(mids[i], ys[(i, f)], th, plain_opts)
@@ -814,19 +840,37 @@ def run_serve(args):
     for (t, i, f, th), s_i in zip(trace, svc):
         finish = max(t, finish) + s_i
         plain_lat.append(1000.0 * (finish - t))
-    plain_value = len(trace) / (finish - trace[0][0])
+    plain = dict(value=len(trace) / (finish - trace[0][0]), p50_ms=float(np.percentile(plain_lat, 50)),
+                 p99_ms=float(np.percentile(plain_lat, 99)), mean_service_ms=1000.0 * float(np.mean(svc)))
     same = all(np.array_equal(np.asarray(r["final"][i]), np.asarray(final_plain[i])) for r in runs for i in r["final"])
+    ctx.close()
+    return dict(runs=runs, plain=plain, same=same, trace=trace, pats=pats)
+
+
+def run_serve(args):
+    world, rank, local = dist_env()
+    if world > 1:
+        raise SystemExit("--serve runs on one GPU")
+    if args.serve_mode == "batched":
+        modes = ["batched:%s:%s" % (x, f) for x in str(args.lanes).split(",")
+                 for f in str(args.tick_frames).split(",")]
+    else:
+        modes = ["slots:%s" % x for x in str(args.slots).split(",")]
+    m = serve_measure(args.patients, args.rate, args.seconds, args.storage, local, modes)
+    runs, plain, trace, pats = m["runs"], m["plain"], m["trace"], m["pats"]
+    head = runs[0]
+    lat, late = head["lat"], head["late"]
     line = {
         "metric": "served reconstructions/s and p50/p99 ms per projection (%d patients, mixed sizes, %g Hz Poisson "
                   "each) vs plain FP32 path" % (args.patients, args.rate),
-        "value": served_value, "unit": UNIT, "n_gpus": 1, "p50_ms": float(np.percentile(lat, 50)),
+        "value": head["value"], "unit": UNIT, "n_gpus": 1, "p50_ms": float(np.percentile(lat, 50)),
         "p99_ms": float(np.percentile(lat, 99)), "higher_is_better": True, "dtype": "f32",
         "data": "synthetic phantoms (seeded)",
         "frames": len(trace), "offered_hz": args.rate * args.patients, "seconds": args.seconds,
-        "slots": slot_list[0],
-        "slots_sweep": [{"slots": r["slots"], "value": r["value"], "p50_ms": float(np.percentile(r["lat"], 50)),
-                         "p99_ms": float(np.percentile(r["lat"], 99)), "gpu_ms_mean": r["gpu_ms_mean"]}
-                        for r in runs],
+        "mode": modes[0],
+        "sweep": [{"mode": md, "value": r["value"], "p50_ms": float(np.percentile(r["lat"], 50)),
+                   "p99_ms": float(np.percentile(r["lat"], 99)), "gpu_ms_mean": r["gpu_ms_mean"]}
+                  for md, r in zip(modes, runs)],
         "config": {"workload": "serving: %d patients, shapes %s, K 3-5, SI amplitude 8-20 mm (whole field scaled), "
                                "512x384 detector, 10 iterations, warm start per patient, %s storage" %
                                (args.patients, sorted(set(str(p["key"]) for p in pats)), args.storage),
@@ -837,18 +881,15 @@ def run_serve(args):
                                "max": float(late.max())},
         "capacity_note": "throughput is capped by the GPU's solve rate when the offered load exceeds it; "
                          "latency then grows with the length of the trace",
-        "plain_fp32": {"value": plain_value, "p50_ms": float(np.percentile(plain_lat, 50)),
-                       "p99_ms": float(np.percentile(plain_lat, 99)),
-                       "mean_service_ms": 1000.0 * float(np.mean(svc)),
-                       "path": "host-driven loop (PR_LOOP_HOST), one frame at a time in arrival order; latency from "
-                               "the measured service times with start = max(arrival, previous finish)",
-                       "storage": "%s, as the served arm (FP32 arithmetic throughout)" % args.storage},
-        "results_identical_to_plain": bool(same),
+        "plain_fp32": dict(plain, path="host-driven loop (PR_LOOP_HOST), one frame at a time in arrival order; "
+                                       "latency from the measured service times with start = max(arrival, previous "
+                                       "finish)", storage="%s, as the served arm (FP32 arithmetic throughout)"
+                                                          % args.storage),
+        "results_identical_to_plain": bool(m["same"]),
         "gpu_ms_mean": head["gpu_ms_mean"],
-        "clocks": clk_summary,
+        "clocks": head["clocks"],
     }
     print(json.dumps(line), flush=True)
-    ctx.close()
     return 0
 
 
@@ -864,7 +905,7 @@ def run_batch(args):
     if world > 1:
         raise SystemExit("--batch runs on one GPU")
     n_pat, per = 8, 8
-    bases, pats = serve_patients(n_pat)
+    bases, pats = serve_patients(n_pat, 8)
     geom = pats[0]["wl"]["geom"]
     trace = []  # (t, patient, frame, angle): 8 random angles and breathing times per patient, seed = patient id
     for i in range(n_pat):
@@ -952,6 +993,11 @@ def main():
     ap.add_argument("--rate", type=float, default=15.0, help="frames per second per patient (--serve)")
     ap.add_argument("--seconds", type=float, default=20.0, help="length of the arrival trace (--serve)")
     ap.add_argument("--slots", default="4", help="concurrent solve streams (--serve); a comma list runs each")
+    ap.add_argument("--serve-mode", default="batched", choices=["batched", "slots"],
+                    help="--serve: tick-batched launches or stream slots")
+    ap.add_argument("--lanes", default="2", help="ticks in flight (--serve-mode batched); a comma list runs each")
+    ap.add_argument("--tick-frames", default="0",
+                    help="most frames per tick (--serve-mode batched, 0 = all pending); a comma list runs each")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -62,6 +62,8 @@ extern "C" {
 #define PR_ETIMEOUT (-5)    /* a bounded wait ran out */
 #define PR_ENOMODEL (-6)    /* unknown or released model id */
 #define PR_EUNSUPPORTED (-7)
+#define PR_QUEUED 1         /* pr_load_model with the admission queue on: the model does not fit
+                               the HBM budget now and waits for admission (not an error) */
 
 /* ---- why a solve stopped (pr_result.stop_reason) ---- */
 #define PR_STOP_GRAD_TOL 1          /* |grad J| <= grad_tol * |grad J at start| */
@@ -176,8 +178,29 @@ int pr_load_model(pr_ctx* ctx, const pr_volume_desc* vol, const pr_geometry* geo
                   const float* f0, const float* mean_dvf, const float* U, int K, int storage,
                   const double tumor_ref_xyz[3], int* model_id);
 
-/* Release a model and its device buffers. */
+/* Release a model and its device buffers (or drop it from the admission
+ * queue). Released memory admits waiting models in FIFO order (see
+ * pr_set_admission_queue); their upload runs inside this call. */
 int pr_release_model(pr_ctx* ctx, int model_id);
+
+/* HBM admission queue (no counterpart in the paper; the serving use of
+ * Section 4's real-time setting). Off by default: pr_load_model then fails
+ * with PR_EADMIT when a model does not fit the context's budget. With
+ * enable != 0, such a model (and every model loaded after it while any
+ * waits) is instead queued: pr_load_model copies its inputs to host memory
+ * owned by the library, assigns *model_id and returns PR_QUEUED. The model is
+ * admitted (uploaded, made resident) as soon as releases free enough budget
+ * for it, in loading order. Frames may be submitted for a waiting model: they
+ * stay queued until it is admitted. Synchronous calls on a waiting model fail
+ * with PR_ENOMODEL. A model larger than the whole budget still fails with
+ * PR_EADMIT. */
+int pr_set_admission_queue(pr_ctx* ctx, int enable);
+
+enum { PR_MODEL_RESIDENT = 0, PR_MODEL_WAITING = 1 };
+
+/* *status = PR_MODEL_RESIDENT or PR_MODEL_WAITING (admission queue).
+ * Errors: PR_EINVAL, PR_ENOMODEL. */
+int pr_model_status(pr_ctx* ctx, int model_id, int* status);
 
 /* Device bytes held by a model (data, workspace, graph buffers). */
 int pr_model_footprint(pr_ctx* ctx, int model_id, size_t* bytes);
@@ -224,7 +247,9 @@ int pr_fetch_result(pr_ctx* ctx, int model_id, pr_result* out);
  * still in flight; different models' solves then overlap on the GPU, and each
  * model's frames run in submission order, each warm-started from the previous
  * (Section 4). Models are admitted to the device by pr_load_model's HBM
- * budget check (PR_EADMIT) and can be loaded and released while serving. The
+ * budget check (PR_EADMIT, or the admission queue of pr_set_admission_queue)
+ * and can be loaded and released while serving. When serving stops, frames
+ * of models still waiting for admission stay queued (a restart drops them). The
  * serving worker is a host thread of the context; while it runs, the
  * synchronous calls (pr_reconstruct, pr_warp, ...) must not be used on a
  * model that has submitted frames outstanding. */
@@ -234,13 +259,36 @@ typedef struct {
     int status;         /* PR_OK or the error of this solve */
     pr_result result;
     double queue_ms;    /* submit to dispatch into a slot (host clock) */
-    double gpu_ms;      /* the solve's device time on its slot stream (CUDA events) */
+    double gpu_ms;      /* slot mode: the solve's device time on its slot stream (CUDA events);
+                           tick-batched mode: launch of its tick to its result (host clock) */
     double latency_ms;  /* submit to completion (host clock) */
 } pr_served;
 
 /* Start the serving worker with `slots` (1..64) concurrent solve streams
  * (after pr_serve_stop this restarts it; results not yet polled are dropped). */
 int pr_serve_start(pr_ctx* ctx, int slots);
+
+/* Start the serving worker in tick-batched mode: each tick gathers, in
+ * submission order, the oldest pending frame of each resident model that has
+ * no frame in flight (at most tick_frames of them; 0 = no limit) and runs
+ * them all with ONE graph launch. The graph holds every resident
+ * model's whole solve (Sections 2.2 and 2.3) as a branch behind a
+ * conditional IF node; a first kernel switches on the branches of the models
+ * the tick took, and the solves of those branches run concurrently on the
+ * GPU. The graph is built once per set of resident models (again after a
+ * load, release or admission) and only the staged frames and flags change
+ * between ticks. `lanes` (1..8) ticks may be in flight at once, each on its
+ * own stream and never sharing a model, so frames arriving during a tick are
+ * taken by the next free lane. Each branch's last kernel writes its final
+ * state into mapped host memory and raises a per-branch flag, so a frame's
+ * result is taken as soon as its own solve finishes, and its model's next
+ * frame can join another lane's tick while the rest of this tick runs.
+ * Results are polled as in slot mode; each model's frames run in submission
+ * order, each warm-started from the previous, and give the same results as
+ * solved alone.
+ * Errors: PR_EINVAL (lanes or tick_frames out of range, serving already
+ * started), PR_ECUDA. */
+int pr_serve_start_batched(pr_ctx* ctx, int lanes, int tick_frames);
 
 /* Queue one frame: y [nv][nu] float32 (host, copied before return), gantry
  * angle, options (NULL = defaults; the host loop mode is not allowed), and a

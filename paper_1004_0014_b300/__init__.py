@@ -192,8 +192,21 @@ class Context:
         return y, steps, open_
 
     # --- serving -------------------------------------------------------------
-    def serve_start(self, slots: int = 4):
-        capi.pr_serve_start(self._ctx, slots)
+    def serve_start(self, slots: int = 4, batched_lanes: int = 0, tick_frames: int = 0):
+        """Slot mode (`slots` concurrent solve streams) or, with batched_lanes
+        > 0, tick-batched mode (one graph launch per tick over the models'
+        pending frames, at most tick_frames of them (0 = all), that many ticks
+        in flight)."""
+        if batched_lanes:
+            capi.pr_serve_start_batched(self._ctx, batched_lanes, tick_frames)
+        else:
+            capi.pr_serve_start(self._ctx, slots)
+
+    def set_admission_queue(self, enable: bool = True):
+        capi.pr_set_admission_queue(self._ctx, enable)
+
+    def model_status(self, mid: int) -> int:
+        return capi.pr_model_status(self._ctx, mid)
 
     def submit(self, mid: int, y, angle_rad: float, opts: SolveOpts | None = None, tag: int = 0):
         capi.pr_submit(self._ctx, mid, y, angle_rad, opts, tag)

@@ -44,7 +44,11 @@ EXPORTED = [
     "pr_forward", "pr_vjp", "pr_cost_grad", "pr_tumor", "pr_invert_dvf", "pr_trial_log", "pr_fix_angle",
     "pr_count_samples", "pr_warp_box", "pr_time_kernel", "pr_model_stats",
     "pr_io_bytes", "pr_cost_grad_static", "pr_serve_start", "pr_submit", "pr_poll", "pr_serve_stop",
+    "pr_serve_start_batched", "pr_set_admission_queue", "pr_model_status",
 ]
+
+PR_QUEUED = 1
+PR_MODEL_RESIDENT, PR_MODEL_WAITING = 0, 1
 
 PR_KERNEL_WARP_FH, PR_KERNEL_PROJECT_FH, PR_KERNEL_REGRAD = 0, 1, 2
 PR_KERNEL_BACKPROJECT, PR_KERNEL_WARP_F, PR_KERNEL_PROJECT_F, PR_KERNEL_INVERT = 3, 4, 5, 6
@@ -163,6 +167,9 @@ def load_library(path: str | None = None):
         "pr_io_bytes": (_I, [_P, _I, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
         "pr_cost_grad_static": (_I, [_I, _P, _P, _P, _P, _I, _I, _D, _D, _P]),
         "pr_serve_start": (_I, [_P, _I]),
+        "pr_serve_start_batched": (_I, [_P, _I, _I]),
+        "pr_set_admission_queue": (_I, [_P, _I]),
+        "pr_model_status": (_I, [_P, _I, ctypes.POINTER(_I)]),
         "pr_submit": (_I, [_P, _I, _P, _D, ctypes.POINTER(SolveOpts), ctypes.c_uint64]),
         "pr_poll": (_I, [_P, _I, ctypes.POINTER(Served)]),
         "pr_serve_stop": (_I, [_P]),
@@ -260,9 +267,21 @@ def pr_load_model(ctx, vol: VolumeDesc, geom: Geometry, f0, mean_dvf, U, K: int,
         raise ValueError("f0, mean_dvf and U must all be on the host or all on the device")
     c0, pc = _dvec(tumor_ref_xyz)
     mid = ctypes.c_int()
-    _check(_lib.pr_load_model(ctx, ctypes.byref(vol), ctypes.byref(geom), lf, pf, pm, pu, int(K),
-                              int(storage), pc, ctypes.byref(mid)))
+    rc = _lib.pr_load_model(ctx, ctypes.byref(vol), ctypes.byref(geom), lf, pf, pm, pu, int(K), int(storage), pc,
+                            ctypes.byref(mid))
+    if rc != PR_QUEUED:  # queued for admission: a handle, not an error
+        _check(rc)
     return mid.value
+
+
+def pr_set_admission_queue(ctx, enable: bool):
+    _check(_lib.pr_set_admission_queue(ctx, 1 if enable else 0))
+
+
+def pr_model_status(ctx, model_id: int) -> int:
+    st = _I()
+    _check(_lib.pr_model_status(ctx, int(model_id), ctypes.byref(st)))
+    return st.value
 
 
 def pr_release_model(ctx, model_id: int):
@@ -447,6 +466,10 @@ def pr_cost_grad_static(device: int, stream, p_dev, q_dev, y_dev, R: int, K: int
 
 def pr_serve_start(ctx, slots: int = 4):
     _check(_lib.pr_serve_start(ctx, int(slots)))
+
+
+def pr_serve_start_batched(ctx, lanes: int = 2, tick_frames: int = 0):
+    _check(_lib.pr_serve_start_batched(ctx, int(lanes), int(tick_frames)))
 
 
 def pr_submit(ctx, model_id: int, y, angle_rad: float, opts: SolveOpts | None = None, tag: int = 0):

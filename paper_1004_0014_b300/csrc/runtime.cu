@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -129,17 +130,69 @@ struct ServeSlot {
 
 struct Batch;  // pr_reconstruct_batch's graph and staging (defined with it)
 
+// Tick-batched serving: a lane is one CUDA graph over every resident model,
+// each model's whole solve behind a conditional IF node whose flag a first
+// kernel sets from the tick's staged `active` array. A tick stages the
+// frames it takes (at most one per model), launches the graph once and copies
+// the models' final states back; lanes run on their own streams and never
+// share a model (a model with a frame in flight is not taken).
+struct TickLane {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t start = nullptr, done = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long epoch = -1;          // model-set epoch the graph was built for
+    std::map<int, int> pos;        // model id -> branch index
+    std::vector<size_t> y_off;     // branch -> offset of its frame in the staging (floats)
+    int cap = 0;                   // branches the staging holds
+    size_t y_cap = 0;              // floats of frame staging
+    int* active = nullptr;         // device: branch flags
+    cudaGraphConditionalHandle* handles = nullptr;  // device: the IF nodes' handles
+    SolveParams* prm = nullptr;    // device: per-branch parameters
+    float* y = nullptr;            // device: frames
+    SolveState* res = nullptr;     // device: final states
+    int* active_h = nullptr;       // pinned mirrors
+    SolveParams* prm_h = nullptr;
+    float* y_h = nullptr;
+    // Results, written by each branch's last kernel straight into mapped
+    // pinned host memory, then the branch's flag is set to the tick's
+    // sequence number: the worker retires each frame as its branch finishes.
+    SolveState* res_h = nullptr;   // mapped pinned (res: its device address)
+    int* flag_h = nullptr;         // mapped pinned (flag: its device address)
+    int* flag = nullptr;
+    int seq = 0;                   // sequence number of the last tick (flags start at 0)
+    bool busy = false;
+    std::vector<ServeRequest> reqs;  // the frames of the tick in flight
+    std::vector<char> retired;       // per frame: result already taken
+    std::chrono::steady_clock::time_point t_dispatch;
+};
+
 struct Serve {
     std::thread worker;
     std::condition_variable cv_work, cv_done;
     std::deque<ServeRequest> pending;
     std::deque<pr_served> done;
-    std::vector<ServeSlot> slots;
+    std::vector<ServeSlot> slots;  // slot mode
+    std::vector<TickLane> lanes;   // tick-batched mode
+    int tick_frames = 0;           // most frames per tick (0 = every dispatchable frame)
     std::set<int> in_flight;  // models with a dispatched solve
     long long outstanding = 0;  // submitted and not yet polled into `done`
     bool stop = false;
     int error = 0;
     std::string error_msg;
+};
+
+// A model that did not fit the HBM budget when loaded with the admission
+// queue on: its inputs (host copies) wait in FIFO order until released
+// memory lets it in.
+struct Waiting {
+    int id = 0;
+    pr_volume_desc vol{};
+    pr_geometry geom{};
+    int K = 0, storage = 0;
+    double c0[3] = {0, 0, 0};
+    std::vector<float> f0, mean, U;
+    size_t need = 0;
 };
 
 }  // namespace
@@ -153,6 +206,9 @@ struct pr_ctx {
     size_t budget = 0, used = 0;
     int next_id = 1;
     std::map<int, Model*> models;
+    long long model_epoch = 0;      // changes whenever a model is admitted or released
+    bool admit_queue = false;       // over-budget models wait instead of failing
+    std::deque<Waiting*> waiting;   // admission queue, FIFO
     float* pad = nullptr;  // scratch for pr_project
     size_t pad_cap = 0;
     RayGeom* rg = nullptr;
@@ -656,6 +712,348 @@ int build_batch_graph(Batch* b, const std::vector<Model*>& ms) {
     return PR_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Tick-batched serving lanes
+// ---------------------------------------------------------------------------
+
+// Sets each branch's IF flag from the tick's staged flags.
+__global__ void k_tick_set(const int* __restrict__ active, const cudaGraphConditionalHandle* __restrict__ h, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cudaGraphSetConditional(h[i], active[i] ? 1u : 0u);
+}
+
+// Word copy (the branch's staging -> model transfers inside the graph).
+__global__ void k_copy_words(const unsigned int* __restrict__ src, unsigned int* __restrict__ dst, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+// A branch's last kernel (one block): its final state into host memory, then,
+// once every thread's stores are visible to the host, the branch's flag set to
+// the tick's sequence number (its entry of the staged flags).
+__global__ void k_publish(const unsigned int* __restrict__ st, unsigned int* res, size_t n, volatile int* flag,
+                          const int* __restrict__ seq) {
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) res[i] = st[i];
+    __threadfence_system();
+    __syncthreads();
+    if (threadIdx.x == 0) *flag = *seq;
+}
+
+constexpr int kMaxLaneModels = 1024;
+
+void lane_free_graph(TickLane& ln) {
+    if (ln.exec) cudaGraphExecDestroy(ln.exec);
+    if (ln.graph) cudaGraphDestroy(ln.graph);
+    ln.exec = nullptr;
+    ln.graph = nullptr;
+    ln.epoch = -1;
+}
+
+void lane_free(TickLane& ln) {
+    lane_free_graph(ln);
+    void* dev[] = {ln.active, ln.handles, ln.prm, ln.y};
+    for (void* d : dev)
+        if (d) cudaFree(d);
+    void* host[] = {ln.active_h, ln.prm_h, ln.y_h, ln.res_h, ln.flag_h};
+    for (void* h : host)
+        if (h) cudaFreeHost(h);
+    ln.active = nullptr, ln.handles = nullptr, ln.prm = nullptr, ln.y = nullptr, ln.res = nullptr;
+    ln.active_h = nullptr, ln.prm_h = nullptr, ln.y_h = nullptr, ln.res_h = nullptr, ln.flag_h = nullptr;
+    ln.flag = nullptr;
+    ln.cap = 0, ln.y_cap = 0;
+}
+
+// One branch: frame and parameters from the staging into the model, the
+// whole solve (Section 2.2 with its own WHILE node, then Section 2.3), the
+// final state into the staging.
+int add_tick_branch(cudaGraph_t body, Model* m, const float* y_src, const SolveParams* prm_src, SolveState* res_dst,
+                    int* flag, const int* seq) {
+    SolveState* st = m->st;
+    Launcher L;
+    L.graph = body;
+    CK(L(k_copy_words, dim3(48), dim3(256), 0, reinterpret_cast<const unsigned int*>(y_src),
+         reinterpret_cast<unsigned int*>(m->y), (size_t)m->R));
+    CK(L(k_copy_words, dim3(1), dim3(256), 0, reinterpret_cast<const unsigned int*>(prm_src),
+         reinterpret_cast<unsigned int*>(&st->prm), sizeof(SolveParams) / 4));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, body, 1, cudaGraphCondAssignDefault));
+    CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
+    CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup, st->fh_box));
+    CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
+                      m->partials, m->counter, kPhaseInit, h, 1, sref(m, st->wt), &m->ss));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cond;
+    CK(cudaGraphAddNode(&cond, body, &L.last, nullptr, 1, &cp));
+    Launcher B;
+    B.graph = cp.conditional.phGraph_out[0];
+    CK(launch_warp(B, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup, st->fh_box));
+    CK(launch_project(B, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
+                      m->partials, m->counter, kPhaseTrial, h, 1, sref(m, st->wt), &m->ss));
+    L.last = cond;
+    CK(launch_tumor(L, m->md, st->w, 0.0, 0, &st->prm, st->tumor, &st->tumor_steps));
+    CK(L(k_publish, dim3(1), dim3(128), 0, reinterpret_cast<const unsigned int*>(st),
+         reinterpret_cast<unsigned int*>(res_dst), sizeof(SolveState) / 4, (volatile int*)flag, seq));
+    return PR_OK;
+}
+
+// (Re)build a lane's graph over the resident models `ms` (id order), growing
+// its staging as needed. Called with the context lock held, so no model can
+// be released meanwhile.
+int build_lane(TickLane& ln, const std::vector<Model*>& ms, long long epoch) {
+    lane_free_graph(ln);
+    const int n = (int)ms.size();
+    if (n > kMaxLaneModels) return fail(PR_EUNSUPPORTED, "more than %d models in a serving lane", kMaxLaneModels);
+    std::vector<size_t> off((size_t)n);
+    size_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        off[(size_t)i] = total;
+        total += ((size_t)ms[(size_t)i]->R + 3) / 4 * 4;
+    }
+    if (ln.cap < n || ln.y_cap < total) {
+        const int cap = std::max(n, 1);
+        const size_t ycap = std::max<size_t>(total, 4);
+        void* dev[] = {ln.active, ln.handles, ln.prm, ln.y};
+        for (void* d : dev)
+            if (d) cudaFree(d);
+        void* host[] = {ln.active_h, ln.prm_h, ln.y_h, ln.res_h, ln.flag_h};
+        for (void* h : host)
+            if (h) cudaFreeHost(h);
+        ln.active = nullptr, ln.handles = nullptr, ln.prm = nullptr, ln.y = nullptr, ln.res = nullptr;
+        ln.active_h = nullptr, ln.prm_h = nullptr, ln.y_h = nullptr, ln.res_h = nullptr, ln.flag_h = nullptr;
+        ln.flag = nullptr, ln.seq = 0;
+        ln.cap = 0, ln.y_cap = 0;
+        cudaError_t e = cudaMalloc(&ln.active, (size_t)cap * sizeof(int));
+        if (!e) e = cudaMalloc(&ln.handles, (size_t)cap * sizeof(cudaGraphConditionalHandle));
+        if (!e) e = cudaMalloc(&ln.prm, (size_t)cap * sizeof(SolveParams));
+        if (!e) e = cudaMalloc(&ln.y, ycap * 4);
+        if (!e) e = cudaHostAlloc((void**)&ln.active_h, (size_t)cap * sizeof(int), cudaHostAllocDefault);
+        if (!e) e = cudaHostAlloc((void**)&ln.prm_h, (size_t)cap * sizeof(SolveParams), cudaHostAllocDefault);
+        if (!e) e = cudaHostAlloc((void**)&ln.y_h, ycap * 4, cudaHostAllocDefault);
+        if (!e) e = cudaHostAlloc((void**)&ln.res_h, (size_t)cap * sizeof(SolveState), cudaHostAllocMapped);
+        if (!e) e = cudaHostAlloc((void**)&ln.flag_h, (size_t)cap * sizeof(int), cudaHostAllocMapped);
+        if (!e) e = cudaHostGetDevicePointer((void**)&ln.res, ln.res_h, 0);
+        if (!e) e = cudaHostGetDevicePointer((void**)&ln.flag, ln.flag_h, 0);
+        if (!e) memset(ln.flag_h, 0, (size_t)cap * sizeof(int));
+        if (e) {
+            cudaGetLastError();
+            return fail(PR_ENOMEM, "serving lane staging: %s", cudaGetErrorString(e));
+        }
+        ln.cap = cap;
+        ln.y_cap = ycap;
+    }
+    CK(cudaGraphCreate(&ln.graph, 0));
+    std::vector<cudaGraphConditionalHandle> hs((size_t)n);
+    for (int i = 0; i < n; ++i) CK(cudaGraphConditionalHandleCreate(&hs[(size_t)i], ln.graph, 0, cudaGraphCondAssignDefault));
+    if (n > 0)
+        CK(cudaMemcpy(ln.handles, hs.data(), (size_t)n * sizeof(cudaGraphConditionalHandle), cudaMemcpyHostToDevice));
+    Launcher L;
+    L.graph = ln.graph;
+    CK(L(k_tick_set, dim3(1), dim3((unsigned)std::max(32, (n + 31) / 32 * 32)), 0, (const int*)ln.active,
+         (const cudaGraphConditionalHandle*)ln.handles, n));
+    const cudaGraphNode_t root = L.last;
+    ln.pos.clear();
+    for (int i = 0; i < n; ++i) {
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = hs[(size_t)i];
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddNode(&node, ln.graph, &root, nullptr, 1, &cp));
+        TRY(add_tick_branch(cp.conditional.phGraph_out[0], ms[(size_t)i], ln.y + off[(size_t)i], ln.prm + i, ln.res + i,
+                            ln.flag + i, ln.active + i));
+        ln.pos[ms[(size_t)i]->id] = i;
+    }
+    CK(cudaGraphInstantiate(&ln.exec, ln.graph, 0));
+    ln.y_off = off;
+    ln.epoch = epoch;
+    return PR_OK;
+}
+
+// Stage one tick's frames into the lane and launch it (lock not held; the
+// chosen models have frames in flight, so they stay resident).
+cudaError_t launch_tick(TickLane& ln, const std::vector<std::pair<Model*, const ServeRequest*>>& work) {
+    const int n = (int)ln.y_off.size();
+    memset(ln.active_h, 0, (size_t)n * sizeof(int));
+    ln.seq = ln.seq == 0x7fffffff ? 1 : ln.seq + 1;
+    cudaError_t e = cudaEventRecord(ln.start, ln.stream);
+    for (const auto& wr : work) {
+        Model* m = wr.first;
+        const ServeRequest* r = wr.second;
+        const int i = ln.pos.at(m->id);
+        ln.active_h[i] = ln.seq;  // switches the branch on; its result flag will carry this value
+        ln.prm_h[i] = make_params(m, r->angle, &r->opts);
+        memcpy(ln.y_h + ln.y_off[(size_t)i], r->y.data(), (size_t)m->R * 4);
+        if (!e) e = cudaMemcpyAsync(ln.y + ln.y_off[(size_t)i], ln.y_h + ln.y_off[(size_t)i], (size_t)m->R * 4,
+                                    cudaMemcpyHostToDevice, ln.stream);
+    }
+    if (!e) e = cudaMemcpyAsync(ln.prm, ln.prm_h, (size_t)n * sizeof(SolveParams), cudaMemcpyHostToDevice, ln.stream);
+    if (!e) e = cudaMemcpyAsync(ln.active, ln.active_h, (size_t)n * sizeof(int), cudaMemcpyHostToDevice, ln.stream);
+    if (!e) e = cudaGraphLaunch(ln.exec, ln.stream);
+    if (!e) e = cudaEventRecord(ln.done, ln.stream);
+    return e;
+}
+
+// Worker of the tick-batched mode: retire finished ticks, then give every
+// free lane the oldest pending frame of each resident model that has nothing
+// in flight, as one launch.
+void serve_loop_ticks(pr_ctx* c) {
+    cudaSetDevice(c->device);
+    Serve* sv = c->serve;
+    std::unique_lock<std::mutex> lock(c->mu);
+    for (;;) {
+        bool busy = false, progressed = false;
+        for (TickLane& ln : sv->lanes) {
+            if (!ln.busy) continue;
+            // frames whose branch has published its result: retire them now,
+            // so that their models can take part in the next free lane's tick
+            const auto now = std::chrono::steady_clock::now();
+            for (size_t k = 0; k < ln.reqs.size(); ++k) {
+                if (ln.retired[k]) continue;
+                const ServeRequest& r = ln.reqs[k];
+                const int i = ln.pos.at(r.model);
+                if (reinterpret_cast<volatile int*>(ln.flag_h)[i] != ln.seq) continue;
+                std::atomic_thread_fence(std::memory_order_acquire);
+                SolveState st_copy;
+                memcpy(&st_copy, (const void*)(ln.res_h + i), sizeof st_copy);
+                pr_served out;
+                memset(&out, 0, sizeof out);
+                out.tag = r.tag;
+                out.model_id = r.model;
+                Model* m = find(c, r.model);
+                if (m) fill_result(m, st_copy, &out.result);
+                out.queue_ms = ms_between(r.t_submit, ln.t_dispatch);
+                out.gpu_ms = ms_between(ln.t_dispatch, now);
+                out.latency_ms = ms_between(r.t_submit, now);
+                sv->in_flight.erase(r.model);
+                sv->done.push_back(out);
+                ln.retired[k] = 1;
+                progressed = true;
+            }
+            if (progressed) sv->cv_done.notify_all();
+            cudaError_t q = cudaEventQuery(ln.done);
+            if (q == cudaErrorNotReady) {
+                busy = true;
+                continue;
+            }
+            // the tick is over: its branches' flags, written before the graph
+            // completed, are all visible now; anything not retired failed
+            std::atomic_thread_fence(std::memory_order_acquire);
+            const auto end = std::chrono::steady_clock::now();
+            for (size_t k = 0; k < ln.reqs.size(); ++k) {
+                if (ln.retired[k]) continue;
+                const ServeRequest& r = ln.reqs[k];
+                const int i = ln.pos.at(r.model);
+                pr_served out;
+                memset(&out, 0, sizeof out);
+                out.tag = r.tag;
+                out.model_id = r.model;
+                Model* m = find(c, r.model);
+                if (q == cudaSuccess && m && reinterpret_cast<volatile int*>(ln.flag_h)[i] == ln.seq) {
+                    SolveState st_copy;
+                    memcpy(&st_copy, (const void*)(ln.res_h + i), sizeof st_copy);
+                    fill_result(m, st_copy, &out.result);
+                    out.queue_ms = ms_between(r.t_submit, ln.t_dispatch);
+                    out.gpu_ms = ms_between(ln.t_dispatch, end);
+                    out.latency_ms = ms_between(r.t_submit, end);
+                } else {
+                    out.status = PR_ECUDA;
+                    sv->error = PR_ECUDA;
+                    sv->error_msg = q != cudaSuccess ? std::string("served tick failed: ") + cudaGetErrorString(q)
+                                                     : std::string("a served branch finished without its result");
+                }
+                sv->in_flight.erase(r.model);
+                sv->done.push_back(out);
+            }
+            ln.reqs.clear();
+            ln.retired.clear();
+            ln.busy = false;
+            sv->cv_done.notify_all();
+            progressed = true;
+        }
+        bool dispatchable = false;
+        for (TickLane& ln : sv->lanes) {
+            if (ln.busy || sv->error) continue;
+            std::vector<ServeRequest> chosen;
+            std::set<int> taken;
+            for (auto it = sv->pending.begin(); it != sv->pending.end();) {
+                if (sv->tick_frames > 0 && (int)chosen.size() >= sv->tick_frames) break;
+                if (!sv->in_flight.count(it->model) && !taken.count(it->model) && find(c, it->model)) {
+                    taken.insert(it->model);
+                    chosen.push_back(std::move(*it));
+                    it = sv->pending.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+            if (chosen.empty()) break;
+            dispatchable = true;
+            int rc = PR_OK;
+            if (ln.epoch != c->model_epoch) {
+                std::vector<Model*> ms;
+                for (auto& kv : c->models) ms.push_back(kv.second);
+                rc = build_lane(ln, ms, c->model_epoch);
+            }
+            std::vector<std::pair<Model*, const ServeRequest*>> work;
+            for (const ServeRequest& r : chosen) {
+                work.push_back({find(c, r.model), &r});
+                sv->in_flight.insert(r.model);
+            }
+            ln.busy = true;
+            ln.t_dispatch = std::chrono::steady_clock::now();
+            cudaError_t e = rc ? cudaErrorUnknown : cudaSuccess;
+            if (!e) {
+                lock.unlock();
+                e = launch_tick(ln, work);
+                lock.lock();
+            }
+            if (e) {
+                ln.busy = false;
+                sv->error = PR_ECUDA;
+                sv->error_msg = rc ? std::string("serving lane build failed: ") + g_err
+                                   : std::string("tick dispatch failed: ") + cudaGetErrorString(e);
+                for (const ServeRequest& r : chosen) {
+                    sv->in_flight.erase(r.model);
+                    pr_served out;
+                    memset(&out, 0, sizeof out);
+                    out.tag = r.tag;
+                    out.model_id = r.model;
+                    out.status = PR_ECUDA;
+                    sv->done.push_back(out);
+                }
+                sv->cv_done.notify_all();
+                continue;
+            }
+            for (ServeRequest& r : chosen) {
+                r.y.clear();
+                r.y.shrink_to_fit();
+            }
+            ln.retired.assign(chosen.size(), 0);
+            ln.reqs = std::move(chosen);
+            busy = true;
+            progressed = true;
+        }
+        // Stop once idle; frames of models still waiting for admission stay
+        // queued, and after an error nothing more is dispatched.
+        if (sv->stop && !busy && !dispatchable) {
+            bool any = false;
+            for (const ServeRequest& r : sv->pending) any = any || find(c, r.model) != nullptr;
+            if (!any || sv->error) break;
+        }
+        if (busy && !progressed) {
+            lock.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            lock.lock();
+        } else if (!busy && !progressed) {
+            sv->cv_work.wait_for(lock, std::chrono::milliseconds(50));
+        }
+    }
+}
+
 void serve_loop(pr_ctx* c) {
     cudaSetDevice(c->device);
     Serve* sv = c->serve;
@@ -697,9 +1095,10 @@ void serve_loop(pr_ctx* c) {
         for (ServeSlot& sl : sv->slots) {
             if (sl.busy || sv->error) continue;
             auto it = sv->pending.begin();
-            while (it != sv->pending.end() && sv->in_flight.count(it->model)) ++it;
+            while (it != sv->pending.end() && (sv->in_flight.count(it->model) || !find(c, it->model))) ++it;
             if (it == sv->pending.end()) break;
             Model* m = find(c, it->model);
+            if (m && !m->exec && build_graph(c, m) != PR_OK) m = nullptr;  // admitted while serving
             sl.req = std::move(*it);
             sv->pending.erase(it);
             sl.t_dispatch = std::chrono::steady_clock::now();
@@ -751,7 +1150,13 @@ void serve_loop(pr_ctx* c) {
             busy = true;
             progressed = true;
         }
-        if (sv->stop && !busy && sv->pending.empty()) break;
+        if (sv->stop && !busy) {
+            // stop once idle; frames of models still waiting for admission stay
+            // queued, and after an error nothing more is dispatched
+            bool any = false;
+            for (const ServeRequest& r : sv->pending) any = any || find(c, r.model) != nullptr;
+            if (!any || sv->error) break;
+        }
         if (busy && !progressed) {
             // a solve is running: poll its event again shortly
             lock.unlock();
@@ -784,6 +1189,13 @@ void serve_free(pr_ctx* c) {
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.host_state) cudaFreeHost(sl.host_state);
         if (sl.y_pinned) cudaFreeHost(sl.y_pinned);
+    }
+    for (TickLane& ln : c->serve->lanes) {
+        if (ln.stream) cudaStreamSynchronize(ln.stream);
+        lane_free(ln);
+        if (ln.start) cudaEventDestroy(ln.start);
+        if (ln.done) cudaEventDestroy(ln.done);
+        if (ln.stream) cudaStreamDestroy(ln.stream);
     }
     delete c->serve;
     c->serve = nullptr;
@@ -854,32 +1266,22 @@ void pr_destroy(pr_ctx* c) {
     batch_free(c);
     for (auto& kv : c->models) free_model(kv.second);
     c->models.clear();
+    for (Waiting* w : c->waiting) delete w;
+    c->waiting.clear();
     if (c->pad) cudaFree(c->pad);
     if (c->rg) cudaFree(c->rg);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
 
-int pr_load_model(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom, int location, const float* f0,
-                  const float* mean_dvf, const float* U, int K, int storage, const double tumor_ref_xyz[3],
-                  int* model_id) {
-    if (!c || !model_id) return fail(PR_EINVAL, "null context or model_id");
-    if (!vol_ok(vol)) return fail(PR_EINVAL, "invalid volume descriptor");
-    if (!geom_ok(geom)) return fail(PR_EINVAL, "invalid geometry");
-    if (K < 1 || K > PR_MAX_K) return fail(PR_EINVAL, "K=%d outside 1..%d", K, PR_MAX_K);
-    if (storage != PR_F32 && storage != PR_BF16) return fail(PR_EINVAL, "unknown storage %d", storage);
-    if (location != PR_HOST && location != PR_DEVICE) return fail(PR_EINVAL, "unknown location %d", location);
-    if (!f0 || !mean_dvf || !U || !tumor_ref_xyz) return fail(PR_EINVAL, "null input array");
-    CK(cudaSetDevice(c->device));
-    size_t need = model_bytes(*vol, *geom, K, storage);
-    size_t used_now;
-    {
-        std::lock_guard<std::mutex> lock(c->mu);
-        used_now = c->used;
-    }
-    if (used_now + need > c->budget)
-        return fail(PR_EADMIT, "model needs %zu bytes, %zu of %zu budget in use", need, used_now, c->budget);
+}  // extern "C"
 
+namespace {
+
+// Allocate, upload and register a model under `id` (0 = a new id).
+int load_resident(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom, int location, const float* f0,
+                  const float* mean_dvf, const float* U, int K, int storage, const double tumor_ref_xyz[3], int id,
+                  int* model_id) {
     Model* m = new Model;
     m->vol = *vol;
     m->geom = *geom;
@@ -994,15 +1396,141 @@ int pr_load_model(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
         free_model(m);
         return rc;
     }
-    std::lock_guard<std::mutex> lock(c->mu);
-    m->id = c->next_id++;
-    c->used += m->bytes;
-    c->models[m->id] = m;
-    *model_id = m->id;
+    {
+        std::lock_guard<std::mutex> lock(c->mu);
+        m->id = id ? id : c->next_id++;
+        c->used += m->bytes;
+        c->models[m->id] = m;
+        c->model_epoch += 1;
+        *model_id = m->id;
+    }
+    if (c->serve) c->serve->cv_work.notify_all();  // its queued frames can now run
     return PR_OK;
 }
 
+// Admit waiting models in FIFO order while the budget has room for the one
+// at the front (called after memory was released).
+int admit_waiting(pr_ctx* c) {
+    for (;;) {
+        Waiting* w = nullptr;
+        {
+            std::lock_guard<std::mutex> lock(c->mu);
+            if (c->waiting.empty() || c->used + c->waiting.front()->need > c->budget) return PR_OK;
+            w = c->waiting.front();
+        }
+        int got = 0;
+        int rc = load_resident(c, &w->vol, &w->geom, PR_HOST, w->f0.data(), w->mean.data(), w->U.data(), w->K,
+                               w->storage, w->c0, w->id, &got);
+        if (rc) return rc;  // stays at the front of the queue
+        {
+            std::lock_guard<std::mutex> lock(c->mu);
+            c->waiting.pop_front();
+        }
+        delete w;
+    }
+}
+
+Waiting* find_waiting(pr_ctx* c, int id) {
+    for (Waiting* w : c->waiting)
+        if (w->id == id) return w;
+    return nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pr_load_model(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom, int location, const float* f0,
+                  const float* mean_dvf, const float* U, int K, int storage, const double tumor_ref_xyz[3],
+                  int* model_id) {
+    if (!c || !model_id) return fail(PR_EINVAL, "null context or model_id");
+    if (!vol_ok(vol)) return fail(PR_EINVAL, "invalid volume descriptor");
+    if (!geom_ok(geom)) return fail(PR_EINVAL, "invalid geometry");
+    if (K < 1 || K > PR_MAX_K) return fail(PR_EINVAL, "K=%d outside 1..%d", K, PR_MAX_K);
+    if (storage != PR_F32 && storage != PR_BF16) return fail(PR_EINVAL, "unknown storage %d", storage);
+    if (location != PR_HOST && location != PR_DEVICE) return fail(PR_EINVAL, "unknown location %d", location);
+    if (!f0 || !mean_dvf || !U || !tumor_ref_xyz) return fail(PR_EINVAL, "null input array");
+    CK(cudaSetDevice(c->device));
+    size_t need = model_bytes(*vol, *geom, K, storage);
+    size_t used_now;
+    bool queue;
+    {
+        std::lock_guard<std::mutex> lock(c->mu);
+        used_now = c->used;
+        queue = c->admit_queue;
+        // behind models already waiting, in arrival order
+        if (queue && !c->waiting.empty()) used_now = c->budget;
+    }
+    if (used_now + need <= c->budget)
+        return load_resident(c, vol, geom, location, f0, mean_dvf, U, K, storage, tumor_ref_xyz, 0, model_id);
+    if (!queue || need > c->budget)
+        return fail(PR_EADMIT, "model needs %zu bytes, %zu of %zu budget in use", need, used_now, c->budget);
+    // admission queue: keep host copies of the inputs until memory frees up
+    Waiting* w = new Waiting;
+    w->vol = *vol;
+    w->geom = *geom;
+    w->K = K;
+    w->storage = storage;
+    w->need = need;
+    for (int i = 0; i < 3; ++i) w->c0[i] = tumor_ref_xyz[i];
+    const size_t n = (size_t)vol->nx * vol->ny * vol->nz;
+    w->f0.resize(n);
+    w->mean.resize(3 * n);
+    w->U.resize(3 * (size_t)K * n);
+    const cudaMemcpyKind kind = location == PR_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaMemcpy(w->f0.data(), f0, n * 4, kind);
+    if (!e) e = cudaMemcpy(w->mean.data(), mean_dvf, 3 * n * 4, kind);
+    if (!e) e = cudaMemcpy(w->U.data(), U, 3 * (size_t)K * n * 4, kind);
+    if (e) {
+        delete w;
+        return fail(PR_ECUDA, "copying the waiting model's inputs failed: %s", cudaGetErrorString(e));
+    }
+    {
+        std::lock_guard<std::mutex> lock(c->mu);
+        w->id = c->next_id++;
+        c->waiting.push_back(w);
+        *model_id = w->id;
+    }
+    fail(PR_QUEUED, "model %d needs %zu bytes and waits for admission", *model_id, need);
+    return PR_QUEUED;
+}
+
+int pr_set_admission_queue(pr_ctx* c, int enable) {
+    if (!c) return fail(PR_EINVAL, "null context");
+    std::lock_guard<std::mutex> lock(c->mu);
+    c->admit_queue = enable != 0;
+    return PR_OK;
+}
+
+int pr_model_status(pr_ctx* c, int id, int* status) {
+    if (!c || !status) return fail(PR_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lock(c->mu);
+    if (find(c, id)) {
+        *status = PR_MODEL_RESIDENT;
+        return PR_OK;
+    }
+    for (size_t i = 0; i < c->waiting.size(); ++i)
+        if (c->waiting[i]->id == id) {
+            *status = PR_MODEL_WAITING;
+            return PR_OK;
+        }
+    return fail(PR_ENOMODEL, "unknown model id %d", id);
+}
+
 int pr_release_model(pr_ctx* c, int id) {
+    if (!c) return fail(PR_EINVAL, "null context");
+    {
+        std::lock_guard<std::mutex> lock(c->mu);
+        Waiting* w = find_waiting(c, id);
+        if (w) {
+            if (c->serve)
+                for (const ServeRequest& r : c->serve->pending)
+                    if (r.model == id) return fail(PR_EINVAL, "model %d has served frames outstanding", id);
+            c->waiting.erase(std::find(c->waiting.begin(), c->waiting.end(), w));
+            delete w;
+            return PR_OK;
+        }
+    }
     GET_MODEL(c, id, m);
     CK(cudaStreamSynchronize(c->stream));
     {
@@ -1014,11 +1542,12 @@ int pr_release_model(pr_ctx* c, int id) {
         }
         c->used -= m->bytes;
         c->models.erase(id);
+        c->model_epoch += 1;
     }
     if (c->batch && std::find(c->batch->key.begin(), c->batch->key.end(), id) != c->batch->key.end())
         batch_drop_graph(c->batch);  // its nodes point into this model's buffers
     free_model(m);
-    return PR_OK;
+    return admit_waiting(c);
 }
 
 int pr_model_footprint(pr_ctx* c, int id, size_t* bytes) {
@@ -1554,8 +2083,43 @@ int pr_serve_start(pr_ctx* c, int slots) {
     return PR_OK;
 }
 
+int pr_serve_start_batched(pr_ctx* c, int lanes, int tick_frames) {
+    if (!c) return fail(PR_EINVAL, "null context");
+    if (lanes < 1 || lanes > 8) return fail(PR_EINVAL, "lanes must be 1..8");
+    if (tick_frames < 0) return fail(PR_EINVAL, "tick_frames must be >= 0");
+    if (c->serve && !c->serve->stop) return fail(PR_EINVAL, "serving already started");
+    CK(cudaSetDevice(c->device));
+    if (c->serve) serve_free(c);  // restart after pr_serve_stop: untaken results are dropped
+    Serve* sv = new Serve;
+    sv->tick_frames = tick_frames;
+    sv->lanes.resize(lanes);
+    for (TickLane& ln : sv->lanes) {
+        cudaError_t e = cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking);
+        if (!e) e = cudaEventCreate(&ln.start);
+        if (!e) e = cudaEventCreate(&ln.done);
+        if (e) {
+            c->serve = sv;
+            serve_free(c);
+            return fail(PR_ECUDA, "serving set-up failed: %s", cudaGetErrorString(e));
+        }
+    }
+    c->serve = sv;
+    sv->worker = std::thread(serve_loop_ticks, c);
+    return PR_OK;
+}
+
 int pr_submit(pr_ctx* c, int id, const float* y, double angle, const pr_solve_opts* opts, uint64_t tag) {
-    GET_MODEL(c, id, m);
+    if (!c) return fail(PR_EINVAL, "null context");
+    Model* m = nullptr;
+    int R = 0;
+    {
+        std::lock_guard<std::mutex> lock(c->mu);
+        m = find(c, id);
+        Waiting* w = m ? nullptr : find_waiting(c, id);
+        if (!m && !w) return fail(PR_ENOMODEL, "unknown model id %d", id);
+        R = m ? m->R : w->geom.nu * w->geom.nv;
+    }
+    CK(cudaSetDevice(c->device));
     if (!c->serve) return fail(PR_EINVAL, "serving not started (pr_serve_start)");
     if (!y) return fail(PR_EINVAL, "null y");
     pr_solve_opts o;
@@ -1565,13 +2129,13 @@ int pr_submit(pr_ctx* c, int id, const float* y, double angle, const pr_solve_op
         pr_default_opts(&o);
     if (!opts_ok(&o) || o.loop_mode != PR_LOOP_GRAPH) return fail(PR_EINVAL, "invalid solve options for serving");
     if (!isfinite(angle)) return fail(PR_EINVAL, "angle is not finite");
-    if (!m->exec) TRY(build_graph(c, m));
+    if (m && c->serve->slots.size() && !m->exec) TRY(build_graph(c, m));
     ServeRequest r;
     r.model = id;
     r.tag = tag;
     r.angle = angle;
     r.opts = o;
-    r.y.assign(y, y + m->R);
+    r.y.assign(y, y + R);
     r.t_submit = std::chrono::steady_clock::now();
     {
         std::lock_guard<std::mutex> lock(c->mu);

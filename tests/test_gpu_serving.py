@@ -1,7 +1,10 @@
 """Serving: frames of several patients (different volume sizes) submitted
-together run concurrently in stream slots; every frame's result must be the
-same as when that patient's frames are solved alone, one after the other
-(the kernels' reductions are deterministic, so the same means bitwise)."""
+together run concurrently, in stream slots or in tick-batched launches (one
+graph launch per tick over the pending frames of every patient); every
+frame's result must be the same as when that patient's frames are solved
+alone, one after the other (the kernels' reductions are deterministic, so
+the same means bitwise). Over-budget patients wait in the admission queue
+until a release frees memory."""
 
 import numpy as np
 import pytest
@@ -43,7 +46,22 @@ def _opts():
     return default_opts(max_iters=6)
 
 
-def test_served_results_equal_solo_results(patients):
+def _solo(ctx, mids, patients):
+    solo = {}
+    for i, (mid, p) in enumerate(zip(mids, patients)):
+        ctx.set_state(mid, np.zeros(3))
+        for j, (th, y) in enumerate(p["frames"]):
+            solo[(i, j)] = ctx.reconstruct(mid, y, th, _opts())
+    return solo
+
+
+def _same(a, b, key):
+    for k in ("w", "a", "b", "J", "tumor", "iters", "trials"):
+        assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), (key, k)
+
+
+@pytest.mark.parametrize("mode", ["slots", "batched"])
+def test_served_results_equal_solo_results(patients, mode):
     from paper_1004_0014_b300 import Context
 
     ctx = Context(0)
@@ -56,7 +74,10 @@ def test_served_results_equal_solo_results(patients):
                 solo[(i, j)] = ctx.reconstruct(mid, y, th, _opts())
         for mid in mids:
             ctx.set_state(mid, np.zeros(3))
-        ctx.serve_start(slots=3)
+        if mode == "slots":
+            ctx.serve_start(slots=3)
+        else:
+            ctx.serve_start(batched_lanes=2)
         # interleave the patients' frames as they would arrive
         for j in range(FRAMES):
             for i, (mid, p) in enumerate(zip(mids, patients)):
@@ -70,9 +91,7 @@ def test_served_results_equal_solo_results(patients):
             assert r["latency_ms"] >= r["gpu_ms"] * 0.999 >= 0.0
         ctx.serve_stop()
         for key, a in solo.items():
-            b = served[key]
-            for k in ("w", "a", "b", "J", "tumor", "iters", "trials"):
-                assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), (key, k)
+            _same(a, served[key], key)
     finally:
         ctx.close()
 
@@ -112,5 +131,54 @@ def test_admission_and_release_rules(patients):
         ctx.submit(b, y, th, _opts(), tag=8)
         assert ctx.poll(timeout_ms=60000)["tag"] == 8
         ctx.serve_stop()
+    finally:
+        ctx.close()
+
+
+def test_admission_queue_admits_a_waiting_patient_after_a_release(patients):
+    """A budget that holds one of two patients: the second is queued
+    (PR_QUEUED, status waiting), its submitted frames wait, and releasing
+    the first admits it; its served frames then equal its solo results."""
+    from paper_1004_0014_b300 import Context, PcaReconError, capi
+
+    p0, p1 = patients[0], patients[1]
+    ref = Context(0)
+    try:
+        r0 = ref.load_model(p0["vol"], GEOM, p0["f0"], p0["mean"], p0["U"], p0["c0"])
+        r1 = ref.load_model(p1["vol"], GEOM, p1["f0"], p1["mean"], p1["U"], p1["c0"])
+        need0, need1 = ref.footprint(r0), ref.footprint(r1)
+        solo1 = _solo(ref, [r1], [p1])
+    finally:
+        ref.close()
+    budget = max(need0, need1) + min(need0, need1) // 2
+    ctx = Context(0, hbm_budget_bytes=budget)
+    try:
+        ctx.set_admission_queue(True)
+        a = ctx.load_model(p0["vol"], GEOM, p0["f0"], p0["mean"], p0["U"], p0["c0"])
+        b = ctx.load_model(p1["vol"], GEOM, p1["f0"], p1["mean"], p1["U"], p1["c0"])
+        assert ctx.model_status(a) == capi.PR_MODEL_RESIDENT
+        assert ctx.model_status(b) == capi.PR_MODEL_WAITING
+        with pytest.raises(PcaReconError) as e:
+            ctx.reconstruct(b, p1["frames"][0][1], 0.0)  # not resident yet
+        assert e.value.code == -6
+        ctx.set_state(a, np.zeros(3))
+        ctx.serve_start(batched_lanes=2)
+        for j, (th, y) in enumerate(p1["frames"]):
+            ctx.submit(b, y, th, _opts(), tag=100 + j)
+        for j, (th, y) in enumerate(p0["frames"][:2]):
+            ctx.submit(a, y, th, _opts(), tag=j)
+        got = sorted(ctx.poll(timeout_ms=60000)["tag"] for _ in range(2))
+        assert got == [0, 1]  # the resident patient's frames are served
+        assert ctx.poll(timeout_ms=300) is None  # the waiting patient's frames stay queued
+        ctx.release_model(a)  # frees the budget: b is admitted and its frames run
+        assert ctx.model_status(b) == capi.PR_MODEL_RESIDENT
+        served = {}
+        for _ in p1["frames"]:
+            r = ctx.poll(timeout_ms=60000)
+            assert r["status"] == 0
+            served[(0, r["tag"] - 100)] = r
+        ctx.serve_stop()
+        for key, s1 in solo1.items():
+            _same(s1, served[key], key)
     finally:
         ctx.close()
