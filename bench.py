@@ -983,7 +983,7 @@ def main():
     ap.add_argument("--no-extra-arms", action="store_true",
                     help="skip the BF16-storage and short served arms of the default run")
     ap.add_argument("--adjoint", action="store_true", help="also time the gather-adjoint gradient kernel")
-    ap.add_argument("--detector", default="512x384", choices=["512x384", "200x150", "1000x750"],
+    ap.add_argument("--detector", default="512x384", choices=["512x384", "200x150", "1000x750", "40x30", "20x15"],
                     help="detector sampling of the 40x30 cm panel")
     ap.add_argument("--K", type=int, default=3, choices=range(1, 8), help="PCA modes of the paper-scale model")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"], help="storage of f0 and U")
