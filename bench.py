@@ -181,8 +181,12 @@ def build_model_inputs(detector: str = "512x384", K: int = 3):
     return w, f0, pca.mean.astype(np.float32), pca.U.astype(np.float32), tumor_centre(vol)
 
 
+FIXED_ANGLE = None  # gantry angle (deg) of every frame with --fixed-angle
+
+
 def frame_params(w, j):
-    return math.radians(w["frame_angle_deg"](j)), w["frame_time"](j), w["frame_seed"](j)
+    deg = w["frame_angle_deg"](j) if FIXED_ANGLE is None else FIXED_ANGLE
+    return math.radians(deg), w["frame_time"](j), w["frame_seed"](j)
 
 
 def make_targets(ctx, w, f0, frames):
@@ -383,6 +387,26 @@ def frame_list_text(frames) -> str:
     if len(frames) > 1 and all(b - a == frames[1] - frames[0] for a, b in zip(frames, frames[1:])):
         return "%d, %d, ..., %d" % (frames[0], frames[1], frames[-1])
     return ", ".join(str(j) for j in frames)
+
+
+def run_profile_pass(args):
+    """One model at the workload; the solver-pass projector as a line-search
+    trial runs it, at --profile-angle degrees: a setup pass (no moments), then
+    three trial passes (for ncu: -k regex:k_project_split -s 1 -c 1 takes the
+    first trial pass). Prints the CUDA-event time per trial pass."""
+    from paper_1004_0014_b300 import PR_BF16, PR_F32, Context, capi
+
+    w, f0, mean, U, c0 = build_model_inputs(args.detector, args.K)
+    ctx = Context(0)
+    mid = ctx.load_model(w["vol"], w["geom"], f0, mean, U, c0,
+                         storage=PR_BF16 if args.storage == "bf16" else PR_F32)
+    ctx.set_state(mid, np.array([-1.0, 0.3, 0.05, 0.1, -0.05, 0.0, 0.0][:w["K"]]))
+    th = math.radians(args.profile_angle)
+    ms = ctx.time_kernel(mid, capi.PR_KERNEL_PROJECT_FH_TRIAL, th, iters=3)
+    print(json.dumps({"profile_pass": "k_project_split trial pass", "angle_deg": args.profile_angle, "ms": ms,
+                      "samples": ctx.count_samples(mid, th, ctx.get_state(mid))}), flush=True)
+    ctx.close()
+    return 0
 
 
 def run_ours(args):
@@ -610,9 +634,11 @@ def run_ours(args):
             "config": {"workload": WORKLOAD % (args.storage, Km, args.detector), "volume": [vol.nx, vol.ny, vol.nz],
                        "spacing_mm": [vol.dx, vol.dy, vol.dz], "K": Km, "detector": [geom.nu, geom.nv],
                        "pixel_mm": geom.du, "ray_step_mm": geom.ds, "iterations": w["max_iters"],
-                       "frames": "j = %s (spread over one rotation): angle j deg, t = j/6 s, 1%% noise seed j, "
-                                 "each warm-started from the frame before it in this list (warm-up frames j = %d..-1)"
-                                 % (frame_list_text(frames[W:]), -W),
+                       "frames": ("j = %s (spread over one rotation): angle j deg, t = j/6 s, 1%% noise seed j, "
+                                  "each warm-started from the frame before it in this list (warm-up frames j = %d..-1)"
+                                  % (frame_list_text(frames[W:]), -W)) if FIXED_ANGLE is None else
+                                 ("j = %s at the fixed angle %g deg (fluoroscopy), t = j/6 s, 1%% noise seed j, each "
+                                  "warm-started from the frame before it" % (frame_list_text(frames[W:]), FIXED_ANGLE)),
                        "storage": "bfloat16 f0 and U, float32 mean" if bf16 else "float32",
                        "loop": "on-device (CUDA graph, conditional WHILE)",
                        "l2": "inputs larger than L2: %d MB of DVF fields streamed per warp pass"
@@ -988,6 +1014,10 @@ def main():
     ap.add_argument("--K", type=int, default=3, choices=range(1, 8), help="PCA modes of the paper-scale model")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"], help="storage of f0 and U")
     ap.add_argument("--serve", action="store_true", help="serving arm: patients streaming Poisson frames")
+    ap.add_argument("--profile-angle", type=float, default=None,
+                    help="run only the projector's trial pass at this gantry angle (for ncu), then exit")
+    ap.add_argument("--fixed-angle", type=float, default=None,
+                    help="every frame at this gantry angle (fluoroscopy, Section 5) instead of the rotation")
     ap.add_argument("--batch", action="store_true", help="batched arm: 64 uneven solves in one graph launch")
     ap.add_argument("--patients", type=int, default=16)
     ap.add_argument("--rate", type=float, default=15.0, help="frames per second per patient (--serve)")
@@ -999,8 +1029,12 @@ def main():
     ap.add_argument("--tick-frames", default="0",
                     help="most frames per tick (--serve-mode batched, 0 = all pending); a comma list runs each")
     args = ap.parse_args()
+    global FIXED_ANGLE
+    FIXED_ANGLE = args.fixed_angle
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.profile_angle is not None:
+        return run_profile_pass(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.serve:
