@@ -135,7 +135,8 @@ def test_admission_and_release_rules(patients):
         ctx.close()
 
 
-def test_admission_queue_admits_a_waiting_patient_after_a_release(patients):
+@pytest.mark.parametrize("mode", ["batched", "slots"])
+def test_admission_queue_admits_a_waiting_patient_after_a_release(patients, mode):
     """A budget that holds one of two patients: the second is queued
     (PR_QUEUED, status waiting), its submitted frames wait, and releasing
     the first admits it; its served frames then equal its solo results."""
@@ -162,7 +163,10 @@ def test_admission_queue_admits_a_waiting_patient_after_a_release(patients):
             ctx.reconstruct(b, p1["frames"][0][1], 0.0)  # not resident yet
         assert e.value.code == -6
         ctx.set_state(a, np.zeros(3))
-        ctx.serve_start(batched_lanes=2)
+        if mode == "batched":
+            ctx.serve_start(batched_lanes=2)
+        else:
+            ctx.serve_start(slots=2)
         for j, (th, y) in enumerate(p1["frames"]):
             ctx.submit(b, y, th, _opts(), tag=100 + j)
         for j, (th, y) in enumerate(p0["frames"][:2]):
