@@ -169,7 +169,10 @@ void pr_destroy(pr_ctx* ctx);
  * f0 [nz][ny][nx] reference volume (1/mm), mean_dvf [3][nz][ny][nx] (mm),
  * U [K][3][nz][ny][nx] eigenvector fields, 1 <= K <= PR_MAX_K, all float32 at
  * `location`. `storage` selects the device copy of f0 and U (PR_F32 or
- * PR_BF16, round-to-nearest-even; the mean stays float32). tumor_ref_xyz is the
+ * PR_BF16, round-to-nearest-even; the mean stays float32). With PR_BF16 and
+ * K = 4 or 5 the solver's intermediate derivative images h_k are also held
+ * as float16 beside a float32 f (their ray sums and every reduction stay
+ * float32/float64). tumor_ref_xyz is the
  * tumor centre in the reference image (mm), used by Section 2.3. The data are
  * copied into resident, immutable device buffers; the model's warm-start w is
  * set to 0. Returns PR_EADMIT if the model would exceed the HBM budget.

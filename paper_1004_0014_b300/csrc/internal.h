@@ -31,6 +31,15 @@ enum WarpMode : int {
 // (h_4, h_5), so that every corner is one 16-byte and one 8-byte aligned load.
 inline int fh_channels(int K) { return K <= 3 ? 4 : (K <= 5 ? 6 : 8); }
 
+// Layout code of the solver volume: fh_channels(K) as above, or kFhHalf6 for a
+// model stored in bfloat16 with K = 4 or 5, whose (f, h_1..h_5) are one 16-byte
+// record per voxel: f as float32, then (h_1, h_2), (h_3, h_4) and (h_5, 0) as
+// float16 pairs (the ray sums of every channel still run in float32).
+constexpr int kFhHalf6 = 16;
+inline int fh_layout(int K, int storage) { return (storage == 1 && (K == 4 || K == 5)) ? kFhHalf6 : fh_channels(K); }
+inline int fh_floats(int layout) { return layout == kFhHalf6 ? 4 : layout; }   // stored floats per voxel
+inline int fh_logical(int layout) { return layout == kFhHalf6 ? 6 : layout; }  // channels the projector sums
+
 // G1: x = mean + U w (Eq. 1), f(v) = F0(v + x(v)), h_k(v) (Section 2.2).
 // w_dev: K doubles in device memory. sup (device, nullable; padded modes
 // only): the model's support record; voxels outside the support box at w_dev

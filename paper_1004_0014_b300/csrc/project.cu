@@ -14,6 +14,7 @@
 // divergent exits. The solver pass (k_project_split) splits each warp's range
 // into parts taken from a work queue; the single-channel pass (k_project) gives
 // a block of 256 threads a 32 x 8 tile.
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "internal.h"
@@ -188,6 +189,12 @@ __device__ __forceinline__ void trace_range(const RayLattice& L, const SupportRe
 constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
 constexpr int kRoundBits = 0x4B400000; // its bit pattern
 
+// The two float16 values packed in a float's bits, as floats (low half first).
+__device__ __forceinline__ float2 unpack_half2(float x) {
+    const unsigned int u = __float_as_uint(x);
+    return __half22float2(*reinterpret_cast<const __half2*>(&u));
+}
+
 // Sample accumulation that keeps the eight corners of the last trilinear cell
 // in registers: consecutive samples 1 mm apart often fall in the same 2-2.5 mm
 // cell, and then a lane that stays in its cell does not touch L1 for that
@@ -199,7 +206,7 @@ constexpr int kRoundBits = 0x4B400000; // its bit pattern
 // (-1, n) of its axis: its cell is then within the padded volume. With kClamp
 // the corner is clamped to [-1, n - 1] and the weights saturated, so a point
 // anywhere lands on the zero border and adds exactly zero.
-template <int NCH>
+template <int NCH, bool HH = false>
 struct CellCache {
     unsigned int base = 0xffffffffu;
     float c[8][NCH];     // corners: index = dx + 2 dy + 4 dz
@@ -235,13 +242,23 @@ struct CellCache {
             base = b;
             const unsigned int off[4] = {0u, (unsigned int)vd.nxp, plane, plane + (unsigned int)vd.nxp};
             const float4* v4 = reinterpret_cast<const float4*>(vol);
+            if constexpr (HH) {
+                // one 16-byte record per corner: f, then float16 pairs (h1, h2), (h3, h4), (h5, 0)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const float4 a = __ldg(v4 + b + off[k >> 1] + (k & 1));
+                    const float2 p = unpack_half2(a.y), q = unpack_half2(a.z), r = unpack_half2(a.w);
+                    c[k][0] = a.x, c[k][1] = p.x, c[k][2] = p.y, c[k][3] = q.x, c[k][4] = q.y, c[k][5] = r.x;
+                }
+            } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 float4 a0 = __ldg(v4 + b + off[k]), a1 = __ldg(v4 + b + off[k] + 1);
                 c[2 * k][0] = a0.x, c[2 * k][1] = a0.y, c[2 * k][2] = a0.z, c[2 * k][3] = a0.w;
                 c[2 * k + 1][0] = a1.x, c[2 * k + 1][1] = a1.y, c[2 * k + 1][2] = a1.z, c[2 * k + 1][3] = a1.w;
             }
-            if constexpr (NCH == 6) {
+            }
+            if constexpr (NCH == 6 && !HH) {
                 const float2* v2 = reinterpret_cast<const float2*>(vol + 4 * vd.np);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -780,7 +797,7 @@ __device__ __noinline__ void finish_tile(const SplitArgs& A, int tile, int iu, i
     if (prev == (unsigned int)min(kGroupTiles, A.ntiles - group * kGroupTiles) - 1) finish_group<NCH>(A, group);
 }
 
-template <int NCH>
+template <int NCH, bool HH = false>
 __global__ void __launch_bounds__(kSplitThreads, NCH == 4 ? 4 : 2) k_project_split(SplitArgs A) {
     const RayGeom g = *A.rg;
     const int lane = threadIdx.x & 31;
@@ -845,7 +862,7 @@ __global__ void __launch_bounds__(kSplitThreads, NCH == 4 ? 4 : 2) k_project_spl
                     }
                 }
                 const unsigned int bias = cell_bias(A.vd);
-                CellCache<NCH> cache;
+                CellCache<NCH, HH> cache;
                 if (__all_sync(0xffffffffu, inside)) {
                     for (float sf = (float)s_a, se = (float)s_e; sf < se; sf += 1.0f) {
                         float qm[3];
@@ -1069,15 +1086,17 @@ int split_grid(int nch) {
     // per device and channel count; several host threads may ask at once (the
     // serving worker and callers), and any of them may fill an entry: they all
     // compute the same value
-    static std::atomic<int> cached[3][64] = {};
+    static std::atomic<int> cached[4][64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-    std::atomic<int>& c = cached[nch == 8 ? 2 : (nch == 6 ? 1 : 0)][dev];
+    std::atomic<int>& c = cached[nch == kFhHalf6 ? 3 : (nch == 8 ? 2 : (nch == 6 ? 1 : 0))][dev];
     int v = c.load(std::memory_order_relaxed);
     if (v == 0) {
         int sms = 0, per = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (nch == 8)
+        if (nch == kFhHalf6)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_project_split<6, true>, kSplitThreads, 0);
+        else if (nch == 8)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_project_split<8>, kSplitThreads, 0);
         else if (nch == 6)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_project_split<6>, kSplitThreads, 0);
@@ -1103,6 +1122,7 @@ cudaError_t launch_project(Launcher& L, const VolDev& vd, const float* vol_pad, 
         if (blocks <= 0) return cudaErrorInvalidDevice;
         const int need = (ntiles * kParts + kSplitThreads / 32 - 1) / (kSplitThreads / 32);
         const dim3 grid((unsigned)(need < blocks ? need : blocks));
+        if (nch == kFhHalf6) return L(k_project_split<6, true>, grid, dim3(kSplitThreads), 0, S);
         if (nch == 8) return L(k_project_split<8>, grid, dim3(kSplitThreads), 0, S);
         if (nch == 6) return L(k_project_split<6>, grid, dim3(kSplitThreads), 0, S);
         if (nch == 4) return L(k_project_split<4>, grid, dim3(kSplitThreads), 0, S);

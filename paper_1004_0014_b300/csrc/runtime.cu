@@ -389,8 +389,9 @@ size_t model_bytes(const pr_volume_desc& v, const pr_geometry& g, int K, int sto
     VolDev vd = make_vd(v);
     size_t n = (size_t)vd.n, np = (size_t)vd.np, R = (size_t)g.nu * g.nv;
     size_t ts = storage == PR_BF16 ? 2 : 4;
-    size_t nch = (size_t)fh_channels(K);
-    return np * ts + 3 * n * 4 + 3 * (size_t)K * n * ts + np * nch * 4 + np * 4 + R * 4 + R * K * 4 + R * 4 +
+    const int layout = fh_layout(K, storage);
+    size_t nch = (size_t)fh_logical(layout);
+    return np * ts + 3 * n * 4 + 3 * (size_t)K * n * ts + np * (size_t)fh_floats(layout) * 4 + np * 4 + R * 4 + R * K * 4 + R * 4 +
            R * 4 + n * 4 + partial_doubles(g, vd) * 8 + 64 + sizeof(SolveState) + 64 + 128 +
            sizeof(RayGeom) + 16 + (size_t)project_blocks(g.nu, g.nv) * sizeof(int) + sizeof(Support) +
            (size_t)split_tiles(g.nu, g.nv) * sizeof(int) + split_part_floats(g.nu, g.nv, (int)nch) * 4 +
@@ -1288,7 +1289,7 @@ int load_resident(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
     m->geom.ds = resolved_ds(*vol, *geom);
     m->K = K;
     m->storage = storage;
-    m->nch = fh_channels(K);
+    m->nch = fh_layout(K, storage);
     m->R = geom->nu * geom->nv;
     VolDev vd = make_vd(*vol);
     size_t n = (size_t)vd.n, np = (size_t)vd.np, R = (size_t)m->R;
@@ -1300,7 +1301,7 @@ int load_resident(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
     A(&m->f0p, np * ts);
     A(&m->mean, 3 * n * 4);
     A(&m->U, 3 * (size_t)K * n * ts);
-    A(&m->fh, np * m->nch * 4);
+    A(&m->fh, np * fh_floats(m->nch) * 4);
     A(&m->fpad, np * 4);
     A(&m->p, R * 4);
     A(&m->q, R * K * 4);
@@ -1318,7 +1319,7 @@ int load_resident(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
     A(&m->order, (size_t)project_blocks(geom->nu, geom->nv) * sizeof(int));
     A(&m->sup, sizeof(Support));
     A(&m->order_w, (size_t)split_tiles(geom->nu, geom->nv) * sizeof(int));
-    A(&m->ss.part, split_part_floats(geom->nu, geom->nv, m->nch) * 4);
+    A(&m->ss.part, split_part_floats(geom->nu, geom->nv, fh_logical(m->nch)) * 4);
     A(&m->ss.tile_mom, (size_t)split_tiles(geom->nu, geom->nv) * kProjMom * 8);
     A(&m->ss.group_mom, (size_t)split_groups(geom->nu, geom->nv) * kProjMom * 8);
     A(&m->ss.ctr, split_counters(geom->nu, geom->nv) * 4);
@@ -1347,7 +1348,7 @@ int load_resident(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
     std::vector<int> order_w_host((size_t)split_tiles(geom->nu, geom->nv));
     do {
         if ((e = cudaMemsetAsync(m->f0p, 0, np * ts, s))) break;
-        if ((e = cudaMemsetAsync(m->fh, 0, np * m->nch * 4, s))) break;
+        if ((e = cudaMemsetAsync(m->fh, 0, np * fh_floats(m->nch) * 4, s))) break;
         if ((e = cudaMemsetAsync(m->fpad, 0, np * 4, s))) break;
         if ((e = cudaMemsetAsync(m->partials, 0, partial_doubles(m->geom, m->md.vd) * 8, s))) break;
         if ((e = cudaMemsetAsync(m->counter, 0, 64, s))) break;
@@ -1946,7 +1947,7 @@ int pr_invert_dvf(pr_ctx* c, int id, const double* w, double tol, int max_iter, 
     CK(cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned int), c->stream));
     CK(launch_invert(L, m->md, m->wdev, reinterpret_cast<float4*>(m->fh), tol, max_iter, y_dev, stats));
     // the scratch field overwrote the solver volume's zero border
-    CK(cudaMemsetAsync(m->fh, 0, (size_t)m->md.vd.np * m->nch * 4, c->stream));
+    CK(cudaMemsetAsync(m->fh, 0, (size_t)m->md.vd.np * fh_floats(m->nch) * 4, c->stream));
     unsigned int st[2] = {0, 0};
     CK(cudaMemcpyAsync(st, stats, sizeof st, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -2024,7 +2025,7 @@ int pr_time_kernel(pr_ctx* c, int id, int which, double angle, int iters, double
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (which == PR_KERNEL_INVERT && err == cudaSuccess)  // restore the zero border (the field was scratch)
-        err = cudaMemsetAsync(m->fh, 0, (size_t)m->md.vd.np * m->nch * 4, c->stream);
+        err = cudaMemsetAsync(m->fh, 0, (size_t)m->md.vd.np * fh_floats(m->nch) * 4, c->stream);
     if (ytmp || sst) {
         cudaError_t e2 = cudaStreamSynchronize(c->stream);
         if (ytmp) cudaFree(ytmp);

@@ -16,6 +16,10 @@
 // without reading any field: the result is the same volume, and the field
 // stream shrinks to the blocks that meet the box. The decision is one per
 // block, so the evaluating threads carry no extra state.
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
 #include "internal.h"
 
 namespace pr {
@@ -60,9 +64,21 @@ __device__ __forceinline__ bool range_in_box(const VolDev& vd, int vb, int ve, c
 }
 
 // Zeros for the voxels v0..v0+3 (those below n) in the padded output layout.
+// Whether the solver volume of this model type is the packed float32 f +
+// float16 h record (bfloat16 storage, K = 4 or 5; see fh_layout).
+template <int K, typename TS>
+__host__ __device__ constexpr bool half_h() {
+    return std::is_same<TS, __nv_bfloat16>::value && (K == 4 || K == 5);
+}
+
+__device__ __forceinline__ float pack_half2(float a, float b) {
+    const __half2 h = __floats2half2_rn(a, b);
+    return __uint_as_float(*reinterpret_cast<const unsigned int*>(&h));
+}
+
 template <int K, int MODE, typename TS>
 __device__ __forceinline__ void zero4(const WarpArgs<TS>& A, long long v0) {
-    constexpr int kNch = K <= 3 ? 4 : (K <= 5 ? 6 : 8);
+    constexpr int kNch = half_h<K, TS>() ? 4 : (K <= 3 ? 4 : (K <= 5 ? 6 : 8));
     const VolDev& vd = A.vd;
     const int jk = (int)v0 / vd.nx;
     int i = (int)v0 - jk * vd.nx, j = jk % vd.ny, kz = jk / vd.ny;
@@ -160,7 +176,11 @@ __device__ __forceinline__ void warp4(const WarpArgs<TS>& A, long long v0, const
                 h[k] = kH ? __fmaf_rn(gz, u[k][2][e], __fmaf_rn(gy, u[k][1][e], gx * u[k][0][e])) : 0.0f;
 
             const int pidx = ((kz + 1) * vd.nyp + (j + 1)) * vd.nxp + (i + 1);
-            if (MODE == kWarpFH) {
+            if (MODE == kWarpFH && half_h<K, TS>()) {
+                reinterpret_cast<float4*>(A.out_pad)[pidx] =
+                    make_float4(val, pack_half2(h[0], h[1 % K]), pack_half2(h[2 % K], h[3 % K]),
+                                pack_half2(K == 5 ? h[4 % K] : 0.0f, 0.0f));
+            } else if (MODE == kWarpFH) {
                 float o[kNch];
                 o[0] = val;
 #pragma unroll

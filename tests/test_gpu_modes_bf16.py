@@ -144,15 +144,21 @@ def test_k5_inverse_field(k5, name):
     assert err < 1e-3
 
 
-def test_k4_cost_gradient_and_solve(k5):
-    """K = 4 (the 6-channel solver volume with one unused channel): cost and
-    both gradient forms at a point, and a short solve, against the oracle."""
-    from paper_1004_0014_b300 import default_opts
+@pytest.mark.parametrize("name", ["f32", "bf16"])
+def test_k4_cost_gradient_and_solve(k5, name):
+    """K = 4 (the solver volume with one unused h channel: float32 channels,
+    or with bfloat16 storage the packed float32 f + float16 h record): cost and
+    both gradient forms at a point, and a short solve, against the oracle (on
+    the bfloat16-rounded inputs for bfloat16 storage)."""
+    from paper_1004_0014_b300 import PR_BF16, PR_F32, default_opts
 
     pca, ctx, vol, geom, th = k5["pca"], k5["ctx"], k5["vol"], k5["geom"], k5["th"]
     f0 = k5["models"]["f32"][1].f0.astype(np.float32)
     mean, U = pca.mean.astype(np.float32), pca.U[:4].astype(np.float32)
-    mid = ctx.load_model(vol, geom, f0, mean, U, k5["models"]["f32"][1].c0)
+    mid = ctx.load_model(vol, geom, f0, mean, U, k5["models"]["f32"][1].c0,
+                         storage=PR_BF16 if name == "bf16" else PR_F32)
+    if name == "bf16":
+        f0, U = _bf16(f0), _bf16(U)
     om = O.Model(vol, f0.astype(np.float64), mean.astype(np.float64), U.astype(np.float64),
                  k5["models"]["f32"][1].c0)
     try:
@@ -160,7 +166,7 @@ def test_k4_cost_gradient_and_solve(k5):
         go, Jo, _ = O.gradient(om, geom, th, w, 1.01, -0.002, k5["y"].astype(np.float64))
         for mode in (0, 1):
             J, g = ctx.cost_grad(mid, k5["yd"], th, w, 1.01, -0.002, mode)
-            report("k4_cost_grad", mode=mode, J_rel=abs(J - Jo) / Jo, g_rel=rel(g, go))
+            report("k4_cost_grad_" + name, mode=mode, J_rel=abs(J - Jo) / Jo, g_rel=rel(g, go))
             assert abs(J - Jo) / Jo < TOL_PROJ
             assert rel(g, go) < TOL_GRAD
         res = ctx.reconstruct(mid, k5["y"], th, default_opts(max_iters=8, cold_start=1))
@@ -169,7 +175,7 @@ def test_k4_cost_gradient_and_solve(k5):
             ctx.trial_log(mid),
             lambda rp: O.reconstruct(om, geom, th, k5["y"].astype(np.float64), np.zeros(4), so, replay=rp), so)
         eo = own_path_errors(res, own)
-        report("k4_solve", w_rel=rel(res["w"], ores.w), J_rel=abs(res["J"] - ores.J) / ores.J,
+        report("k4_solve_" + name, w_rel=rel(res["w"], ores.w), J_rel=abs(res["J"] - ores.J) / ores.J,
                backtracks=res["backtracks"], oracle_backtracks=ores.backtracks, ties=ties, **eo)
         assert eo["own_J_rel"] < TOL_PROJ
         assert res["iters"] == ores.iters
