@@ -462,7 +462,14 @@ def run_ours(args):
 
     # ---------------- end to end: host buffers through pr_reconstruct ----------------
     y_host = ys.cpu().pin_memory()
-    ctx.set_state(mid, w_start)
+    # the same W untimed warm-up frames, through the same call, right before
+    # the timed ones: the GPU has idled while y_host was staged, and the timed
+    # frames start from the state they start from in the device-resident leg
+    ctx.set_state(mid, np.zeros(w["K"]))
+    for i in range(W):
+        capi.pr_reconstruct(ctx._ctx, mid, y_host[i], angles[i], opts)
+    if not np.array_equal(ctx.get_state(mid), w_start):
+        raise RuntimeError("the end-to-end warm-up did not reach the device-resident leg's start state")
     torch.cuda.synchronize()
     barrier(dist)
     t0 = time.perf_counter()
@@ -475,7 +482,9 @@ def run_ours(args):
 
     # ---------------- plain FP32 path: host-driven loop ----------------
     plain_opts = default_opts(max_iters=w["max_iters"], loop_mode=PR_LOOP_HOST)
-    ctx.set_state(mid, w_start)
+    ctx.set_state(mid, np.zeros(w["K"]))
+    for i in range(W):  # the same untimed warm-up, through this path
+        capi.pr_reconstruct(ctx._ctx, mid, ys[i], angles[i], plain_opts)
     torch.cuda.synchronize()
     plain = []
     for i in range(W, W + K):
@@ -628,10 +637,12 @@ def run_ours(args):
     # ---------------- short served arm: 16 mixed patients, 8 Hz each, 5 s ----------------
     served = None
     if world == 1 and not args.no_extra_arms:
-        sm = serve_measure(16, 8.0, 5.0, "f32", local, ["batched:2:2", "slots:2"])
+        sm = serve_measure(16, 8.0, 5.0, "bf16", local, ["batched:2:2", "slots:2"])
         served = {"patients": 16, "rate_hz_each": 8.0, "seconds": 5.0, "frames": len(sm["trace"]),
-                  "results_identical_to_plain": bool(sm["same"]),
-                  "plain_fp32_one_at_a_time": sm["plain"]}
+                  "storage": "served: bfloat16 f0 and U (FP32 arithmetic, FP64 reductions); plain_fp32: float32",
+                  "results_identical_to_plain_bf16": bool(sm["same"]),
+                  "plain_fp32_one_at_a_time": sm["plain_fp32"],
+                  "plain_bf16_one_at_a_time": sm["plain"]}
         for md, r in zip(("batched_2lanes_2frames_per_tick", "slots_2"), sm["runs"]):
             served[md] = {"value": r["value"], "unit": UNIT, "p50_ms": float(np.percentile(r["lat"], 50)),
                           "p99_ms": float(np.percentile(r["lat"], 99)), "gpu_ms_mean": r["gpu_ms_mean"]}
@@ -845,25 +856,59 @@ def serve_once(ctx, mids, pats, ys, trace, opts, n_slots, local, lanes=0, tick_f
                 gpu_ms_mean=float(np.mean([done[n][1]["gpu_ms"] for n in range(len(trace))])))
 
 
+def _plain_path(ctx, mids, pats, ys, trace):
+    """The plain path on a serving trace: the host-driven loop, one frame at a
+    time in arrival order, every patient from w = 0. Latency comes from the
+    measured service times (start = max(arrival, previous finish)). Returns the
+    figures and each patient's final w."""
+    from paper_1004_0014_b300 import PR_LOOP_HOST, default_opts
+
+    plain_opts = default_opts(max_iters=10, loop_mode=PR_LOOP_HOST)
+    for pt, mid in zip(pats, mids):
+        ctx.set_state(mid, np.zeros(pt["K"]))
+    svc, final = [], {}
+    for (t, i, f, th) in trace:
+        t0 = time.perf_counter()
+        res = ctx.reconstruct(mids[i], ys[(i, f)], th, plain_opts)
+        svc.append(time.perf_counter() - t0)
+        final[i] = res["w"]
+    finish, lat = 0.0, []
+    for (t, i, f, th), s_i in zip(trace, svc):
+        finish = max(t, finish) + s_i
+        lat.append(1000.0 * (finish - t))
+    figures = dict(value=len(trace) / (finish - trace[0][0]), p50_ms=float(np.percentile(lat, 50)),
+                   p99_ms=float(np.percentile(lat, 99)), mean_service_ms=1000.0 * float(np.mean(svc)))
+    return figures, final
+
+
+def _load_patients(ctx, bases, pats, geom, storage):
+    from paper_1004_0014_b300 import PR_BF16, PR_F32
+
+    mids = []
+    for pt in pats:
+        b = bases[pt["key"]]
+        mids.append(ctx.load_model(b["vol"], geom, b["f0"], pt["alpha"] * b["mean"], b["U"][:pt["K"]], b["c0"],
+                                   storage=PR_BF16 if storage == "bf16" else PR_F32))
+    return mids
+
+
 def serve_measure(patients: int, rate: float, seconds: float, storage: str, local: int, modes, workers: int = 8):
     """Serve a Poisson trace of `patients` mixed patients at `rate` Hz each for
     `seconds` once per mode in `modes` ("batched:L:F" = tick-batched with L
     lanes and at most F frames per tick (0 or absent = all), "slots:S" = S solve
-    streams), then the plain FP32 path (host-driven loop,
-    one frame at a time in arrival order) on the same trace. Returns the runs
-    and the plain path's figures."""
-    from paper_1004_0014_b300 import PR_BF16, PR_F32, PR_LOOP_HOST, Context, default_opts
+    streams), then the plain path (host-driven loop, one frame at a time in
+    arrival order) on the same trace with the same models, whose final w the
+    served ones must equal bitwise. With bfloat16 storage the plain path also
+    runs on float32-storage models of the same patients (`plain_fp32`).
+    Returns the runs and the plain paths' figures."""
+    from paper_1004_0014_b300 import Context, default_opts
 
     bases, pats = serve_patients(patients, workers)
     geom = pats[0]["wl"]["geom"]
     trace = serve_trace(patients, rate, seconds)
     ctx = Context(local)
     ys = serve_targets(ctx, bases, pats, trace, geom)
-    mids = []
-    for pt in pats:
-        b = bases[pt["key"]]
-        mids.append(ctx.load_model(b["vol"], geom, b["f0"], pt["alpha"] * b["mean"], b["U"][:pt["K"]], b["c0"],
-                                   storage=PR_BF16 if storage == "bf16" else PR_F32))
+    mids = _load_patients(ctx, bases, pats, geom, storage)
     opts = default_opts(max_iters=10)
     # warm-up: two frames per patient, then every patient restarts from w = 0
     ctx.serve_start(slots=4)
@@ -878,24 +923,16 @@ def serve_measure(patients: int, rate: float, seconds: float, storage: str, loca
         kind, n, *rest = mode.split(":")
         runs.append(serve_once(ctx, mids, pats, ys, trace, opts, int(n) if kind == "slots" else 4, local,
                                lanes=int(n) if kind == "batched" else 0, tick_frames=int(rest[0]) if rest else 0))
-    plain_opts = default_opts(max_iters=10, loop_mode=PR_LOOP_HOST)
-    for pt, mid in zip(pats, mids):
-        ctx.set_state(mid, np.zeros(pt["K"]))
-    svc, final_plain = [], {}
-    for (t, i, f, th) in trace:
-        t0 = time.perf_counter()
-        res = ctx.reconstruct(mids[i], ys[(i, f)], th, plain_opts)
-        svc.append(time.perf_counter() - t0)
-        final_plain[i] = res["w"]
-    finish, plain_lat = 0.0, []
-    for (t, i, f, th), s_i in zip(trace, svc):
-        finish = max(t, finish) + s_i
-        plain_lat.append(1000.0 * (finish - t))
-    plain = dict(value=len(trace) / (finish - trace[0][0]), p50_ms=float(np.percentile(plain_lat, 50)),
-                 p99_ms=float(np.percentile(plain_lat, 99)), mean_service_ms=1000.0 * float(np.mean(svc)))
+    plain, final_plain = _plain_path(ctx, mids, pats, ys, trace)
     same = all(np.array_equal(np.asarray(r["final"][i]), np.asarray(final_plain[i])) for r in runs for i in r["final"])
+    plain_fp32 = plain
+    if storage != "f32":
+        for mid in mids:
+            ctx.release_model(mid)
+        mids32 = _load_patients(ctx, bases, pats, geom, "f32")
+        plain_fp32, _ = _plain_path(ctx, mids32, pats, ys, trace)
     ctx.close()
-    return dict(runs=runs, plain=plain, same=same, trace=trace, pats=pats)
+    return dict(runs=runs, plain=plain, plain_fp32=plain_fp32, same=same, trace=trace, pats=pats)
 
 
 def run_serve(args):
@@ -932,11 +969,11 @@ def run_serve(args):
                                "max": float(late.max())},
         "capacity_note": "throughput is capped by the GPU's solve rate when the offered load exceeds it; "
                          "latency then grows with the length of the trace",
-        "plain_fp32": dict(plain, path="host-driven loop (PR_LOOP_HOST), one frame at a time in arrival order; "
-                                       "latency from the measured service times with start = max(arrival, previous "
-                                       "finish)", storage="%s, as the served arm (FP32 arithmetic throughout)"
-                                                          % args.storage),
-        "results_identical_to_plain": bool(m["same"]),
+        "plain_fp32": dict(m["plain_fp32"], path="host-driven loop (PR_LOOP_HOST), one frame at a time in arrival "
+                                                 "order; latency from the measured service times with start = "
+                                                 "max(arrival, previous finish)", storage="float32"),
+        "plain_same_storage": dict(plain, storage="%s, as the served arm" % args.storage),
+        "results_identical_to_plain_same_storage": bool(m["same"]),
         "gpu_ms_mean": head["gpu_ms_mean"],
         "clocks": head["clocks"],
     }

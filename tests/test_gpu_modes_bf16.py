@@ -183,3 +183,48 @@ def test_k4_cost_gradient_and_solve(k5, name):
         assert rel(res["w"], ores.w) < TOL_W
     finally:
         ctx.release_model(mid)
+
+
+@pytest.mark.parametrize("K", [3, 2, 1])
+def test_k_le_3_bf16_cost_gradient_and_solve(k5, K):
+    """bfloat16 storage with K <= 3 (f0 and U in bfloat16, the solver volume's
+    (f, h_1..h_3) in float32 with the unused channels zero). Cost, projection
+    and both gradient forms at a point, and a short solve, against the oracle
+    on the bfloat16-rounded inputs. (A float16 (f, h) record of 8 bytes was
+    measured here at 2e-4 relative J error: f needs more than float16's 11
+    bits, because the residual is a small fraction of P f.)"""
+    from paper_1004_0014_b300 import PR_BF16, default_opts
+
+    pca, ctx, vol, geom, th = k5["pca"], k5["ctx"], k5["vol"], k5["geom"], k5["th"]
+    c0 = k5["models"]["f32"][1].c0
+    f0 = k5["models"]["f32"][1].f0.astype(np.float32)
+    mean, U = pca.mean.astype(np.float32), pca.U[:K].astype(np.float32)
+    mid = ctx.load_model(vol, geom, f0, mean, U, c0, storage=PR_BF16)
+    om = O.Model(vol, _bf16(f0).astype(np.float64), mean.astype(np.float64), _bf16(U).astype(np.float64), c0)
+    try:
+        w = np.array([0.5, -0.2, 0.1][:K])
+        go, Jo, _ = O.gradient(om, geom, th, w, 1.01, -0.002, k5["y"].astype(np.float64))
+        for mode in (0, 1):
+            J, g, p = ctx.cost_grad(mid, k5["yd"], th, w, 1.01, -0.002, mode, return_p=True)
+            po = O.project(vol, geom, th, O.warp(vol, om.f0, O.dvf(vol, om.mean, om.U, w)))
+            report("k%d_bf16_cost_grad" % K, mode=mode, p_rel=rel(p.cpu().numpy(), po), J_rel=abs(J - Jo) / Jo,
+                   g_rel=rel(g, go))
+            assert rel(p.cpu().numpy(), po) < TOL_PROJ
+            assert abs(J - Jo) / Jo < TOL_PROJ
+            assert rel(g, go) < TOL_GRAD
+        res = ctx.reconstruct(mid, k5["y"], th, default_opts(max_iters=8, cold_start=1))
+        so = library_opts(max_iters=8)
+        ores, ties, own = checked_oracle_solve(
+            ctx.trial_log(mid),
+            lambda rp: O.reconstruct(om, geom, th, k5["y"].astype(np.float64), np.zeros(K), so, replay=rp), so)
+        eo = own_path_errors(res, own)
+        et = float(np.max(np.abs(res["tumor"] - ores.tumor)))
+        report("k%d_bf16_solve" % K, w_rel=rel(res["w"], ores.w), J_rel=abs(res["J"] - ores.J) / ores.J,
+               tumor_mm=et, ties=ties, **eo)
+        assert eo["own_J_rel"] < TOL_PROJ
+        assert res["iters"] == ores.iters
+        assert abs(res["J"] - ores.J) / ores.J < TOL_PROJ
+        assert rel(res["w"], ores.w) < TOL_W
+        assert et < TOL_TUMOR_MM
+    finally:
+        ctx.release_model(mid)

@@ -60,18 +60,23 @@ def _same(a, b, key):
         assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), (key, k)
 
 
+@pytest.mark.parametrize("storage", ["f32", "bf16", "mixed"])
 @pytest.mark.parametrize("mode", ["slots", "batched"])
-def test_served_results_equal_solo_results(patients, mode):
-    from paper_1004_0014_b300 import Context
+def test_served_results_equal_solo_results(patients, mode, storage):
+    """storage: every model in float32 or bfloat16, or "mixed" (the middle
+    patient in float32, the others in bfloat16)."""
+    from paper_1004_0014_b300 import PR_BF16, PR_F32, Context
+
+    def st(i):
+        if storage == "mixed":
+            return PR_F32 if i == 1 else PR_BF16
+        return PR_BF16 if storage == "bf16" else PR_F32
 
     ctx = Context(0)
     try:
-        mids = [ctx.load_model(p["vol"], GEOM, p["f0"], p["mean"], p["U"], p["c0"]) for p in patients]
-        solo = {}
-        for i, (mid, p) in enumerate(zip(mids, patients)):
-            ctx.set_state(mid, np.zeros(3))
-            for j, (th, y) in enumerate(p["frames"]):
-                solo[(i, j)] = ctx.reconstruct(mid, y, th, _opts())
+        mids = [ctx.load_model(p["vol"], GEOM, p["f0"], p["mean"], p["U"], p["c0"], storage=st(i))
+                for i, p in enumerate(patients)]
+        solo = _solo(ctx, mids, patients)
         for mid in mids:
             ctx.set_state(mid, np.zeros(3))
         if mode == "slots":
