@@ -458,6 +458,11 @@ struct Launcher {
     cudaGraphNode_t last{};
     bool has_last = false;
     int count = 0;  // kernels launched or recorded
+    // Graph mode: the next kernel node depends on `last` through a
+    // programmatic edge from its launch-completion port (it may start once
+    // every block of `last` has started; it must execute griddepcontrol.wait
+    // before it reads what `last` writes). Cleared by that node.
+    bool programmatic_next = false;
 
     template <typename... KArgs, typename... Args>
     cudaError_t operator()(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
@@ -487,7 +492,23 @@ struct Launcher {
         p.kernelParams = ptrs;
         p.extra = nullptr;
         cudaGraphNode_t n;
-        cudaError_t e = cudaGraphAddKernelNode(&n, graph, has_last ? &last : nullptr, has_last ? 1 : 0, &p);
+        cudaError_t e;
+        if (programmatic_next && has_last) {
+            cudaGraphNodeParams np = {};
+            np.type = cudaGraphNodeTypeKernel;
+            np.kernel.func = p.func;
+            np.kernel.gridDim = grid;
+            np.kernel.blockDim = block;
+            np.kernel.sharedMemBytes = (unsigned)smem;
+            np.kernel.kernelParams = ptrs;
+            cudaGraphEdgeData ed = {};
+            ed.from_port = cudaGraphKernelNodePortLaunchCompletion;
+            ed.type = cudaGraphDependencyTypeProgrammatic;
+            e = cudaGraphAddNode(&n, graph, &last, &ed, 1, &np);
+        } else {
+            e = cudaGraphAddKernelNode(&n, graph, has_last ? &last : nullptr, has_last ? 1 : 0, &p);
+        }
+        programmatic_next = false;
         if (e == cudaSuccess) {
             last = n;
             has_last = true;

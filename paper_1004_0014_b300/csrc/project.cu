@@ -808,6 +808,7 @@ __global__ void __launch_bounds__(kSplitThreads, NCH == 4 ? 4 : 2) k_project_spl
     bool nonzero = true;
     float margin = 0.0f;
     if (A.sup.sup && A.sup.w) nonzero = support_box(*A.sup.sup, A.vd, A.sup.w, A.sup.K, lo, hi, &margin);
+    bool volume_ready = false;
 
     for (;;) {
         unsigned int item = 0;
@@ -841,6 +842,16 @@ __global__ void __launch_bounds__(kSplitThreads, NCH == 4 ? 4 : 2) k_project_spl
 #pragma unroll
         for (int c = 0; c < NCH; ++c) acc[c] = 0.0f;
         float comp = 0.0f;
+        if (!volume_ready) {
+            // Launched behind the warp kernel with a programmatic edge, this
+            // grid may start while the warp's last blocks still write the
+            // volume: the ray set-up above reads only w, the geometry and
+            // the support, and the samples wait here for the warp grid to
+            // complete with its writes visible (a no-op after an ordinary
+            // dependency).
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+            volume_ready = true;
+        }
         if (s_hi >= s_lo) {
             const int Ls = s_hi - s_lo + 1;
             const int s_a = s_lo + (Ls * part) / kParts, s_e = s_lo + (Ls * (part + 1)) / kParts;

@@ -455,6 +455,7 @@ int build_graph(pr_ctx* c, Model* m) {
     SolveState* st = m->st;
     CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
     CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup, st->fh_box));
+    L.programmatic_next = true;  // the projector waits for the warp before sampling
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseInit, m->hloop, 1, sref(m, st->wt), &m->ss));
     cudaGraphNodeParams cp = {};
@@ -467,6 +468,7 @@ int build_graph(pr_ctx* c, Model* m) {
     Launcher B;
     B.graph = cp.conditional.phGraph_out[0];
     CK(launch_warp(B, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup, st->fh_box));
+    B.programmatic_next = true;  // the projector waits for the warp before sampling
     CK(launch_project(B, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseTrial, m->hloop, 1, sref(m, st->wt), &m->ss));
     L.last = cond;
@@ -677,6 +679,7 @@ int add_solve_nodes(cudaGraph_t g, Model* m, const cudaGraphNode_t* dep, const f
     L.has_last = true;
     CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
     CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup, st->fh_box));
+    L.programmatic_next = true;  // the projector waits for the warp before sampling
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseInit, h, 1, sref(m, st->wt), &m->ss));
     cudaGraphNodeParams cp = {};
@@ -689,6 +692,7 @@ int add_solve_nodes(cudaGraph_t g, Model* m, const cudaGraphNode_t* dep, const f
     Launcher B;
     B.graph = cp.conditional.phGraph_out[0];
     CK(launch_warp(B, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup, st->fh_box));
+    B.programmatic_next = true;  // the projector waits for the warp before sampling
     CK(launch_project(B, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseTrial, h, 1, sref(m, st->wt), &m->ss));
     L.last = cond;
@@ -780,6 +784,7 @@ int add_tick_branch(cudaGraph_t body, Model* m, const float* y_src, const SolveP
     CK(cudaGraphConditionalHandleCreate(&h, body, 1, cudaGraphCondAssignDefault));
     CK(launch_begin(L, m->y, m->R, st, m->partials, m->counter));
     CK(launch_warp(L, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup, st->fh_box));
+    L.programmatic_next = true;  // the projector waits for the warp before sampling
     CK(launch_project(L, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseInit, h, 1, sref(m, st->wt), &m->ss));
     cudaGraphNodeParams cp = {};
@@ -792,6 +797,7 @@ int add_tick_branch(cudaGraph_t body, Model* m, const float* y_src, const SolveP
     Launcher B;
     B.graph = cp.conditional.phGraph_out[0];
     CK(launch_warp(B, m->md, st->wt, kWarpFH, m->fh, nullptr, nullptr, m->sup, st->fh_box));
+    B.programmatic_next = true;  // the projector waits for the warp before sampling
     CK(launch_project(B, m->md.vd, m->fh, m->nch, m->K, &st->prm.rg, m->order, m->geom.nu, m->geom.nv, m->p, m->q, m->y, st,
                       m->partials, m->counter, kPhaseTrial, h, 1, sref(m, st->wt), &m->ss));
     L.last = cond;
