@@ -150,7 +150,7 @@ struct SolveState {
     double mu_next;  // first trial step of the next iteration or warm-started solve (0 = none)
     double w_prev[8];  // final w of the solve before the last one (for the predictor)
     int history;       // warm-started solves in a row with a known final w (0, 1, >= 2)
-    // Voxel box (lo x, y, z, hi x, y, z) that every 1024-voxel block of the
+    // Voxel box (lo x, y, z, hi x, y, z) that every 512-voxel chunk of the
     // model's (f, h) volume holding a nonzero meets; all zeros (a one-voxel
     // box) is valid for the all-zero volume of a freshly loaded model. Written
     // by the controller after each solver pass, read by the next warp pass.

@@ -44,8 +44,8 @@ inline int fh_logical(int layout) { return layout == kFhHalf6 ? 6 : layout; }  /
 // w_dev: K doubles in device memory. sup (device, nullable; padded modes
 // only): the model's support record; voxels outside the support box at w_dev
 // are exact zeros and are written as zeros without reading their fields.
-// dirty (device, 6 ints, nullable; with sup): a box that every 1024-voxel
-// block of out_pad holding a nonzero meets; blocks that miss both it and the
+// dirty (device, 6 ints, nullable; with sup): a box that every 512-voxel
+// chunk of out_pad holding a nonzero meets; chunks that miss both it and the
 // support box are not written. The caller keeps it valid after the pass (the
 // solve's controller records the pass's box; other callers use
 // launch_warp_box).

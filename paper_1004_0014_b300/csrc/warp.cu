@@ -1,8 +1,8 @@
 // G1: fused DVF synthesis and trilinear warp (Eq. 1, Section 2.2).
 //
-// One thread handles four consecutive voxels of the flat grid. It reads the
-// mean DVF (3 planes) and the K eigenvector fields (3K planes) with 16-byte
-// vector loads (8-byte for bfloat16 storage), forms x = mean + sum_k u_k w_k,
+// One thread handles two consecutive voxels of the flat grid. It reads the
+// mean DVF (3 planes) and the K eigenvector fields (3K planes) with 8-byte
+// vector loads (4-byte for bfloat16 storage), forms x = mean + sum_k u_k w_k,
 // pulls back to q = v + x / spacing, and evaluates the zero-padded trilinear
 // interpolant of f0 at q from the padded reference volume. On gradient points
 // it also forms the exact derivative of the interpolant and h_k = (df/dx) . u_k
@@ -10,22 +10,45 @@
 // 12 + 12K bytes of field reads per voxel (float32) against 4 bytes of f
 // (+4K of h) written; the f0 taps hit L1/L2.
 //
-// For the padded outputs that only the projector reads, a block whose 1024
-// voxels all lie outside the support box of the warped volume at w (the
-// displacement bound around the nonzero voxels of f0) writes their zeros
-// without reading any field: the result is the same volume, and the field
-// stream shrinks to the blocks that meet the box. The decision is one per
-// block, so the evaluating threads carry no extra state.
+// For the padded outputs that only the projector reads, a chunk of 512
+// voxels that all lie outside the support box of the warped volume at w (the
+// displacement bound around the nonzero voxels of f0) gets its zeros written
+// without any field read: the result is the same volume, and the field stream
+// shrinks to the chunks that meet the box. Those modes run resident blocks
+// that take the decisions for all their chunks at once, then stream.
+//
+// Two voxels per thread (not four) keep the registers at 51 for K <= 3, so
+// five 256-thread blocks share an SM: the f0 taps wait on the pull-back point,
+// and more resident warps hide that wait (measured 78 -> 64 us per paper-scale
+// pass, K = 3).
 #include <cuda_fp16.h>
 
 #include <type_traits>
 
 #include "internal.h"
 
+#include <algorithm>
+#include <atomic>
+
 namespace pr {
 namespace {
 
 constexpr int kWarpThreads = 256;
+constexpr int kWarpVox = 2;  // voxels per thread
+
+__device__ __forceinline__ void ld2(const float* p, float (&v)[2]) {
+    float2 t = __ldg(reinterpret_cast<const float2*>(p));
+    v[0] = t.x;
+    v[1] = t.y;
+}
+__device__ __forceinline__ void ld2(const __nv_bfloat16* p, float (&v)[2]) {
+    unsigned int t = __ldg(reinterpret_cast<const unsigned int*>(p));
+    float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&t));
+    v[0] = a.x;
+    v[1] = a.y;
+}
+constexpr int kWarpChunk = kWarpVox * kWarpThreads;  // voxels per block and step
+constexpr int kWarpMaxChunks = 128;                 // chunks per block (support-restricted modes)
 
 template <typename TS>
 struct WarpArgs {
@@ -39,7 +62,7 @@ struct WarpArgs {
     float* h_flat;
     const Support* sup;  // padded modes: skip the field reads outside the support box (nullable)
     const int* dirty;    // with sup: box of the blocks that may still hold nonzeros (nullable, see k_warp)
-    int vec_ok;      // N % 4 == 0: planes are 16-byte aligned for vector loads
+    int vec_ok;      // N % 2 == 0: planes are aligned for the two-voxel vector loads
 };
 
 // Whether any voxel of the flat range [vb, ve] lies in the inclusive box
@@ -63,7 +86,6 @@ __device__ __forceinline__ bool range_in_box(const VolDev& vd, int vb, int ve, c
     return false;
 }
 
-// Zeros for the voxels v0..v0+3 (those below n) in the padded output layout.
 // Whether the solver volume of this model type is the packed float32 f +
 // float16 h record (bfloat16 storage, K = 4 or 5; see fh_layout).
 template <int K, typename TS>
@@ -76,14 +98,15 @@ __device__ __forceinline__ float pack_half2(float a, float b) {
     return __uint_as_float(*reinterpret_cast<const unsigned int*>(&h));
 }
 
+// Zeros for the voxels v0, v0 + 1 (those below n) in the padded output layout.
 template <int K, int MODE, typename TS>
-__device__ __forceinline__ void zero4(const WarpArgs<TS>& A, long long v0) {
+__device__ __forceinline__ void zero_pair(const WarpArgs<TS>& A, long long v0) {
     constexpr int kNch = half_h<K, TS>() ? 4 : (K <= 3 ? 4 : (K <= 5 ? 6 : 8));
     const VolDev& vd = A.vd;
     const int jk = (int)v0 / vd.nx;
     int i = (int)v0 - jk * vd.nx, j = jk % vd.ny, kz = jk / vd.ny;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < 2; ++e) {
         if (v0 + e < vd.n) {
             const int pidx = ((kz + 1) * vd.nyp + (j + 1)) * vd.nxp + (i + 1);
             if (MODE == kWarpFH) {
@@ -111,11 +134,11 @@ __device__ __forceinline__ void zero4(const WarpArgs<TS>& A, long long v0) {
 
 __device__ __forceinline__ float lerp(float a, float b, float t) { return __fmaf_rn(t, b - a, a); }
 
-// DVF synthesis, pull-back warp and (kH) h_k for the four consecutive voxels
-// v0..v0+3 whose mean (mx) and eigenvector (u) values are already in registers.
+// DVF synthesis, pull-back warp and (kH) h_k for the two consecutive voxels
+// v0, v0 + 1 whose mean (mx) and eigenvector (u) values are already in registers.
 template <int K, int MODE, typename TS>
-__device__ __forceinline__ void warp4(const WarpArgs<TS>& A, long long v0, const float (&w)[K],
-                                      const float (&mx)[3][4], const float (&u)[K][3][4]) {
+__device__ __forceinline__ void warp_pair(const WarpArgs<TS>& A, long long v0, const float (&w)[K],
+                                      const float (&mx)[3][2], const float (&u)[K][3][2]) {
     constexpr bool kH = (MODE == kWarpFH || MODE == kWarpFlatFH);
     constexpr int kNch = K <= 3 ? 4 : (K <= 5 ? 6 : 8);
     const VolDev& vd = A.vd;
@@ -128,7 +151,7 @@ __device__ __forceinline__ void warp4(const WarpArgs<TS>& A, long long v0, const
     const int plane = vd.nxp * vd.nyp;
 
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < 2; ++e) {
         if (v0 + e < n) {
             float d0 = mx[0][e], d1 = mx[1][e], d2 = mx[2][e];
 #pragma unroll
@@ -214,56 +237,36 @@ __device__ __forceinline__ void warp4(const WarpArgs<TS>& A, long long v0, const
     }
 }
 
+// Resident 256-thread blocks per SM the register cap aims at: five for K <= 3
+// (four for bfloat16, whose conversions would spill at five), fewer for the
+// larger per-thread field sets.
+template <int K, typename TS>
+constexpr int warp_min_blocks() {
+    return K <= 3 ? (std::is_same<TS, float>::value ? 5 : 4) : (K <= 5 ? 3 : 2);
+}
+
+// Fields of the two voxels v0, v0 + 1 (v0 < n), then the warp and h (warp_pair).
 template <int K, int MODE, typename TS>
-__global__ void __launch_bounds__(kWarpThreads) k_warp(WarpArgs<TS> A) {
-    const VolDev& vd = A.vd;
-    long long v0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * 4;
-    const long long n = vd.n;
-
-    if ((MODE == kWarpFH || MODE == kWarpFPad) && A.sup) {
-        // One decision per block: a block that meets the support box at w is
-        // evaluated; one that does not writes zeros and reads no field, unless
-        // it also misses the dirty box (A.dirty: every block that may still
-        // hold a nonzero from an earlier pass meets it), so that it holds
-        // zeros already and is left alone.
-        __shared__ int action;  // 0: already zero, 1: write zeros, 2: evaluate
-        if (threadIdx.x == 0) {
-            int old[6];
-            if (A.dirty)
-                for (int c = 0; c < 6; ++c) old[c] = __ldcg(A.dirty + c);
-            int lo[3], hi[3];
-            warp_box(A.sup, vd, A.w, K, lo, hi);
-            const int box[6] = {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]};
-            const int vb = (int)(blockIdx.x * (long long)blockDim.x * 4);
-            const int ve = (int)(min((long long)vb + 4LL * blockDim.x, n) - 1);
-            action = range_in_box(vd, vb, ve, box) ? 2 : (!A.dirty || range_in_box(vd, vb, ve, old) ? 1 : 0);
-        }
-        __syncthreads();
-        if (action != 2) {
-            if (action == 1 && v0 < n) zero4<K, MODE, TS>(A, v0);
-            return;
-        }
-    }
-    if (v0 >= n) return;
-
+__device__ __forceinline__ void eval_pair(const WarpArgs<TS>& A, long long v0) {
+    const long long n = A.vd.n;
     float w[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) w[k] = (float)A.w[k];
 
-    // Fields of the four voxels: mean (3) and eigenvectors (3K).
-    float mx[3][4];
-    float u[K][3][4];
-    const bool full = A.vec_ok && (v0 + 3 < n);
+    // Fields of the two voxels: mean (3) and eigenvectors (3K).
+    float mx[3][2];
+    float u[K][3][2];
+    const bool full = A.vec_ok && (v0 + 1 < n);
     if (full) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) ld4(A.mean + c * n + v0, mx[c]);
+        for (int c = 0; c < 3; ++c) ld2(A.mean + c * n + v0, mx[c]);
 #pragma unroll
         for (int k = 0; k < K; ++k)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) ld4(A.U + (3LL * k + c) * n + v0, u[k][c]);
+            for (int c = 0; c < 3; ++c) ld2(A.U + (3LL * k + c) * n + v0, u[k][c]);
     } else {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int e = 0; e < 2; ++e) {
             long long v = v0 + e < n ? v0 + e : n - 1;
 #pragma unroll
             for (int c = 0; c < 3; ++c) mx[c][e] = __ldg(A.mean + c * n + v);
@@ -273,8 +276,53 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp(WarpArgs<TS> A) {
                 for (int c = 0; c < 3; ++c) u[k][c][e] = ld_val(A.U + (3LL * k + c) * n + v);
         }
     }
+    warp_pair<K, MODE, TS>(A, v0, w, mx, u);
+}
 
-    warp4<K, MODE, TS>(A, v0, w, mx, u);
+template <int K, int MODE, typename TS>
+__global__ void __launch_bounds__(kWarpThreads, warp_min_blocks<K, TS>()) k_warp(WarpArgs<TS> A) {
+    const VolDev& vd = A.vd;
+    const long long n = vd.n;
+
+    if ((MODE == kWarpFH || MODE == kWarpFPad) && A.sup) {
+        // Resident blocks: block b takes the 512-voxel chunks b, b + G, ...
+        // (G blocks). A chunk that meets the support box at w is evaluated; one
+        // that does not writes zeros and reads no field, unless it also misses
+        // the dirty box (A.dirty: every chunk that may still hold a nonzero
+        // from an earlier pass meets it), so that it holds zeros already and
+        // is left alone. The decisions of all of a block's chunks are taken
+        // at its start, one thread per chunk, so a block waits for them once.
+        __shared__ unsigned char action[kWarpMaxChunks];  // 0: already zero, 1: write zeros, 2: evaluate
+        const long long nchunks = (n + kWarpChunk - 1) / kWarpChunk;
+        const int mine = (int)((nchunks - blockIdx.x + gridDim.x - 1) / gridDim.x);
+        if ((int)threadIdx.x < mine) {
+            const long long chunk = blockIdx.x + (long long)threadIdx.x * gridDim.x;
+            int old[6];
+            if (A.dirty)
+                for (int c = 0; c < 6; ++c) old[c] = __ldcg(A.dirty + c);
+            int lo[3], hi[3];
+            warp_box(A.sup, vd, A.w, K, lo, hi);
+            const int box[6] = {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]};
+            const int vb = (int)(chunk * kWarpChunk);
+            const int ve = (int)(min((long long)vb + kWarpChunk, n) - 1);
+            action[threadIdx.x] =
+                range_in_box(vd, vb, ve, box) ? 2 : (!A.dirty || range_in_box(vd, vb, ve, old) ? 1 : 0);
+        }
+        __syncthreads();
+        for (int i = 0; i < mine; ++i) {
+            const long long v0 = (blockIdx.x + (long long)i * gridDim.x) * kWarpChunk + threadIdx.x * kWarpVox;
+            const int act = action[i];
+            if (v0 >= n || act == 0) continue;
+            if (act == 2)
+                eval_pair<K, MODE, TS>(A, v0);
+            else
+                zero_pair<K, MODE, TS>(A, v0);
+        }
+        return;
+    }
+    const long long v0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * kWarpVox;
+    if (v0 >= n) return;
+    eval_pair<K, MODE, TS>(A, v0);
 }
 
 __global__ void k_warp_box(VolDev vd, const double* __restrict__ w, int K, const Support* __restrict__ sup, int grow,
@@ -282,6 +330,24 @@ __global__ void k_warp_box(VolDev vd, const double* __restrict__ w, int K, const
     int lo[3], hi[3];
     warp_box(sup, vd, w, K, lo, hi, grow);
     for (int c = 0; c < 3; ++c) box[c] = lo[c], box[3 + c] = hi[c];
+}
+
+// Blocks of k_warp<K, MODE, TS> resident on the current device at once
+// (computed once per device; concurrent callers compute the same value).
+template <int K, int MODE, typename TS>
+int resident_blocks() {
+    static std::atomic<int> cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    int v = cached[dev].load(std::memory_order_relaxed);
+    if (v == 0) {
+        int sms = 0, per = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_warp<K, MODE, TS>, kWarpThreads, 0);
+        v = sms * (per > 0 ? per : 1);
+        cached[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
 }
 
 template <int K, typename TS>
@@ -298,9 +364,16 @@ cudaError_t dispatch_mode(Launcher& L, const ModelDev& m, const double* w, int m
     A.h_flat = h_flat;
     A.sup = (mode == kWarpFH || mode == kWarpFPad) ? sup : nullptr;
     A.dirty = A.sup ? dirty : nullptr;
-    A.vec_ok = (m.vd.n % 4 == 0) ? 1 : 0;
-    long long threads = (m.vd.n + 3) / 4;
+    A.vec_ok = (m.vd.n % kWarpVox == 0) ? 1 : 0;
+    long long threads = (m.vd.n + kWarpVox - 1) / kWarpVox;
     dim3 grid((unsigned)((threads + kWarpThreads - 1) / kWarpThreads));
+    if (A.sup) {  // resident blocks over the chunks (at most kWarpMaxChunks each)
+        const long long nchunks = (m.vd.n + kWarpChunk - 1) / kWarpChunk;
+        long long g = mode == kWarpFH ? resident_blocks<K, kWarpFH, TS>() : resident_blocks<K, kWarpFPad, TS>();
+        if (g <= 0) return cudaErrorInvalidDevice;
+        g = std::max(g, (nchunks + kWarpMaxChunks - 1) / kWarpMaxChunks);
+        grid = dim3((unsigned)std::min(g, nchunks));
+    }
     switch (mode) {
         case kWarpFH: return L(k_warp<K, kWarpFH, TS>, grid, dim3(kWarpThreads), 0, A);
         case kWarpFPad: return L(k_warp<K, kWarpFPad, TS>, grid, dim3(kWarpThreads), 0, A);
