@@ -17,25 +17,28 @@
 // shrinks to the chunks that meet the box. Those modes run resident blocks
 // that take the decisions for all their chunks at once, then stream.
 //
-// Two voxels per thread (not four) keep the registers at 51 for K <= 3, so
-// five 256-thread blocks share an SM: the f0 taps wait on the pull-back point,
-// and more resident warps hide that wait (measured 78 -> 64 us per paper-scale
-// pass, K = 3).
+// Two voxels per thread (not four) keep the registers at 48-51 for K <= 3,
+// so five 256-thread blocks share an SM: the f0 taps wait on the pull-back
+// point, and more resident warps hide that wait (measured 78 -> 64 us per
+// paper-scale pass, K = 3).
 #include <cuda_fp16.h>
-
-#include <type_traits>
-
-#include "internal.h"
 
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
+
+#include "internal.h"
 
 namespace pr {
 namespace {
 
 constexpr int kWarpThreads = 256;
-constexpr int kWarpVox = 2;  // voxels per thread
+constexpr int kWarpVox = 2;                          // voxels per thread
+constexpr int kWarpChunk = kWarpVox * kWarpThreads;  // voxels per block and step
+constexpr int kWarpMaxChunks = 128;                  // chunks per block (support-restricted modes)
 
+// The two consecutive values at p (8-byte aligned float32, 4-byte aligned
+// bfloat16), as floats.
 __device__ __forceinline__ void ld2(const float* p, float (&v)[2]) {
     float2 t = __ldg(reinterpret_cast<const float2*>(p));
     v[0] = t.x;
@@ -47,8 +50,6 @@ __device__ __forceinline__ void ld2(const __nv_bfloat16* p, float (&v)[2]) {
     v[0] = a.x;
     v[1] = a.y;
 }
-constexpr int kWarpChunk = kWarpVox * kWarpThreads;  // voxels per block and step
-constexpr int kWarpMaxChunks = 128;                 // chunks per block (support-restricted modes)
 
 template <typename TS>
 struct WarpArgs {
