@@ -112,7 +112,7 @@ int split_tiles(int nu, int nv);
 int split_groups(int nu, int nv);
 size_t split_part_floats(int nu, int nv, int nch);
 size_t split_counters(int nu, int nv);
-// Host: 8x4 warp tiles in launch order (split_tiles ints), centre first.
+// Host: 4x8 warp tiles in launch order (split_tiles ints), centre first.
 void project_warp_tile_order(int nu, int nv, int* order);
 
 // order: device permutation of the detector tiles (nullable), see project_tile_order.
