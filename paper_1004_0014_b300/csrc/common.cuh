@@ -53,6 +53,7 @@ struct RayGeom {
     float sdd;
     float origin[3];  // world position of voxel (0, 0, 0)
     float sp[3];      // voxel spacing, mm
+    int tile_u;       // detector columns of the split projector's warp tile: 4 (4 x 8) or 2 (2 x 16)
 };
 
 // Where a model's warped volume can be nonzero (computed once at load). The

@@ -102,17 +102,21 @@ cudaError_t launch_count_samples(Launcher& L, const VolDev& vd, const RayGeom* r
 // and counters that must be zero before the first launch (each launch leaves
 // them zero).
 struct SplitScratch {
-    const int* order = nullptr;   // split_tiles ints (project_warp_tile_order)
+    const int* order = nullptr;   // split_order_ints ints (project_warp_tile_order)
     float* part = nullptr;        // split_part_floats floats
     double* tile_mom = nullptr;   // split_tiles x kProjMom doubles
     double* group_mom = nullptr;  // split_groups x kProjMom doubles
     unsigned int* ctr = nullptr;  // split_counters uints, zeroed once
 };
+// Scratch sizes of the split projector: tiles and tile groups of the warp
+// tile shape (4 x 8 or 2 x 16 pixels, RayGeom::tile_u) with more tiles.
 int split_tiles(int nu, int nv);
 int split_groups(int nu, int nv);
 size_t split_part_floats(int nu, int nv, int nch);
 size_t split_counters(int nu, int nv);
-// Host: 4x8 warp tiles in launch order (split_tiles ints), centre first.
+int split_order_ints(int nu, int nv);
+// Host: the launch order of the 4 x 8 warp tiles, centre first, followed by
+// that of the 2 x 16 tiles (split_order_ints ints).
 void project_warp_tile_order(int nu, int nv, int* order);
 
 // order: device permutation of the detector tiles (nullable), see project_tile_order.

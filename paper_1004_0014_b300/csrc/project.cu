@@ -6,12 +6,14 @@
 // fixed point.
 //
 // Projector layout: one thread per ray; a warp of the solver pass owns a
-// 4 x 8 patch of detector pixels (4 along u, 8 along v), so the 32 samples a
-// warp takes at one step lie within about one voxel of each other and the
-// eight trilinear taps of the warp hit a handful of cache lines. The taller
-// patch keeps the warp's rays in fewer columns of the volume, so on oblique
-// gantry angles their cell changes fall on the same steps more often (4-8%
-// faster than 8 x 4 at every angle but 0, where it is equal). All lanes of a warp march the union of their sample
+// 4 x 8 patch of detector pixels (4 along u, 8 along v), or 2 x 16 within 30
+// degrees of a diagonal of the volume's x-y axes, so the 32 samples a warp
+// takes at one step lie within about one voxel of each other and the eight
+// trilinear taps of the warp hit a handful of cache lines. A tall patch keeps
+// the warp's rays in few (x, y) columns of the volume: each corner load then
+// touches fewer cache lines (4 x 8 is 4-8% faster than 8 x 4 at every angle
+// but 0, where it is equal; 2 x 16 is 3-6% faster again from 15 to 75
+// degrees and slower near the axes). All lanes of a warp march the union of their sample
 // ranges; a point outside the interpolant's support is clamped onto the zero
 // border of the padded volume and adds exactly zero, so the loop has no
 // divergent exits. The solver pass (k_project_split) splits each warp's range
@@ -640,7 +642,7 @@ __global__ void __launch_bounds__(kProjThreads, NCH == 4 ? 4 : 1) k_project(Proj
 // The 4/8-channel pass has 1.3 rays per resident thread at paper scale, and
 // its run time was the time of the longest 32x8 tile: the last wave left SMs
 // idle and blocks held their slots while waiting for their slowest warp. Here
-// the unit of work is a quarter of the sample range of a 4x8-ray warp tile.
+// the unit of work is a quarter of the sample range of a 32-ray warp tile.
 // Warps take items from a global counter, longest tiles first (the parts of
 // a tile one after another), so the busy time evens out at the scale of a
 // quarter of a ray. Each part's sums go to scratch; the warp that finishes a
@@ -658,20 +660,25 @@ constexpr float kInsideMargin = 1.0f / 64.0f;
 constexpr int kGroupTiles = 64;  // tiles per fixed-order moment group
 constexpr int kSplitThreads = 256;
 
+// Warp tiles of tu x (32 / tu) detector pixels covering nu x nv.
+__host__ __device__ __forceinline__ int split_tiles_of(int nu, int nv, int tu) {
+    return ((nu + tu - 1) / tu) * ((nv + 32 / tu - 1) / (32 / tu));
+}
+
 struct SplitArgs {
     const float* vol;
     VolDev vd;
     const RayGeom* rg;
-    const int* order;  // warp-tile permutation, longest rays first (nullable)
+    const int* order;  // warp-tile permutations of both shapes, longest rays first (nullable)
     int nu, nv, K;
-    int ntu, ntiles, ngroups;
+    int ntiles, ngroups;  // of the shape with more tiles: the scratch layout (split_tiles)
     float* p;
     float* q;
     const float* y;
     SolveState* st;
-    float* part;        // [ntiles][kParts][NCH + 1][32]: channel sums and the f compensation
-    double* tile_mom;   // [ntiles][kProjMom]
-    double* group_mom;  // [ngroups][kProjMom]
+    float* part;        // [tile][kParts][NCH + 1][32]: channel sums and the f compensation
+    double* tile_mom;   // [tile][kProjMom]
+    double* group_mom;  // [group][kProjMom]
     unsigned int* ctr;  // [0] queue, [1] warps done, [2] groups done, [4 + g] group g, [4 + ngroups + t] tile t
     int phase;
     cudaGraphConditionalHandle h;
@@ -685,11 +692,11 @@ struct SplitArgs {
 // only one warp per group runs it, so its code and registers stay out of the
 // per-tile path.
 template <int NCH>
-__device__ __noinline__ void finish_group(const SplitArgs& A, int group) {
+__device__ __noinline__ void finish_group(const SplitArgs& A, int group, int ntiles, int ngroups) {
     constexpr int KM = NCH == 8 ? 7 : (NCH == 6 ? 5 : 3);
     constexpr int NV = 3 + 3 * KM;
     const int lane = threadIdx.x & 31;
-    const int gsize = min(kGroupTiles, A.ntiles - group * kGroupTiles);
+    const int gsize = min(kGroupTiles, ntiles - group * kGroupTiles);
     unsigned int prev = 0;
     __threadfence();
     if (lane == 0) A.ctr[4 + group] = 0;
@@ -708,14 +715,14 @@ __device__ __noinline__ void finish_group(const SplitArgs& A, int group) {
     __syncwarp();
     if (lane == 0) prev = atomicAdd(A.ctr + 2, 1u);
     prev = __shfl_sync(0xffffffffu, prev, 0);
-    if (prev != (unsigned int)A.ngroups - 1) return;
+    if (prev != (unsigned int)ngroups - 1) return;
 
     // ---- this warp completed the last group: totals in group order, controller ----
     __threadfence();
     double tot[NV];
 #pragma unroll
     for (int m = 0; m < NV; ++m) tot[m] = 0.0;
-    for (int gg = lane; gg < A.ngroups; gg += 32)
+    for (int gg = lane; gg < ngroups; gg += 32)
 #pragma unroll
         for (int m = 0; m < NV; ++m) tot[m] += __ldcg(A.group_mom + (size_t)gg * kProjMom + m);
     {
@@ -736,7 +743,8 @@ __device__ __noinline__ void finish_group(const SplitArgs& A, int group) {
 // group and total sums. Kept out of line so that its registers do not weigh on
 // the sample loop.
 template <int NCH>
-__device__ __noinline__ void finish_tile(const SplitArgs& A, int tile, int iu, int iv, bool valid, float ds) {
+__device__ __noinline__ void finish_tile(const SplitArgs& A, int tile, int iu, int iv, bool valid, float ds, int ntiles,
+                                         int ngroups) {
     constexpr int KM = NCH == 8 ? 7 : (NCH == 6 ? 5 : 3);
     constexpr int NV = 3 + 3 * KM;
     const int lane = threadIdx.x & 31;
@@ -797,15 +805,29 @@ __device__ __noinline__ void finish_tile(const SplitArgs& A, int tile, int iu, i
     const int group = tile / kGroupTiles;
     if (lane == 0) prev = atomicAdd(A.ctr + 4 + group, 1u);
     prev = __shfl_sync(0xffffffffu, prev, 0);
-    if (prev == (unsigned int)min(kGroupTiles, A.ntiles - group * kGroupTiles) - 1) finish_group<NCH>(A, group);
+    if (prev == (unsigned int)min(kGroupTiles, ntiles - group * kGroupTiles) - 1)
+        finish_group<NCH>(A, group, ntiles, ngroups);
 }
 
 template <int NCH, bool HH = false>
 __global__ void __launch_bounds__(kSplitThreads, NCH == 4 ? 4 : 2) k_project_split(SplitArgs A) {
     const RayGeom g = *A.rg;
     const int lane = threadIdx.x & 31;
-    const unsigned int n_items = (unsigned int)A.ntiles * kParts;
-    unsigned int* tile_ctr = A.ctr + 4 + A.ngroups;
+    // This angle's warp tile, tu x (32 / tu) pixels (4 x 8 or 2 x 16): its
+    // tile counts live in shared memory and are read once per work item, so
+    // they hold no registers across the sample loop.
+    __shared__ int shape[5];  // tu, tiles along u, tiles, tile groups, offset of its order
+    if (threadIdx.x == 0) {
+        const int tu = g.tile_u == 2 ? 2 : 4, nt = split_tiles_of(A.nu, A.nv, tu);
+        shape[0] = tu;
+        shape[1] = (A.nu + tu - 1) / tu;
+        shape[2] = nt;
+        shape[3] = (nt + kGroupTiles - 1) / kGroupTiles;
+        shape[4] = tu == 2 ? split_tiles_of(A.nu, A.nv, 4) : 0;
+    }
+    __syncthreads();
+    const volatile int* vshape = shape;
+    unsigned int* tile_ctr = A.ctr + 4 + A.ngroups;  // the layout's (largest) group count
 
     float lo[3] = {-1.0f, -1.0f, -1.0f}, hi[3] = {g.nmax[0], g.nmax[1], g.nmax[2]};
     bool nonzero = true;
@@ -817,11 +839,13 @@ __global__ void __launch_bounds__(kSplitThreads, NCH == 4 ? 4 : 2) k_project_spl
         unsigned int item = 0;
         if (lane == 0) item = atomicAdd(A.ctr, 1u);
         item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= n_items) break;
+        const int ntiles = vshape[2];
+        if (item >= (unsigned int)ntiles * kParts) break;
         const int slot = (int)(item / kParts), part = (int)(item - (unsigned int)slot * kParts);
-        int tile = A.order ? __ldg(A.order + slot) : slot;
-        if (tile < 0 || tile >= A.ntiles) tile = slot;  // a permutation never trips this
-        const int iu = (tile % A.ntu) * 4 + (lane & 3), iv = (tile / A.ntu) * 8 + (lane >> 2);
+        int tile = A.order ? __ldg(A.order + vshape[4] + slot) : slot;
+        if (tile < 0 || tile >= ntiles) tile = slot;  // a permutation never trips this
+        const int tu = vshape[0], ntu = vshape[1];
+        const int iu = (tile % ntu) * tu + (lane & (tu - 1)), iv = (tile / ntu) * (32 / tu) + (lane / tu);
         const bool valid = iu < A.nu && iv < A.nv;
 
         float b[3];
@@ -911,7 +935,7 @@ __global__ void __launch_bounds__(kSplitThreads, NCH == 4 ? 4 : 2) k_project_spl
         prev = __shfl_sync(0xffffffffu, prev, 0);
         if (prev != kParts - 1) continue;
 
-        finish_tile<NCH>(A, tile, iu, iv, valid, g.ds);
+        finish_tile<NCH>(A, tile, iu, iv, valid, g.ds, vshape[2], vshape[3]);
     }
     // The last warp to leave resets the queue for the next launch (no warp of
     // this launch reads it again).
@@ -1075,23 +1099,28 @@ cudaError_t launch_begin(Launcher& L, const float* y, int R, SolveState* st, dou
     return L(k_begin, dim3(kReduceBlocks), dim3(kReduceThreads), 0, y, R, st, partials, counter);
 }
 
-int split_tiles(int nu, int nv) { return ((nu + 3) / 4) * ((nv + 7) / 8); }
+int split_tiles(int nu, int nv) { return max(split_tiles_of(nu, nv, 4), split_tiles_of(nu, nv, 2)); }
 int split_groups(int nu, int nv) { return (split_tiles(nu, nv) + kGroupTiles - 1) / kGroupTiles; }
 size_t split_part_floats(int nu, int nv, int nch) { return (size_t)split_tiles(nu, nv) * kParts * (nch + 1) * 32; }
 size_t split_counters(int nu, int nv) { return 4 + (size_t)split_groups(nu, nv) + (size_t)split_tiles(nu, nv); }
+int split_order_ints(int nu, int nv) { return split_tiles_of(nu, nv, 4) + split_tiles_of(nu, nv, 2); }
 
 void project_warp_tile_order(int nu, int nv, int* order) {
-    // 4x8-ray warp tiles sorted by the distance of their centre from the
-    // detector centre (long central rays first); ties by tile index.
-    const int ntu = (nu + 3) / 4, ntv = (nv + 7) / 8, n = ntu * ntv;
+    // For each tile shape (4 x 8, then 2 x 16): the warp tiles sorted by the
+    // distance of their centre from the detector centre (long central rays
+    // first); ties by tile index.
     const double cu = 0.5 * nu, cv = 0.5 * nv;
-    std::vector<std::pair<double, int>> keys((size_t)n);
-    for (int t = 0; t < n; ++t) {
-        double u = ((t % ntu) + 0.5) * 4 - cu, v = ((t / ntu) + 0.5) * 8 - cv;
-        keys[(size_t)t] = {u * u + v * v, t};
+    for (int tu : {4, 2}) {
+        const int tv = 32 / tu, ntu = (nu + tu - 1) / tu, n = split_tiles_of(nu, nv, tu);
+        std::vector<std::pair<double, int>> keys((size_t)n);
+        for (int t = 0; t < n; ++t) {
+            double u = ((t % ntu) + 0.5) * tu - cu, v = ((t / ntu) + 0.5) * tv - cv;
+            keys[(size_t)t] = {u * u + v * v, t};
+        }
+        std::sort(keys.begin(), keys.end());
+        for (int t = 0; t < n; ++t) order[t] = keys[(size_t)t].second;
+        order += n;
     }
-    std::sort(keys.begin(), keys.end());
-    for (int t = 0; t < n; ++t) order[t] = keys[(size_t)t].second;
 }
 
 namespace {
@@ -1130,7 +1159,7 @@ cudaError_t launch_project(Launcher& L, const VolDev& vd, const float* vol_pad, 
                            const SplitScratch* ss) {
     if (nch >= 4 && ss && ss->ctr) {
         const int ntiles = split_tiles(nu, nv), ngroups = split_groups(nu, nv);
-        SplitArgs S{vol_pad, vd, rg, ss->order, nu, nv, K, (nu + 3) / 4, ntiles, ngroups, p, q, y, st,
+        SplitArgs S{vol_pad, vd, rg, ss->order, nu, nv, K, ntiles, ngroups, p, q, y, st,
                     ss->part, ss->tile_mom, ss->group_mom, ss->ctr, phase, h, use_graph, sup};
         const int blocks = split_grid(nch);
         if (blocks <= 0) return cudaErrorInvalidDevice;

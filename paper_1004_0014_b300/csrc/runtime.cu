@@ -284,6 +284,11 @@ RayGeom make_rg(const pr_volume_desc& v, const pr_geometry& g, double th) {
     r.cu = (float)cu;
     r.cv = (float)cv;
     r.sdd = (float)g.sdd;
+    // Warp tile of the split projector: within 15 degrees of a volume axis the
+    // detector's u direction runs along one axis and 4 x 8 pixels are fastest;
+    // nearer the diagonals 2 x 16 keeps a warp's rays in fewer (x, y) columns
+    // (measured crossover at paper scale).
+    r.tile_u = fmin(fabs(st), fabs(ct)) < 0.2588190451 ? 4 : 2;
     return r;
 }
 
@@ -394,7 +399,7 @@ size_t model_bytes(const pr_volume_desc& v, const pr_geometry& g, int K, int sto
     return np * ts + 3 * n * 4 + 3 * (size_t)K * n * ts + np * (size_t)fh_floats(layout) * 4 + np * 4 + R * 4 + R * K * 4 + R * 4 +
            R * 4 + n * 4 + partial_doubles(g, vd) * 8 + 64 + sizeof(SolveState) + 64 + 128 +
            sizeof(RayGeom) + 16 + (size_t)project_blocks(g.nu, g.nv) * sizeof(int) + sizeof(Support) +
-           (size_t)split_tiles(g.nu, g.nv) * sizeof(int) + split_part_floats(g.nu, g.nv, (int)nch) * 4 +
+           (size_t)split_order_ints(g.nu, g.nv) * sizeof(int) + split_part_floats(g.nu, g.nv, (int)nch) * 4 +
            ((size_t)split_tiles(g.nu, g.nv) + split_groups(g.nu, g.nv)) * kProjMom * 8 +
            split_counters(g.nu, g.nv) * 4 + kTrialLog +
            (size_t)((v.nx + 3) / 4) * ((v.ny + 3) / 4) * ((v.nz + 3) / 4);
@@ -1324,7 +1329,7 @@ int load_resident(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
     A(&m->steps, 16);
     A(&m->order, (size_t)project_blocks(geom->nu, geom->nv) * sizeof(int));
     A(&m->sup, sizeof(Support));
-    A(&m->order_w, (size_t)split_tiles(geom->nu, geom->nv) * sizeof(int));
+    A(&m->order_w, (size_t)split_order_ints(geom->nu, geom->nv) * sizeof(int));
     A(&m->ss.part, split_part_floats(geom->nu, geom->nv, fh_logical(m->nch)) * 4);
     A(&m->ss.tile_mom, (size_t)split_tiles(geom->nu, geom->nv) * kProjMom * 8);
     A(&m->ss.group_mom, (size_t)split_groups(geom->nu, geom->nv) * kProjMom * 8);
@@ -1351,7 +1356,7 @@ int load_resident(pr_ctx* c, const pr_volume_desc* vol, const pr_geometry* geom,
     cudaMemcpyKind kind = location == PR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     cudaStream_t s = c->stream;
     std::vector<int> order_host((size_t)project_blocks(geom->nu, geom->nv));  // lives until the sync below
-    std::vector<int> order_w_host((size_t)split_tiles(geom->nu, geom->nv));
+    std::vector<int> order_w_host((size_t)split_order_ints(geom->nu, geom->nv));
     do {
         if ((e = cudaMemsetAsync(m->f0p, 0, np * ts, s))) break;
         if ((e = cudaMemsetAsync(m->fh, 0, np * fh_floats(m->nch) * 4, s))) break;
