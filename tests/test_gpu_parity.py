@@ -165,6 +165,27 @@ def test_cost_and_gradient_match_oracle(ctx, small):
             assert eg < TOL_GRAD
 
 
+@pytest.mark.parametrize("deg", [0.0, 10.0, 14.0, 16.0, 45.0, 80.0, 100.0, 200.0])
+def test_solver_projector_matches_oracle_for_both_warp_tiles(ctx, small, deg):
+    """The solver-pass projector (P f, P h_k and the fused moments) takes 4 x 8
+    detector pixels per warp within 15 degrees of a volume axis and 2 x 16
+    elsewhere: P f, J and the forward-mode gradient against the oracle on both
+    sides of the switch and around the rotation."""
+    vol, geom, om = small["vol"], small["geom"], small["om"]
+    th = math.radians(deg)
+    ft = O.warp(vol, om.f0, small["x_test"])
+    y = _f32(noisy(O.project(vol, geom, th, ft), small["seed"]))
+    w, a, b = np.array([0.4, -0.3, 0.2]), 1.02, -0.01
+    J, g, p = ctx.cost_grad(small["mid"], _cuda(y), th, w, a, b, 0, return_p=True)
+    po = O.project(vol, geom, th, O.warp(vol, om.f0, O.dvf(vol, om.mean, om.U, w)))
+    go, Jo, _ = O.gradient(om, geom, th, w, a, b, _up(y))
+    ep, eJ, eg = rel(p.cpu().numpy(), po), abs(J - Jo) / Jo, rel(g, go)
+    report("solver_projector_tiles", deg=deg, p_rel=ep, J_rel=eJ, g_rel=eg)
+    assert ep < TOL_PROJ
+    assert eJ < TOL_PROJ
+    assert eg < TOL_GRAD
+
+
 def test_forward_and_vjp_match_oracle(ctx, small):
     import torch
 
