@@ -47,9 +47,8 @@ WORKLOAD = "paper-scale plain method, %s storage: 256x256x120 @ 2x2x2.5 mm, K=%d
 # Trials and accepted steps per reconstruction of this library's solver on this
 # workload (measured on the GPU arm); used only to scale the oracle's per-step
 # sample to a whole reconstruction in the reference arm.
-TRIALS_PER_SOLVE = 10.8
+TRIALS_PER_SOLVE = 10.7
 ITERS_PER_SOLVE = 9.5
-REF_ROWS = 12  # detector rows the reference arm projects per step
 
 
 # ----------------------------------------------------------------------------
@@ -264,9 +263,9 @@ def warp_voxels_evaluated(vol, box, block_voxels: int = 1024) -> int:
     return int(sizes[blocks].sum())
 
 
-def recorded_traffic(kernel: str, source: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, only
-    if the kernel's source file is unchanged since the capture (else None)."""
+def recorded_capture(kernel: str, source: str):
+    """The committed ncu record of `kernel` (profiles/traffic.json), only if the
+    kernel's source file is unchanged since the capture (else None)."""
     import hashlib
 
     try:
@@ -274,7 +273,13 @@ def recorded_traffic(kernel: str, source: str):
         sha = hashlib.sha256(open(os.path.join(ROOT, "paper_1004_0014_b300", "csrc", source), "rb").read()).hexdigest()
     except (OSError, ValueError, KeyError):
         return None
-    return rec["bytes_per_launch"] if rec.get("source_sha256") == sha else None
+    return rec if rec.get("source_sha256") == sha else None
+
+
+def recorded_traffic(kernel: str, source: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None."""
+    rec = recorded_capture(kernel, source)
+    return rec["bytes_per_launch"] if rec else None
 
 
 # ----------------------------------------------------------------------------
@@ -558,7 +563,9 @@ def run_ours(args):
                 "algorithmic_flops_per_launch": flops, "share_of_solve": share_proj,
                 "algorithmic_bytes_per_launch": bytes_proj,
                 "achieved_gbs": bytes_proj / (t_proj_ms / 1000.0) / 1e9,
-                "limiter": "L1 data pipe returning the trilinear corners (ncu: L1/TEX throughput 76% at 0 deg, 92% at 60 deg; DRAM 1.6%)"}
+                "limiter": "L1 data pipe returning the trilinear corners (ncu, DRAM 1.6%)",
+                "l1_data_pipe_pct_of_peak": ((recorded_capture("k_project_split<4>", "project.cu") or {})
+                                             .get("l1_data_pipe_pct") if (Km == 3 and not bf16) else None)}
     ts = 2 if bf16 else 4  # bytes per stored value of f0 and U
     # the solver's warp evaluates the blocks that meet the support box at w;
     # with w repeated (the timing loop) the others hold zeros already and are
