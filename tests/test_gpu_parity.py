@@ -88,7 +88,7 @@ def test_warp_matches_oracle(ctx, small):
 
 
 def test_warp_ragged_grid_matches_oracle(ctx):
-    vol = RAGGED_VOL  # N = 1287: not a multiple of 4, rows not 4-aligned
+    vol = RAGGED_VOL  # N = 1287: odd (the two-voxel vector loads fall back), rows not aligned
     rng = np.random.default_rng(7)
     f0 = _f32(rng.random(vol.shape))
     mean = _f32(2.0 * rng.standard_normal((3,) + vol.shape))
@@ -184,6 +184,35 @@ def test_solver_projector_matches_oracle_for_both_warp_tiles(ctx, small, deg):
     assert ep < TOL_PROJ
     assert eJ < TOL_PROJ
     assert eg < TOL_GRAD
+
+
+@pytest.mark.parametrize("th", [0.1, 0.8])
+def test_solver_projector_ragged_matches_oracle(ctx, th):
+    """The solver projector on a ragged grid and a 37 x 21 detector (partial
+    warp tiles along both detector axes), with 4 x 8 (0.1 rad) and 2 x 16
+    (0.8 rad) warp tiles: P f, J and the forward-mode gradient against the
+    oracle."""
+    vol, geom = RAGGED_VOL, RAGGED_GEOM
+    rng = np.random.default_rng(11)
+    f0 = _f32(rng.random(vol.shape))
+    mean = _f32(2.0 * rng.standard_normal((3,) + vol.shape))
+    U = _f32(rng.standard_normal((2, 3) + vol.shape))
+    mid = ctx.load_model(vol, geom, f0, mean, U, np.zeros(3))
+    om = O.Model(vol, _up(f0), _up(mean), _up(U), np.zeros(3))
+    try:
+        w, a, b = np.array([0.3, -0.8]), 0.9, 0.05
+        f = O.warp(vol, om.f0, O.dvf(vol, om.mean, om.U, w))
+        po = O.project(vol, geom, th, f)
+        y = _f32(noisy(po, 5))
+        J, g, p = ctx.cost_grad(mid, _cuda(y), th, w, a, b, 0, return_p=True)
+        go, Jo, _ = O.gradient(om, geom, th, w, a, b, _up(y))
+        ep, eJ, eg = rel(p.cpu().numpy(), po), abs(J - Jo) / Jo, rel(g, go)
+        report("solver_projector_ragged", angle=th, p_rel=ep, J_rel=eJ, g_rel=eg)
+        assert ep < TOL_PROJ
+        assert eJ < TOL_PROJ
+        assert eg < TOL_GRAD
+    finally:
+        ctx.release_model(mid)
 
 
 def test_forward_and_vjp_match_oracle(ctx, small):
