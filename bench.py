@@ -247,10 +247,11 @@ def timed_frames(steps: int, warmup: int):
     return list(range(-warmup, 0)) + timed
 
 
-def warp_voxels_evaluated(vol, box, block_voxels: int = 1024) -> int:
-    """Voxels of the warp pass's blocks (block_voxels consecutive voxels of
-    the flat grid each) that meet the inclusive voxel box ((x0, y0, z0),
-    (x1, y1, z1)); the other blocks write zeros without reading a field."""
+def warp_voxels_evaluated(vol, box, block_voxels: int = 512) -> int:
+    """Voxels of the warp pass's chunks (block_voxels consecutive voxels of
+    the flat grid each, the kernel's 512) that meet the inclusive voxel box
+    ((x0, y0, z0), (x1, y1, z1)); the other chunks write zeros without reading
+    a field."""
     (x0, y0, z0), (x1, y1, z1) = box
     ix, iy, iz = np.arange(vol.nx), np.arange(vol.ny), np.arange(vol.nz)
     inside = (((iz >= z0) & (iz <= z1))[:, None, None] & ((iy >= y0) & (iy <= y1))[None, :, None]
@@ -567,7 +568,7 @@ def run_ours(args):
                 "l1_data_pipe_pct_of_peak": ((recorded_capture("k_project_split<4>", "project.cu") or {})
                                              .get("l1_data_pipe_pct") if (Km == 3 and not bf16) else None)}
     ts = 2 if bf16 else 4  # bytes per stored value of f0 and U
-    # the solver's warp evaluates the blocks that meet the support box at w;
+    # the solver's warp evaluates the 512-voxel chunks that meet the support box at w;
     # with w repeated (the timing loop) the others hold zeros already and are
     # left alone
     n_eval = warp_voxels_evaluated(vol, ctx.warp_box(mid, w_start))

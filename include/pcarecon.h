@@ -383,7 +383,7 @@ int pr_count_samples(pr_ctx* ctx, int model_id, double angle_rad, const double* 
  * (K doubles, host): box[0..2] = lowest x, y, z voxel index, box[3..5] =
  * highest, clamped to the grid (empty when box[c] > box[3 + c]). Voxels
  * outside it lie farther than the displacement bound from every nonzero f0
- * voxel and are exact zeros: a block of the pass (1024 consecutive voxels of
+ * voxel and are exact zeros: a chunk of the pass (512 consecutive voxels of
  * the flat grid) none of whose voxels is in the box writes its zeros without
  * reading a field, or is left alone where no earlier pass can have left a
  * nonzero in it. Synchronous. Errors: PR_EINVAL, PR_ENOMODEL, PR_ECUDA. */

@@ -1,5 +1,5 @@
 """Host-side arithmetic of the benchmark (no GPU): the count of voxels the
-support-restricted warp pass evaluates (blocks of 1024 consecutive voxels of
+support-restricted warp pass evaluates (chunks of 512 consecutive voxels of
 the flat grid that meet the warp box) against a brute-force count, the
 algorithmic flops per projector sample, the reading of the clock samples taken
 during the timed region (a run that saw a slowdown reason must say so), and
@@ -11,7 +11,7 @@ import pytest
 from phantom import Volume
 
 
-def _brute(vol, box, block=1024):
+def _brute(vol, box, block=512):
     (x0, y0, z0), (x1, y1, z1) = box
     n = vol.nx * vol.ny * vol.nz
     total = 0

@@ -1,6 +1,6 @@
 """The solver's warp pass (Eq. 1 and the pull-back of Section 2.2) evaluates
-only the blocks of the grid that meet the support box of the warped volume:
-the displacement bound around the nonzero voxels of f0. Every other block is
+only the 512-voxel chunks of the grid that meet the support box of the warped
+volume: the displacement bound around the nonzero voxels of f0. Every other chunk is
 written as zeros without reading a field, or left alone where no earlier pass
 can have left a nonzero in it. These tests check the bound itself
 (every nonzero f or h_k of the unrestricted warp lies in the reported box),
