@@ -533,6 +533,9 @@ def run_ours(args):
     # The warp kernel is the HBM-bound one; its roofline is reported beside it.
     N, R, Km = vol.n, geom.n_rays, w["K"]
     nch = 4 if Km <= 3 else (6 if Km <= 5 else 8)
+    # bytes of one voxel's record in the solver volume: nch floats, or the
+    # packed 16-byte float32 f + float16 h record of bfloat16 models with K = 4, 5
+    rec_bytes = 16 if (bf16 and Km in (4, 5)) else 4 * nch
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -551,7 +554,7 @@ def run_ours(args):
     share_proj = (1 + trials_per_solve) * t_proj_ms / per_solve_ms
     share_warp = (1 + trials_per_solve) * kern["warp_fh"] / per_solve_ms
     proj_tflops = flops / (t_proj_ms / 1000.0) / 1e12
-    bytes_proj = N * 4 * nch + R * 4 * (1 + Km)
+    bytes_proj = N * rec_bytes + R * 4 * (1 + Km)
     roofline = {"kernel": "k_project_split<%d> (f, h_1..h_%d)" % (nch, Km), "bound": "alu", "achieved": proj_tflops,
                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": proj_tflops / fp32_peak,
                 "traffic": recorded_traffic("k_project_split<4>", "project.cu") if (Km == 3 and not bf16) else None,
@@ -572,7 +575,7 @@ def run_ours(args):
     # with w repeated (the timing loop) the others hold zeros already and are
     # left alone
     n_eval = warp_voxels_evaluated(vol, ctx.warp_box(mid, w_start))
-    bytes_warp = n_eval * (12 + 3 * ts * Km + ts + 4 * nch)
+    bytes_warp = n_eval * (12 + 3 * ts * Km + ts + rec_bytes)
     warp_gbs = bytes_warp / (kern["warp_fh"] / 1000.0) / 1e9
     roofline_warp = {"kernel": "k_warp<%d, f+h, %s>" % (Km, "bf16" if bf16 else "float"), "bound": "hbm",
                      "achieved": warp_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": warp_gbs / hbm_peak,
