@@ -240,12 +240,12 @@ __device__ __forceinline__ void warp_pair(const WarpArgs<TS>& A, long long v0, c
 
 // Resident 256-thread blocks per SM the register cap aims at (measured on the
 // paper-scale pass): K <= 3 five (four for bfloat16, whose conversions spill at
-// five); K = 4, 5 three (four for bfloat16, whose fields take half the
-// registers); K = 6, 7 two.
+// five); K = 4, 5 three (for bfloat16, whose fields take half the registers,
+// five at K = 4 and four at K = 5); K = 6, 7 two.
 template <int K, typename TS>
 constexpr int warp_min_blocks() {
     constexpr bool f32 = std::is_same<TS, float>::value;
-    return K <= 3 ? (f32 ? 5 : 4) : (K <= 5 ? (f32 ? 3 : 4) : 2);
+    return K <= 3 ? (f32 ? 5 : 4) : (K <= 5 ? (f32 ? 3 : (K == 4 ? 5 : 4)) : 2);
 }
 
 // Fields of the two voxels v0, v0 + 1 (v0 < n), then the warp and h (warp_pair).
